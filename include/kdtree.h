@@ -1,0 +1,185 @@
+/*
+ * kdtree.h -- C ABI of the GB300 presorting k-d tree builder.
+ *
+ * The library builds the balanced k-d tree of Brown, "Building a Balanced
+ * k-d Tree in O(kn log n) Time", Section 2.1: n tuples of k coordinates in,
+ * a balanced binary tree of tuple indices with "less than" / "greater than"
+ * children out, duplicate tuples removed.  Every step runs in CUDA kernels
+ * on one GB300 (sm_103a); the calls below only marshal arguments, order
+ * work on a CUDA stream and report status.
+ *
+ * Conventions (all calls):
+ *  - Every call returns a kd_status; none throws or aborts.  After an
+ *    error the context stays usable and kd_last_error() describes it.
+ *  - Input coordinates are borrowed for the duration of the call (kd_submit
+ *    copies them before it returns).  Outputs are allocated by the caller.
+ *  - Pointers flagged "on_device" are CUDA device pointers on the context's
+ *    device; otherwise they are host pointers (page-locked memory gives the
+ *    fastest copies, pageable memory works).
+ *  - 0 <= n <= KD_MAX_N tuples per cloud; 1 <= k <= KD_MAX_K; the sum of
+ *    tuples over a batch is also at most KD_MAX_N.
+ *
+ * Output layout (in-order addresses).  Node address a in [0, m) holds the
+ * tuple chosen as the median of the sub-range whose median address is a;
+ * the root is at (m - 1) / 2; the children of node a with range [lo, hi]
+ * are the medians of [lo, a - 1] and [a + 1, hi] (-1 when empty); the split
+ * dimension of a node at depth t is t mod k.  Medians are lower medians,
+ * lo + (hi - lo) / 2 (the paper uses only odd sizes).  Of a run of identical
+ * tuples the one with the smallest index survives.  Floats compare
+ * numerically (-0.0 equals +0.0); a NaN coordinate is an error.
+ */
+#ifndef KDTREE_H
+#define KDTREE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KD_MAX_K 8
+#define KD_MAX_N 1073741823LL /* 2^30 - 1: look-back status words hold 30-bit counts */
+
+typedef enum {
+    KD_OK = 0,
+    KD_EINVAL = -1,   /* bad argument: null pointer, n or k out of range, bad dtype */
+    KD_ENOMEM = -2,   /* device allocation failed or the memory budget is exceeded */
+    KD_EDEVICE = -3,  /* a CUDA call failed (message in kd_last_error) */
+    KD_ETIMEOUT = -4, /* a bounded device wait or kd_wait ran out of time */
+    KD_EBUSY = -5,    /* the serving queue is full */
+    KD_ENAN = -6      /* a float coordinate is NaN */
+} kd_status;
+
+typedef enum { KD_I32 = 0, KD_I64 = 1, KD_F32 = 2 } kd_dtype;
+
+typedef struct {
+    int device;              /* CUDA device ordinal */
+    void *cuda_stream;       /* cudaStream_t to order work on; NULL: the library makes its own */
+    size_t mem_budget_bytes; /* cap on the library's device workspace; 0: no cap */
+    int tile_T;              /* 0: default.  Reserved for the autotuner */
+    int switch_threshold;    /* subtree size finished on chip; 0: default per k */
+    int debug;               /* nonzero: synchronise and check after every phase */
+} kd_config;
+
+typedef struct {
+    const void *coords; /* row-major n x k array of dtype; borrowed for the call */
+    int64_t n;
+    int k;
+    kd_dtype dtype;
+    int on_device; /* coords is a device pointer */
+} kd_cloud;
+
+typedef struct {
+    int32_t m;           /* out: tuples after duplicate removal (= nodes) */
+    int32_t root;        /* out: root address, (m - 1) / 2, or -1 when m = 0 */
+    int32_t *node_tuple; /* caller-allocated, capacity n: tuple index per address */
+    int32_t *left;       /* optional (NULL to skip), capacity n: child addresses */
+    int32_t *right;      /* optional, capacity n */
+    uint8_t *dim;        /* optional, capacity n: split dimension per address */
+    int on_device;       /* the four arrays are device pointers */
+} kd_tree;
+
+typedef struct kd_ctx kd_ctx;
+typedef struct kd_presorted *kd_handle;
+typedef int64_t kd_ticket;
+
+/*
+ * Create a context on cfg->device.  *out receives the context; it owns a
+ * stream-ordered device memory pool and, if cfg->cuda_stream is NULL, a
+ * stream.  cfg may be NULL for defaults (device 0).
+ */
+kd_status kd_create(kd_ctx **out, const kd_config *cfg);
+
+/*
+ * Presort (Section 2.1, first paragraphs; duplicates paragraph): transform
+ * the coordinates to order-preserving unsigned keys, sort index arrays by
+ * the k cyclic super keys x_d : x_{d+1} : ... : x_{d-1}, and remove
+ * duplicate tuples.  *out receives a handle owning the device arrays
+ * (the k index orders and their rank vectors); pass it to kd_build or
+ * release it with kd_release.  Errors: KD_EINVAL, KD_ENAN, KD_ENOMEM,
+ * KD_EDEVICE, KD_ETIMEOUT.  Synchronises the stream once to learn m.
+ */
+kd_status kd_presort(kd_ctx *ctx, const kd_cloud *cloud, kd_handle *out);
+
+/* m (tuples after duplicate removal), n and k of a presorted handle. */
+kd_status kd_handle_info(kd_handle h, int64_t *n, int32_t *m, int *k);
+
+/*
+ * Copy the k presorted, deduplicated index arrays of a handle (array d in
+ * super-key-d order, tuple indices local to the cloud) into out, k rows of
+ * m int32 each, row-major.  For checking the presort on its own.
+ */
+kd_status kd_handle_arrays(kd_ctx *ctx, kd_handle h, int32_t *out, int on_device);
+
+/*
+ * Build (Section 2.1, partition and recursion paragraphs; Appendix
+ * "Optimized Partitioning" for partitioning only the k-1 non-primary
+ * arrays): level by level, the median of each segment of the primary array
+ * becomes a node and the other arrays are partitioned around it in address
+ * order, keeping their sorted order.  Consumes and releases the handle
+ * (also on error).  out->node_tuple must hold n entries.
+ */
+kd_status kd_build(kd_ctx *ctx, kd_handle h, kd_tree *out);
+
+/* Release a handle that will not be built. */
+kd_status kd_release(kd_ctx *ctx, kd_handle h);
+
+/*
+ * Presort and build `count` independent clouds (same k and dtype) as one
+ * batch: the clouds share every launch.  outs[i] receives cloud i's tree;
+ * the result of each cloud equals its plain kd_presort + kd_build result.
+ */
+kd_status kd_build_batch(kd_ctx *ctx, const kd_cloud *clouds, int count, kd_tree *outs);
+
+/*
+ * Serving: enqueue one build request.  The coordinates are copied before
+ * the call returns; out's arrays must stay valid until kd_wait reports the
+ * ticket done.  A background scheduler admits queued requests while
+ * earlier ones run, within cfg->mem_budget_bytes, and co-batches requests of
+ * equal k and dtype.  KD_EBUSY when the queue is full.
+ */
+kd_status kd_submit(kd_ctx *ctx, const kd_cloud *cloud, kd_tree *out, kd_ticket *ticket);
+
+/*
+ * Wait up to timeout_ms (negative: forever) for a ticket.  Returns the
+ * request's own status, or KD_ETIMEOUT if it is still pending.  A finished
+ * ticket is forgotten once it has been reported.
+ */
+kd_status kd_wait(kd_ctx *ctx, kd_ticket ticket, int timeout_ms);
+
+/* Serving statistics: completed requests and their admission-to-result
+ * latency percentiles (microseconds). */
+kd_status kd_serving_stats(kd_ctx *ctx, int64_t *completed, double *p50_us, double *p99_us);
+
+/* Stop serving, free every device resource and the context. */
+kd_status kd_destroy(kd_ctx *ctx);
+
+/* Text of the last error on this context ("" if none).  Valid until the
+ * next call on the context. */
+const char *kd_last_error(kd_ctx *ctx);
+
+/* Kernels launched by this context since creation (instrumentation). */
+int64_t kd_launch_count(kd_ctx *ctx);
+
+/*
+ * Kernel timing (instrumentation; active when cfg->debug & 2): CUDA events
+ * recorded on the context's stream around every launch, summed per kernel
+ * family (0 transform, 1 sort pass, 2 dedup, 3 records, 4 level pass,
+ * 5 finisher, 6 top nodes, 7 other).  *ms: device time, *launches: launch
+ * count, *units: elements the launches processed, *bytes: the algorithmic
+ * bytes those launches must move (reads + writes per element of each kernel,
+ * summed over launches).  Any output pointer may be NULL.  Synchronises the
+ * stream.
+ */
+kd_status kd_kernel_stats(kd_ctx *ctx, int family, double *ms, int64_t *launches, double *units,
+                          double *bytes);
+
+/* Zero the kernel timing sums. */
+kd_status kd_kernel_stats_reset(kd_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KDTREE_H */

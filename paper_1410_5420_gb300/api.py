@@ -1,0 +1,238 @@
+"""Python binding of the C ABI (include/kdtree.h), same names as the C calls.
+
+Only argument marshalling happens here: tensors and arrays become pointers
+and sizes, outputs are allocated, status codes become exceptions.  Every
+step of the presort and build runs in the library's CUDA kernels.
+Device tensors (torch, CUDA) are passed as device pointers; numpy arrays and
+CPU tensors as host pointers.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _lib
+from ._lib import KdCloud, KdConfig, KdTree
+
+try:
+    import torch
+except Exception:  # pragma: no cover - torch is present on every target
+    torch = None
+
+
+class KdError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_lib.STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_NP_DT = {np.dtype(np.int32): _lib.KD_I32, np.dtype(np.int64): _lib.KD_I64, np.dtype(np.float32): _lib.KD_F32}
+
+
+def _torch_dt():
+    return {torch.int32: _lib.KD_I32, torch.int64: _lib.KD_I64, torch.float32: _lib.KD_F32}
+
+
+class Context:
+    """A kd_ctx: device, stream, memory pool."""
+
+    def __init__(self, ptr: int, device: int):
+        self.ptr = ctypes.c_void_p(ptr)
+        self.device = device
+
+    def check(self, rc: int):
+        if rc != _lib.KD_OK:
+            msg = _lib.load().kd_last_error(self.ptr)
+            raise KdError(rc, msg.decode() if msg else "")
+
+    def close(self):
+        if self.ptr:
+            _lib.load().kd_destroy(self.ptr)
+            self.ptr = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+@dataclass
+class Handle:
+    ptr: ctypes.c_void_p
+    n: int
+    m: int
+    k: int
+    on_device: bool
+
+
+def kd_create(device: int = 0, stream=None, mem_budget_bytes: int = 0, switch_threshold: int = 0,
+              debug: int = 0) -> Context:
+    """kd_create.  ``stream``: a torch.cuda.Stream, an int handle, or None for
+    torch's current stream on ``device``."""
+    lib = _lib.load()
+    if stream is None and torch is not None and torch.cuda.is_available():
+        stream = torch.cuda.current_stream(device)
+    sh = stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0)
+    cfg = KdConfig(device, ctypes.c_void_p(sh), mem_budget_bytes, 0, switch_threshold, debug)
+    out = ctypes.c_void_p()
+    rc = lib.kd_create(ctypes.byref(out), ctypes.byref(cfg))
+    if rc != _lib.KD_OK:
+        raise KdError(rc, "kd_create failed")
+    return Context(out.value, device)
+
+
+def _cloud(coords) -> tuple[KdCloud, object]:
+    """KdCloud for a torch tensor or numpy array; returns (struct, keep-alive)."""
+    if torch is not None and isinstance(coords, torch.Tensor):
+        t = coords.contiguous()
+        if t.dim() != 2 or t.dtype not in _torch_dt():
+            raise ValueError("coords must be an n x k int32/int64/float32 tensor")
+        return KdCloud(t.data_ptr(), t.shape[0], t.shape[1], _torch_dt()[t.dtype], int(t.is_cuda)), t
+    a = np.ascontiguousarray(coords)
+    if a.ndim != 2 or a.dtype not in _NP_DT:
+        raise ValueError("coords must be an n x k int32/int64/float32 array")
+    return KdCloud(a.ctypes.data, a.shape[0], a.shape[1], _NP_DT[a.dtype], 0), a
+
+
+def kd_presort(ctx: Context, coords) -> Handle:
+    """kd_presort: presort + dedup; the handle owns the device arrays."""
+    c, keep = _cloud(coords)
+    h = ctypes.c_void_p()
+    ctx.check(_lib.load().kd_presort(ctx.ptr, ctypes.byref(c), ctypes.byref(h)))
+    del keep
+    n, m, k = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int()
+    ctx.check(_lib.load().kd_handle_info(h, ctypes.byref(n), ctypes.byref(m), ctypes.byref(k)))
+    return Handle(h, n.value, m.value, k.value, bool(c.on_device))
+
+
+def kd_handle_arrays(ctx: Context, h: Handle) -> np.ndarray:
+    """The k presorted deduplicated index arrays (k x m, host)."""
+    out = np.empty((h.k, max(h.m, 1)), dtype=np.int32)
+    ctx.check(_lib.load().kd_handle_arrays(ctx.ptr, h.ptr, ctypes.c_void_p(out.ctypes.data), 0))
+    return out[:, : h.m]
+
+
+def _alloc_tree(n: int, on_device: bool, device: int, children: bool):
+    cap = max(n, 1)
+    if on_device:
+        dev = torch.device("cuda", device)
+        node = torch.empty(cap, dtype=torch.int32, device=dev)
+        left = torch.empty(cap, dtype=torch.int32, device=dev) if children else None
+        right = torch.empty(cap, dtype=torch.int32, device=dev) if children else None
+        dim = torch.empty(cap, dtype=torch.uint8, device=dev) if children else None
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None  # noqa: E731
+    else:
+        node = np.empty(cap, dtype=np.int32)
+        left = np.empty(cap, dtype=np.int32) if children else None
+        right = np.empty(cap, dtype=np.int32) if children else None
+        dim = np.empty(cap, dtype=np.uint8) if children else None
+        ptr = lambda a: ctypes.c_void_p(a.ctypes.data) if a is not None else None  # noqa: E731
+    tree = KdTree(0, -1, ptr(node), ptr(left), ptr(right), ptr(dim), int(on_device))
+    return tree, {"node_tuple": node, "left": left, "right": right, "dim": dim}
+
+
+def _result(tree: KdTree, arrays: dict) -> dict:
+    m = tree.m
+    out = {"m": m, "root": tree.root}
+    for key, a in arrays.items():
+        if a is not None:
+            out[key] = a[:m]
+    return out
+
+
+def kd_build(ctx: Context, h: Handle, children: bool = True, on_device: bool | None = None) -> dict:
+    """kd_build: consumes the handle.  Outputs live on the device if the
+    input did (unless ``on_device`` says otherwise)."""
+    dev = h.on_device if on_device is None else on_device
+    tree, arrays = _alloc_tree(h.n, dev, ctx.device, children)
+    ctx.check(_lib.load().kd_build(ctx.ptr, h.ptr, ctypes.byref(tree)))
+    h.ptr = ctypes.c_void_p(0)
+    return _result(tree, arrays)
+
+
+def kd_release(ctx: Context, h: Handle) -> None:
+    if h.ptr:
+        ctx.check(_lib.load().kd_release(ctx.ptr, h.ptr))
+        h.ptr = ctypes.c_void_p(0)
+
+
+def build_tree(ctx: Context, coords, children: bool = True, on_device: bool | None = None) -> dict:
+    """kd_presort followed by kd_build."""
+    return kd_build(ctx, kd_presort(ctx, coords), children=children, on_device=on_device)
+
+
+def kd_build_batch(ctx: Context, clouds: list, children: bool = True, on_device: bool | None = None) -> list:
+    """kd_build_batch over a list of clouds (same k and dtype)."""
+    cs, keep = [], []
+    for c in clouds:
+        s, kk = _cloud(c)
+        cs.append(s)
+        keep.append(kk)
+    arr_c = (KdCloud * len(cs))(*cs)
+    trees, arrays = [], []
+    for s in cs:
+        dev = bool(s.on_device) if on_device is None else on_device
+        t, a = _alloc_tree(s.n, dev, ctx.device, children)
+        trees.append(t)
+        arrays.append(a)
+    arr_t = (KdTree * len(trees))(*trees)
+    ctx.check(_lib.load().kd_build_batch(ctx.ptr, arr_c, len(cs), arr_t))
+    del keep
+    return [_result(arr_t[i], arrays[i]) for i in range(len(cs))]
+
+
+class Ticket:
+    def __init__(self, value: int, tree: KdTree, arrays: dict, keep):
+        self.value = value
+        self.tree = tree
+        self.arrays = arrays
+        self.keep = keep
+
+
+def kd_submit(ctx: Context, coords, children: bool = True) -> Ticket:
+    """kd_submit: enqueue a serving request (host outputs)."""
+    c, keep = _cloud(coords)
+    tree, arrays = _alloc_tree(c.n, False, ctx.device, children)
+    t = ctypes.c_int64()
+    ctx.check(_lib.load().kd_submit(ctx.ptr, ctypes.byref(c), ctypes.byref(tree), ctypes.byref(t)))
+    return Ticket(t.value, tree, arrays, keep)
+
+
+def kd_wait(ctx: Context, ticket: Ticket, timeout_ms: int = -1) -> dict:
+    ctx.check(_lib.load().kd_wait(ctx.ptr, ticket.value, timeout_ms))
+    return _result(ticket.tree, ticket.arrays)
+
+
+def kd_serving_stats(ctx: Context) -> dict:
+    n = ctypes.c_int64()
+    p50, p99 = ctypes.c_double(), ctypes.c_double()
+    ctx.check(_lib.load().kd_serving_stats(ctx.ptr, ctypes.byref(n), ctypes.byref(p50), ctypes.byref(p99)))
+    return {"completed": n.value, "p50_us": p50.value, "p99_us": p99.value}
+
+
+def kd_launch_count(ctx: Context) -> int:
+    return int(_lib.load().kd_launch_count(ctx.ptr))
+
+
+def kd_kernel_stats(ctx: Context) -> dict:
+    """Per kernel family: device ms, launches, elements processed and
+    algorithmic bytes moved (collected when the context was created with
+    debug & 2)."""
+    out = {}
+    for f, name in enumerate(_lib.FAMILIES):
+        ms, n, u, b = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+        ctx.check(_lib.load().kd_kernel_stats(ctx.ptr, f, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(u),
+                                              ctypes.byref(b)))
+        out[name] = {"ms": ms.value, "launches": n.value, "units": u.value, "bytes": b.value}
+    return out
+
+
+def kd_kernel_stats_reset(ctx: Context) -> None:
+    ctx.check(_lib.load().kd_kernel_stats_reset(ctx.ptr))
+
+
+def kd_destroy(ctx: Context) -> None:
+    ctx.close()

@@ -1,0 +1,1036 @@
+// kd_api.cu -- host side of the C ABI declared in include/kdtree.h.
+//
+// Orders the presort and build kernels of one cloud or a batch of clouds on
+// the context's stream, owns device workspace (a private stream-ordered
+// memory pool with an optional byte budget), and runs the serving
+// scheduler.  No arithmetic of the method happens here: every step of the
+// path is a kernel in kd_presort.cu / kd_build.cu.
+#include <algorithm>
+#include <array>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "kd_internal.cuh"
+#include "kdtree.h"
+
+namespace kd {
+cudaError_t launch_transform(int dtype, const void* coords, int64_t n, int k, void* keys, int64_t stride,
+                             const int64_t* cloud_start, int ncloud, uint32_t* cloud_plane, int cloud_digits,
+                             uint32_t* hist, int* err, cudaStream_t s);
+int sort_tile();
+cudaError_t launch_sort_pass(int key64, int mode, const int64_t* count_ptr, int64_t max_count,
+                             const void* key_src, const uint32_t* gidx, void* key_dst, const PayloadArgs& pay,
+                             const uint32_t* hist_row, int shift, uint32_t* status, uint32_t* tile_ctr, int* err,
+                             cudaStream_t s);
+cudaError_t launch_dedup(int key64, int64_t n, const void* key0, const uint32_t* ids, const void* keys,
+                         int64_t stride, int k, const uint32_t* cloud_plane, int cloud_digits, uint32_t* ids_out,
+                         uint32_t* status, uint32_t* tile_ctr, int64_t* m_out, uint32_t* hist, int32_t* mcloud,
+                         int* err, cudaStream_t s);
+cudaError_t launch_records(const int64_t* m_ptr, int64_t max_m, int k, const AllPlanes& rec, uint32_t present_bits,
+                           cudaStream_t s);
+cudaError_t launch_arrays_out(const int64_t* m_ptr, int64_t max_m, int k, const AllPlanes& rec,
+                              const uint32_t* perm0, int32_t* out, cudaStream_t s);
+int level_tile(int k);
+int level_status_stride(int k);
+cudaError_t launch_level_pass(int k, const AllBufs& bufs, int q, const LevelTile* tiles, int ntiles,
+                              const CloudDev* clouds, uint32_t* medr, const uint32_t* perm0, uint32_t* status,
+                              uint32_t* tile_ctr, int* err, cudaStream_t s);
+size_t finish_smem(int k, int smax);
+cudaError_t launch_finish(const AllBufs& bufs, int k, const FinUnit* units, int nunits, const CloudDev* clouds,
+                          const uint32_t* perm0, int smax, int* err, cudaStream_t s);
+cudaError_t launch_top_nodes(const CloudDev* clouds, const int64_t* prefix, int ncloud, int64_t total, int k,
+                             const uint32_t* perm0, uint32_t* medr, int all_nodes, cudaStream_t s);
+}  // namespace kd
+
+using namespace kd;
+
+namespace {
+
+enum Family { F_TRANSFORM = 0, F_SORT, F_DEDUP, F_RECORDS, F_LEVEL, F_FINISH, F_TOP, F_OTHER, F_COUNT };
+
+struct TimedLaunch {
+    int family;
+    cudaEvent_t a, b;
+    double units;
+    int64_t* units_dev;  // if set, units = *units_dev read after completion
+    double bytes_per_unit;  // algorithmic bytes per element of this launch
+};
+
+struct Request;
+
+}  // namespace
+
+struct kd_presorted {
+    int k = 0, dtype = 0, count = 0;
+    int64_t N = 0, M = 0;
+    std::vector<int64_t> n_c, in_off, m_c, m_off;
+    uint32_t* perm0 = nullptr;
+    AllPlanes rec{};
+    void* rec_block = nullptr;
+    int64_t* d_m = nullptr;
+    size_t bytes = 0;
+};
+
+struct kd_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaMemPool_t pool = nullptr;
+    size_t budget = 0;
+    size_t in_use = 0;
+    int debug = 0;
+    int smax_override = 0;
+    std::string last_error;
+    std::recursive_mutex mu;
+    std::unordered_map<void*, size_t> sizes;
+    std::atomic<int64_t> launches{0};
+    // kernel timing (debug bit 2)
+    std::vector<TimedLaunch> timed;
+    std::vector<cudaEvent_t> event_pool;
+    double fam_ms[F_COUNT] = {0};
+    double fam_units[F_COUNT] = {0};
+    double fam_bytes[F_COUNT] = {0};
+    int64_t fam_launches[F_COUNT] = {0};
+    // pinned host scratch for small uploads
+    void* pinned = nullptr;
+    size_t pinned_bytes = 0;
+    // serving
+    std::thread server;
+    std::mutex qmu;
+    std::condition_variable qcv, donecv;
+    std::deque<std::shared_ptr<Request>> queue;
+    std::unordered_map<kd_ticket, std::shared_ptr<Request>> tickets;
+    bool stopping = false;
+    bool server_started = false;
+    kd_ticket next_ticket = 1;
+    std::vector<double> latencies_us;
+    int64_t completed = 0;
+    size_t serve_in_flight_bytes = 0;
+};
+
+namespace {
+
+struct Request {
+    kd_cloud cloud{};
+    std::vector<unsigned char> coords;  // host copy
+    kd_tree out{};
+    kd_status status = KD_OK;
+    bool done = false;
+    std::chrono::steady_clock::time_point t_submit, t_done;
+    size_t est_bytes = 0;
+};
+
+kd_status fail(kd_ctx* ctx, kd_status code, const std::string& msg) {
+    if (ctx) ctx->last_error = msg;
+    return code;
+}
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t _e = (call);                                                                   \
+        if (_e != cudaSuccess)                                                                     \
+            return fail(ctx, KD_EDEVICE, std::string(#call) + ": " + cudaGetErrorString(_e));      \
+    } while (0)
+
+#define CKS(expr)                                                                                  \
+    do {                                                                                           \
+        kd_status _s = (expr);                                                                     \
+        if (_s != KD_OK) return _s;                                                                \
+    } while (0)
+
+kd_status dev_alloc(kd_ctx* ctx, void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) return KD_OK;
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (ctx->budget && ctx->in_use + bytes > ctx->budget)
+        return fail(ctx, KD_ENOMEM, "device memory budget exceeded (" + std::to_string(ctx->in_use + bytes) +
+                                        " > " + std::to_string(ctx->budget) + " bytes)");
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes, ctx->pool, ctx->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(ctx, KD_ENOMEM, std::string("device allocation failed: ") + cudaGetErrorString(e));
+    }
+    ctx->in_use += bytes;
+    ctx->sizes[*p] = bytes;
+    return KD_OK;
+}
+
+void dev_free(kd_ctx* ctx, void* p) {
+    if (!p) return;
+    auto it = ctx->sizes.find(p);
+    if (it != ctx->sizes.end()) {
+        ctx->in_use -= it->second;
+        ctx->sizes.erase(it);
+    }
+    cudaFreeAsync(p, ctx->stream);
+}
+
+// Frees its allocations when it goes out of scope (temporaries of a call).
+struct Scratch {
+    kd_ctx* ctx;
+    std::vector<void*> ptrs;
+    explicit Scratch(kd_ctx* c) : ctx(c) {}
+    ~Scratch() {
+        for (void* p : ptrs) dev_free(ctx, p);
+    }
+    template <typename T>
+    kd_status get(T** out, size_t bytes) {
+        void* p = nullptr;
+        kd_status s = dev_alloc(ctx, &p, bytes);
+        if (s != KD_OK) return s;
+        ptrs.push_back(p);
+        *out = static_cast<T*>(p);
+        return KD_OK;
+    }
+};
+
+cudaEvent_t take_event(kd_ctx* ctx) {
+    if (!ctx->event_pool.empty()) {
+        cudaEvent_t e = ctx->event_pool.back();
+        ctx->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Launch bookkeeping: count, and (timing mode) events around the launch.
+struct LaunchTimer {
+    kd_ctx* ctx;
+    int fam;
+    double units;
+    int64_t* units_dev;
+    double bpu;
+    cudaEvent_t a = nullptr;
+    LaunchTimer(kd_ctx* c, int f, double u, int64_t* ud = nullptr, double bytes_per_unit = 0)
+        : ctx(c), fam(f), units(u), units_dev(ud), bpu(bytes_per_unit) {
+        ctx->launches++;
+        if (ctx->debug & 2) {
+            a = take_event(ctx);
+            cudaEventRecord(a, ctx->stream);
+        }
+    }
+    ~LaunchTimer() {
+        if (a) {
+            cudaEvent_t b = take_event(ctx);
+            cudaEventRecord(b, ctx->stream);
+            ctx->timed.push_back(TimedLaunch{fam, a, b, units, units_dev, bpu});
+        }
+    }
+};
+
+void collect_timing(kd_ctx* ctx) {
+    if (ctx->timed.empty()) return;
+    cudaStreamSynchronize(ctx->stream);
+    for (auto& t : ctx->timed) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, t.a, t.b);
+        double u = t.units;
+        if (t.units_dev) {
+            int64_t v = 0;
+            cudaMemcpy(&v, t.units_dev, sizeof(v), cudaMemcpyDeviceToHost);
+            u = (double)v;
+        }
+        ctx->fam_ms[t.family] += ms;
+        ctx->fam_units[t.family] += u;
+        ctx->fam_bytes[t.family] += u * t.bytes_per_unit;
+        ctx->fam_launches[t.family] += 1;
+        ctx->event_pool.push_back(t.a);
+        ctx->event_pool.push_back(t.b);
+    }
+    ctx->timed.clear();
+}
+
+kd_status check_device_err(kd_ctx* ctx, int* d_err) {
+    int err = 0;
+    CK(cudaMemcpyAsync(&err, d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (err & ERR_NAN) return fail(ctx, KD_ENAN, "a float coordinate is NaN");
+    if (err & ERR_TIMEOUT) return fail(ctx, KD_ETIMEOUT, "a device look-back wait exceeded its bound");
+    if (err & ERR_INTERNAL) return fail(ctx, KD_EDEVICE, "internal consistency check failed on the device");
+    return KD_OK;
+}
+
+size_t dtype_size(int dtype) { return dtype == KD_I64 ? 8 : 4; }
+
+kd_status validate_cloud(kd_ctx* ctx, const kd_cloud* c) {
+    if (!c) return fail(ctx, KD_EINVAL, "cloud is NULL");
+    if (c->k < 1 || c->k > KD_MAX_K) return fail(ctx, KD_EINVAL, "k must be in [1, 8]");
+    if (c->dtype != KD_I32 && c->dtype != KD_I64 && c->dtype != KD_F32)
+        return fail(ctx, KD_EINVAL, "unknown dtype");
+    if (c->n < 0 || c->n > KD_MAX_N) return fail(ctx, KD_EINVAL, "n out of range [0, 2^30 - 1]");
+    if (c->n > 0 && !c->coords) return fail(ctx, KD_EINVAL, "coords is NULL");
+    return KD_OK;
+}
+
+int bytes_for(int64_t v) {
+    int b = 0;
+    while (v > 0) {
+        ++b;
+        v >>= 8;
+    }
+    return b;
+}
+
+// ------------------------------------------------------------ presort
+struct Pass {
+    int plane;  // coordinate index, or -1 for the cloud-id plane
+    int digit;
+    int mode;
+    int w;      // key word bytes of the plane
+};
+
+// Algorithmic bytes per element of one sort pass: the key word read (and
+// written unless the next pass gathers a new plane), each payload word read
+// and written (an iota plane is only written), plus the tuple id read for
+// a gather.
+double pass_bytes(const Pass& P, bool writes_key, int npay) {
+    return (double)P.w * (writes_key ? 2 : 1) + 8.0 * npay + (P.mode == KEY_GATHER ? 4.0 : 0.0);
+}
+
+kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_presorted** out) {
+    *out = nullptr;
+    if (count < 1 || !clouds) return fail(ctx, KD_EINVAL, "no clouds");
+    for (int i = 0; i < count; ++i) CKS(validate_cloud(ctx, &clouds[i]));
+    const int k = clouds[0].k, dtype = clouds[0].dtype;
+    for (int i = 1; i < count; ++i)
+        if (clouds[i].k != k || clouds[i].dtype != dtype)
+            return fail(ctx, KD_EINVAL, "all clouds of a batch must share k and dtype");
+    std::unique_ptr<kd_presorted> H(new kd_presorted());
+    H->k = k;
+    H->dtype = dtype;
+    H->count = count;
+    H->n_c.resize(count);
+    H->in_off.resize(count + 1);
+    int64_t N = 0;
+    for (int i = 0; i < count; ++i) {
+        H->n_c[i] = clouds[i].n;
+        H->in_off[i] = N;
+        N += clouds[i].n;
+    }
+    H->in_off[count] = N;
+    if (N > KD_MAX_N) return fail(ctx, KD_EINVAL, "total tuples of the batch exceed 2^30 - 1");
+    H->N = N;
+    const int key64 = dtype == KD_I64;
+    const int w = key64 ? 8 : 4;
+    const int D = w;
+    const int cloud_digits = count > 1 ? std::max(1, bytes_for(count - 1)) : 0;
+    const int nrows = k * D + cloud_digits;
+    const size_t tsz = dtype_size(dtype);
+    cudaStream_t s = ctx->stream;
+
+    // persistent (handle-owned) allocations
+    void* p = nullptr;
+    CKS(dev_alloc(ctx, &p, sizeof(int64_t)));
+    H->d_m = (int64_t*)p;
+    CK(cudaMemsetAsync(H->d_m, 0, sizeof(int64_t), s));
+    H->M = 0;
+    H->m_c.assign(count, 0);
+    H->m_off.assign(count + 1, 0);
+    if (N == 0) {
+        *out = H.release();
+        return KD_OK;
+    }
+    CKS(dev_alloc(ctx, &p, (size_t)N * 4));
+    H->perm0 = (uint32_t*)p;
+    const size_t rec_planes = k >= 2 ? (size_t)k * k : 0;
+    if (rec_planes) {
+        kd_status st = dev_alloc(ctx, &H->rec_block, rec_planes * N * 4);
+        if (st != KD_OK) {
+            dev_free(ctx, H->perm0);
+            dev_free(ctx, H->d_m);
+            return st;
+        }
+        for (int d = 0; d < k; ++d)
+            for (int q = 0; q < k; ++q) H->rec.p[d][q] = (uint32_t*)H->rec_block + ((size_t)d * k + q) * N;
+    }
+    H->bytes = (size_t)N * 4 + rec_planes * N * 4;
+    struct Guard {
+        kd_ctx* c;
+        kd_presorted* h;
+        bool armed = true;
+        ~Guard() {
+            if (armed && h) {
+                dev_free(c, h->perm0);
+                dev_free(c, h->rec_block);
+                dev_free(c, h->d_m);
+            }
+        }
+    } guard{ctx, H.get()};
+
+    Scratch S(ctx);
+    // coordinates on the device, clouds back to back
+    const void* coords = nullptr;
+    if (count == 1 && clouds[0].on_device) {
+        coords = clouds[0].coords;
+    } else {
+        unsigned char* cb = nullptr;
+        CKS(S.get(&cb, (size_t)N * k * tsz));
+        for (int i = 0; i < count; ++i)
+            if (clouds[i].n)
+                CK(cudaMemcpyAsync(cb + (size_t)H->in_off[i] * k * tsz, clouds[i].coords,
+                                   (size_t)clouds[i].n * k * tsz,
+                                   clouds[i].on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+        coords = cb;
+    }
+    unsigned char* keys = nullptr;
+    uint32_t *cloud_plane = nullptr, *hist = nullptr;
+    int64_t *cstart = nullptr, *d_n = nullptr;
+    int32_t* mcloud = nullptr;
+    int* d_err = nullptr;
+    CKS(S.get(&keys, (size_t)k * N * w));
+    if (count > 1) {
+        CKS(S.get(&cloud_plane, (size_t)N * 4));
+        CKS(S.get(&cstart, (size_t)(count + 1) * 8));
+    }
+    CKS(S.get(&hist, (size_t)nrows * RADIX * 4));
+    CKS(S.get(&d_n, 8));
+    CKS(S.get(&mcloud, (size_t)count * 4));
+    CKS(S.get(&d_err, 4));
+    CK(cudaMemsetAsync(hist, 0, (size_t)nrows * RADIX * 4, s));
+    CK(cudaMemsetAsync(d_err, 0, 4, s));
+    std::vector<int32_t> nc32(count);
+    for (int i = 0; i < count; ++i) nc32[i] = (int32_t)H->n_c[i];
+    CK(cudaMemcpyAsync(d_n, &N, 8, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(mcloud, nc32.data(), (size_t)count * 4, cudaMemcpyHostToDevice, s));
+    if (count > 1)
+        CK(cudaMemcpyAsync(cstart, H->in_off.data(), (size_t)(count + 1) * 8, cudaMemcpyHostToDevice, s));
+    {
+        LaunchTimer lt(ctx, F_TRANSFORM, (double)N, nullptr, (double)k * (tsz + w) + (count > 1 ? 4 : 0));
+        CK(launch_transform(dtype, coords, N, k, keys, N, cstart, count, cloud_plane, cloud_digits, hist, d_err, s));
+    }
+    std::vector<uint32_t> h_hist((size_t)nrows * RADIX);
+    CK(cudaMemcpyAsync(h_hist.data(), hist, h_hist.size() * 4, cudaMemcpyDeviceToHost, s));
+    CKS(check_device_err(ctx, d_err));  // synchronises
+    auto trivial = [&](int row) {
+        int nz = 0;
+        for (int b = 0; b < RADIX; ++b) nz += h_hist[(size_t)row * RADIX + b] != 0;
+        return nz <= 1;
+    };
+    auto row_of = [&](int plane, int digit) { return plane >= 0 ? plane * D + digit : k * D + digit; };
+
+    // pass lists ------------------------------------------------------
+    // a sort = its passes; the first pass of each plane always runs
+    auto plane_passes = [&](std::vector<Pass>& v, int plane, int ndig, bool first_of_sort_direct) {
+        for (int b = 0; b < ndig; ++b) {
+            if (b > 0 && trivial(row_of(plane, b))) continue;
+            int mode = b == 0 ? (first_of_sort_direct ? KEY_DIRECT : KEY_GATHER) : KEY_BUF;
+            v.push_back(Pass{plane, b, mode, plane >= 0 ? w : 4});
+        }
+    };
+    std::vector<Pass> s0;
+    for (int c = k - 1; c >= 0; --c) plane_passes(s0, c, D, c == k - 1);
+    std::vector<std::vector<Pass>> chain;  // chain[i] sorts array d = k-1-i
+    for (int d = k - 1; d >= 1; --d) {
+        std::vector<Pass> v;
+        plane_passes(v, d, D, false);
+        if (count > 1) plane_passes(v, -1, cloud_digits, false);
+        chain.push_back(v);
+    }
+    std::vector<Pass> cloud_sort;
+    if (count > 1) plane_passes(cloud_sort, -1, cloud_digits, false);
+
+    // buffers
+    const int64_t tiles = (N + sort_tile() - 1) / sort_tile();
+    size_t npasses = s0.size() + cloud_sort.size();
+    for (auto& v : chain) npasses += v.size();
+    uint32_t *status = nullptr, *ctrs = nullptr;
+    const size_t status_words_per = (size_t)tiles * RADIX;
+    CKS(S.get(&status, (npasses * status_words_per + (size_t)tiles) * 4));
+    CKS(S.get(&ctrs, (npasses + 1) * 4));
+    CK(cudaMemsetAsync(status, 0, (npasses * status_words_per + (size_t)tiles) * 4, s));
+    CK(cudaMemsetAsync(ctrs, 0, (npasses + 1) * 4, s));
+    unsigned char* kbuf[2];
+    uint32_t* ibuf[2];
+    const int maxpay = k + 1;
+    uint32_t* pbuf[2][MAXPAY];
+    CKS(S.get(&kbuf[0], (size_t)N * w));
+    CKS(S.get(&kbuf[1], (size_t)N * w));
+    CKS(S.get(&ibuf[0], (size_t)N * 4));
+    CKS(S.get(&ibuf[1], (size_t)N * 4));
+    if (k >= 2)
+        for (int b = 0; b < 2; ++b)
+            for (int j = 0; j < maxpay; ++j) CKS(S.get(&pbuf[b][j], (size_t)N * 4));
+    size_t pass_no = 0;
+    auto plane_ptr = [&](int plane) -> const void* {
+        return plane >= 0 ? (const void*)(keys + (size_t)plane * N * w) : (const void*)cloud_plane;
+    };
+    auto plane64 = [&](int plane) { return plane >= 0 ? key64 : 0; };
+
+    // S_0: ids by super key 0 (all n tuples) ----------------------------
+    int kc = 0, ic = 0;  // current key / id buffer
+    for (size_t i = 0; i < s0.size(); ++i) {
+        const Pass& P = s0[i];
+        const bool last = i + 1 == s0.size();
+        const bool next_gathers = !last && s0[i + 1].mode != KEY_BUF;
+        PayloadArgs pay{};
+        pay.n = 1;
+        pay.src[0] = P.mode == KEY_DIRECT ? nullptr : ibuf[ic];
+        pay.dst[0] = ibuf[ic ^ 1];
+        const void* ksrc = P.mode == KEY_BUF ? (const void*)kbuf[kc] : plane_ptr(P.plane);
+        void* kdst = next_gathers ? nullptr : (void*)kbuf[kc ^ 1];
+        LaunchTimer lt(ctx, F_SORT, (double)N, nullptr, pass_bytes(P, kdst != nullptr, pay.n));
+        CK(launch_sort_pass(plane64(P.plane), P.mode, d_n, N, ksrc, ibuf[ic], kdst, pay,
+                            hist + (size_t)row_of(P.plane, P.digit) * RADIX, 8 * P.digit,
+                            status + pass_no * status_words_per, ctrs + pass_no, d_err, s));
+        ++pass_no;
+        kc ^= 1;
+        ic ^= 1;
+    }
+    // dedup ---------------------------------------------------------------
+    uint32_t* dedup_out = count == 1 ? H->perm0 : ibuf[ic ^ 1];
+    {
+        LaunchTimer lt(ctx, F_DEDUP, (double)N, nullptr, 2.0 * w + 8);
+        CK(launch_dedup(key64, N, kbuf[kc], ibuf[ic], keys, N, k, cloud_plane, cloud_digits, dedup_out,
+                        status + npasses * status_words_per, ctrs + npasses, H->d_m, hist, mcloud, d_err, s));
+    }
+    ic ^= 1;
+    // cloud grouping of array 0 (batches) ----------------------------------
+    for (size_t i = 0; i < cloud_sort.size(); ++i) {
+        const Pass& P = cloud_sort[i];
+        const bool last = i + 1 == cloud_sort.size();
+        PayloadArgs pay{};
+        pay.n = 1;
+        pay.src[0] = ibuf[ic];
+        pay.dst[0] = last ? H->perm0 : ibuf[ic ^ 1];
+        const void* ksrc = P.mode == KEY_BUF ? (const void*)kbuf[kc] : plane_ptr(-1);
+        LaunchTimer lt(ctx, F_SORT, 0.0, H->d_m, pass_bytes(P, !last, 1));
+        CK(launch_sort_pass(0, P.mode, H->d_m, N, ksrc, ibuf[ic], last ? nullptr : (void*)kbuf[kc ^ 1], pay,
+                            hist + (size_t)row_of(-1, P.digit) * RADIX, 8 * P.digit,
+                            status + pass_no * status_words_per, ctrs + pass_no, d_err, s));
+        ++pass_no;
+        kc ^= 1;
+        ic ^= 1;
+    }
+    // chain: array d = stable sort of array d+1 by x_d (then cloud) --------
+    // payload plane list: [id (while a later gather needs it)], R_0, R_{k-1}, ..., R_{d+1}
+    if (k >= 2) {
+        const uint32_t* id_src = H->perm0;  // array 0 order
+        int gathers_left = 0;
+        for (auto& v : chain)
+            for (auto& P : v) gathers_left += P.mode == KEY_GATHER;
+        std::vector<int> ranks_prev;  // rank planes carried by the previous array (R index list)
+        for (size_t ci = 0; ci < chain.size(); ++ci) {
+            const int d = k - 1 - (int)ci;
+            const auto& v = chain[ci];
+            // current sources of payload planes
+            std::vector<int> ranks = ranks_prev;
+            ranks.push_back((d + 1) % k);  // new plane: R_{d+1} = source position
+            // source pointers for the first pass: from rec[d+1][r] or iota
+            std::vector<const uint32_t*> rsrc(ranks.size());
+            for (size_t j = 0; j < ranks.size(); ++j)
+                rsrc[j] = (j + 1 == ranks.size()) ? nullptr : H->rec.p[(d + 1) % k][ranks[j]];
+            const uint32_t* cur_id = id_src;
+            int pb = 0;  // payload ping-pong
+            for (size_t i = 0; i < v.size(); ++i) {
+                const Pass& P = v[i];
+                const bool last = i + 1 == v.size();
+                if (P.mode == KEY_GATHER) --gathers_left;
+                const bool carry_id = gathers_left > 0;
+                const bool next_gathers = !last && v[i + 1].mode != KEY_BUF;
+                PayloadArgs pay{};
+                int np = 0;
+                uint32_t* new_id = nullptr;
+                if (carry_id) {
+                    pay.src[np] = cur_id;
+                    new_id = (cur_id == ibuf[0]) ? ibuf[1] : ibuf[0];
+                    pay.dst[np] = new_id;
+                    ++np;
+                }
+                for (size_t j = 0; j < ranks.size(); ++j) {
+                    pay.src[np] = rsrc[j];
+                    pay.dst[np] = last ? H->rec.p[d][ranks[j]] : pbuf[pb][j];
+                    ++np;
+                }
+                pay.n = np;
+                const void* ksrc = P.mode == KEY_BUF ? (const void*)kbuf[kc] : plane_ptr(P.plane);
+                void* kdst = (last || next_gathers) ? nullptr : (void*)kbuf[kc ^ 1];
+                LaunchTimer lt(ctx, F_SORT, 0.0, H->d_m, pass_bytes(P, kdst != nullptr, pay.n));
+                CK(launch_sort_pass(plane64(P.plane), P.mode, H->d_m, N, ksrc, cur_id, kdst, pay,
+                                    hist + (size_t)row_of(P.plane, P.digit) * RADIX, 8 * P.digit,
+                                    status + pass_no * status_words_per, ctrs + pass_no, d_err, s));
+                ++pass_no;
+                kc ^= 1;
+                if (carry_id) cur_id = new_id;
+                for (size_t j = 0; j < ranks.size(); ++j) rsrc[j] = last ? H->rec.p[d][ranks[j]] : pbuf[pb][j];
+                pb ^= 1;
+            }
+            id_src = cur_id;
+            ranks_prev = ranks;
+        }
+        // remaining planes of every array
+        uint32_t present = 0;
+        for (int d = 1; d < k; ++d) {
+            uint32_t bits = 1u;  // R_0
+            for (int q = d + 1; q < k; ++q) bits |= 1u << q;
+            present |= bits << (d * MAXK);
+        }
+        int scat = 0, own = 0, readp = k - 1;
+        for (int d = 0; d < k; ++d) {
+            const uint32_t bits = (present >> (d * MAXK)) & 0xffu;
+            for (int q = 0; q < k; ++q)
+                if (!((bits >> q) & 1u)) {
+                    if (q == d) ++own; else if (d != 1) ++scat;
+                }
+        }
+        LaunchTimer lt(ctx, F_RECORDS, 0.0, H->d_m, 4.0 * (readp + own + scat));
+        CK(launch_records(H->d_m, N, k, H->rec, present, s));
+    }
+    // learn m ----------------------------------------------------------------
+    int64_t M = 0;
+    CK(cudaMemcpyAsync(&M, H->d_m, 8, cudaMemcpyDeviceToHost, s));
+    std::vector<int32_t> mc(count);
+    CK(cudaMemcpyAsync(mc.data(), mcloud, (size_t)count * 4, cudaMemcpyDeviceToHost, s));
+    CKS(check_device_err(ctx, d_err));
+    H->M = M;
+    int64_t acc = 0;
+    for (int i = 0; i < count; ++i) {
+        H->m_c[i] = mc[i];
+        H->m_off[i] = acc;
+        acc += mc[i];
+    }
+    H->m_off[count] = acc;
+    if (acc != M) return fail(ctx, KD_EDEVICE, "per-cloud counts do not add up to m");
+    if (ctx->debug & 1) CK(cudaStreamSynchronize(s));
+    guard.armed = false;
+    *out = H.release();
+    return KD_OK;
+}
+
+void release_handle(kd_ctx* ctx, kd_presorted* h) {
+    if (!h) return;
+    dev_free(ctx, h->perm0);
+    dev_free(ctx, h->rec_block);
+    dev_free(ctx, h->d_m);
+    delete h;
+}
+
+// ---------------------------------------------------------------- build
+int64_t max_seg(int64_t m, int L) {
+    for (int l = 0; l < L; ++l) m /= 2;
+    return m;
+}
+int nlevels(int64_t m) {
+    int L = 0;
+    while (((int64_t)1 << L) <= m) ++L;
+    return L;  // ceil(log2(m + 1))
+}
+
+kd_status build_batch(kd_ctx* ctx, kd_presorted* H, kd_tree* outs) {
+    const int k = H->k, count = H->count;
+    const int64_t M = H->M;
+    cudaStream_t s = ctx->stream;
+    for (int i = 0; i < count; ++i) {
+        if (!outs[i].node_tuple && H->m_c[i] > 0) return fail(ctx, KD_EINVAL, "node_tuple output is NULL");
+        outs[i].m = (int32_t)H->m_c[i];
+        outs[i].root = H->m_c[i] > 0 ? (int32_t)((H->m_c[i] - 1) / 2) : -1;
+    }
+    if (M == 0) return KD_OK;
+    Scratch S(ctx);
+    int* d_err = nullptr;
+    CKS(S.get(&d_err, 4));
+    CK(cudaMemsetAsync(d_err, 0, 4, s));
+    const int smax = ctx->smax_override ? ctx->smax_override : (k <= 4 ? 2048 : 1024);
+    if (k >= 2 && smax * 3 < level_tile(k) + 3) return fail(ctx, KD_EINVAL, "switch threshold too small");
+
+    // outputs: user device arrays, or staging for host arrays
+    bool any_host = false, want_l = false, want_r = false, want_d = false;
+    for (int i = 0; i < count; ++i) {
+        any_host |= !outs[i].on_device;
+        want_l |= outs[i].left != nullptr;
+        want_r |= outs[i].right != nullptr;
+        want_d |= outs[i].dim != nullptr;
+    }
+    int32_t *st_node = nullptr, *st_left = nullptr, *st_right = nullptr;
+    uint8_t* st_dim = nullptr;
+    if (any_host) {
+        CKS(S.get(&st_node, (size_t)M * 4));
+        if (want_l) CKS(S.get(&st_left, (size_t)M * 4));
+        if (want_r) CKS(S.get(&st_right, (size_t)M * 4));
+        if (want_d) CKS(S.get(&st_dim, (size_t)M));
+    }
+    std::vector<CloudDev> cd(count);
+    std::vector<int> lam(count);
+    int64_t medr_total = 0;
+    int maxlam = 0;
+    for (int i = 0; i < count; ++i) {
+        CloudDev& c = cd[i];
+        memset(&c, 0, sizeof(c));
+        c.off = H->m_off[i];
+        c.in_off = H->in_off[i];
+        c.m = (int32_t)H->m_c[i];
+        const int64_t m = H->m_c[i];
+        int L = 0;
+        if (k == 1) {
+            L = nlevels(m);
+        } else {
+            while (max_seg(m, L) > smax) ++L;
+        }
+        lam[i] = L;
+        c.lam = L;
+        c.medr_off = medr_total;
+        if (k >= 2 && L >= 1) medr_total += ((int64_t)1 << L) - 1;
+        maxlam = std::max(maxlam, L);
+        if (outs[i].on_device) {
+            c.node = outs[i].node_tuple;
+            c.left = outs[i].left;
+            c.right = outs[i].right;
+            c.dim = outs[i].dim;
+        } else {
+            c.node = st_node + c.off;
+            c.left = outs[i].left ? st_left + c.off : nullptr;
+            c.right = outs[i].right ? st_right + c.off : nullptr;
+            c.dim = outs[i].dim ? st_dim + c.off : nullptr;
+        }
+    }
+    uint32_t* medr = nullptr;
+    if (medr_total) CKS(S.get(&medr, (size_t)medr_total * 4));
+
+    // schedule of level passes -------------------------------------------
+    std::vector<std::vector<LevelTile>> step_tiles;
+    std::vector<int> step_q;
+    std::vector<std::array<int, MAXK>> moves(count), level(count);
+    for (int i = 0; i < count; ++i) {
+        moves[i].fill(0);
+        level[i].fill(0);
+    }
+    const int tile = level_tile(std::max(k, 2));
+    bool need_bufs = false;
+    if (k >= 2) {
+        int tmax = 0;
+        for (int i = 0; i < count; ++i)
+            if (lam[i] >= 1) tmax = std::max(tmax, lam[i] + k - 2);
+        for (int t = 1; t <= tmax; ++t) {
+            const int q = t % k;
+            std::vector<LevelTile> tl;
+            for (int i = 0; i < count; ++i) {
+                if (lam[i] < 1) continue;
+                const int cur = level[i][q];
+                int lin = cur;
+                if (cur % k == q && cur < lam[i]) lin = cur + 1;
+                const int lout = std::min(t, lam[i]);
+                if (lin >= lout) {
+                    level[i][q] = std::max(cur, std::min(lin, lam[i]));
+                    continue;
+                }
+                if (lout - lin > k - 1) return fail(ctx, KD_EDEVICE, "internal: level pass spans too many levels");
+                if (max_seg(H->m_c[i], lin) - 1 < (tile + 2) / 3)
+                    return fail(ctx, KD_EDEVICE, "internal: segments too small for a level-pass tile");
+                const int src = buf_after(moves[i][q]);
+                const int dst = buf_after(moves[i][q] + 1);
+                const int wm = (lout % k == q) && (lout < lam[i]);
+                for (int64_t p0 = 0; p0 < H->m_c[i]; p0 += tile) {
+                    LevelTile T{};
+                    T.cloud = i;
+                    T.lev_in = lin;
+                    T.lev_out = lout;
+                    T.src_buf = src;
+                    T.dst_buf = dst;
+                    T.write_med = wm;
+                    T.pos0 = p0;
+                    T.npos = (int32_t)std::min<int64_t>(tile, H->m_c[i] - p0);
+                    T.first = p0 == 0;
+                    tl.push_back(T);
+                }
+                moves[i][q] += 1;
+                level[i][q] = lout;
+                need_bufs = true;
+            }
+            if (!tl.empty()) {
+                step_tiles.push_back(std::move(tl));
+                step_q.push_back(q);
+            }
+        }
+        for (int i = 0; i < count; ++i) {
+            if (lam[i] < 1) continue;
+            for (int q = 0; q < k; ++q) {
+                int lv = level[i][q];
+                if (lv < lam[i] && lv % k == q && lv + 1 == lam[i]) lv = lam[i];
+                if (lv != lam[i]) return fail(ctx, KD_EDEVICE, "internal: schedule did not reach the finisher level");
+            }
+        }
+    }
+    for (int i = 0; i < count; ++i)
+        for (int q = 0; q < k && q < MAXK; ++q) cd[i].buf[q] = (uint8_t)buf_after(moves[i][q]);
+
+    AllBufs bufs{};
+    for (int d = 0; d < k && k >= 2; ++d)
+        for (int p = 0; p < k; ++p) bufs.p[d][0][p] = H->rec.p[d][p];
+    if (need_bufs) {
+        uint32_t* blk = nullptr;
+        CKS(S.get(&blk, (size_t)2 * k * k * M * 4));
+        for (int b = 1; b <= 2; ++b)
+            for (int d = 0; d < k; ++d)
+                for (int p = 0; p < k; ++p) bufs.p[d][b][p] = blk + (((size_t)(b - 1) * k + d) * k + p) * M;
+    }
+
+    // upload tables -------------------------------------------------------
+    std::vector<int64_t> top_prefix(count + 1, 0);
+    for (int i = 0; i < count; ++i) {
+        int64_t e = 0;
+        if (cd[i].m > 0 && (k == 1 || lam[i] >= 1)) e = ((int64_t)1 << lam[i]) - 1;
+        top_prefix[i + 1] = top_prefix[i] + e;
+    }
+    std::vector<FinUnit> units;
+    if (k >= 2)
+        for (int i = 0; i < count; ++i) {
+            if (cd[i].m == 0) continue;
+            const int64_t nu = (int64_t)1 << lam[i];
+            for (int64_t u = 0; u < nu; ++u) units.push_back(FinUnit{i, (int32_t)u});
+        }
+    size_t ntiles_all = 0;
+    for (auto& v : step_tiles) ntiles_all += v.size();
+    CloudDev* d_cd = nullptr;
+    int64_t* d_prefix = nullptr;
+    FinUnit* d_units = nullptr;
+    LevelTile* d_tiles = nullptr;
+    uint32_t *d_status = nullptr, *d_ctr = nullptr;
+    CKS(S.get(&d_cd, sizeof(CloudDev) * count));
+    CKS(S.get(&d_prefix, sizeof(int64_t) * (count + 1)));
+    CK(cudaMemcpyAsync(d_cd, cd.data(), sizeof(CloudDev) * count, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d_prefix, top_prefix.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s));
+    if (!units.empty()) {
+        CKS(S.get(&d_units, sizeof(FinUnit) * units.size()));
+        CK(cudaMemcpyAsync(d_units, units.data(), sizeof(FinUnit) * units.size(), cudaMemcpyHostToDevice, s));
+    }
+    std::vector<LevelTile> flat;
+    flat.reserve(ntiles_all);
+    for (auto& v : step_tiles) flat.insert(flat.end(), v.begin(), v.end());
+    const int stride = k >= 2 ? level_status_stride(k) : 1;
+    if (!flat.empty()) {
+        CKS(S.get(&d_tiles, sizeof(LevelTile) * flat.size()));
+        CK(cudaMemcpyAsync(d_tiles, flat.data(), sizeof(LevelTile) * flat.size(), cudaMemcpyHostToDevice, s));
+        CKS(S.get(&d_status, flat.size() * stride * 4));
+        CKS(S.get(&d_ctr, step_tiles.size() * 4));
+        CK(cudaMemsetAsync(d_status, 0, flat.size() * stride * 4, s));
+        CK(cudaMemsetAsync(d_ctr, 0, step_tiles.size() * 4, s));
+    }
+    // launches ----------------------------------------------------------------
+    {
+        LaunchTimer lt(ctx, F_TOP, (double)top_prefix[count], nullptr, 13.0);
+        CK(launch_top_nodes(d_cd, d_prefix, count, top_prefix[count], k, H->perm0, medr, k == 1, s));
+    }
+    size_t off = 0;
+    for (size_t st = 0; st < step_tiles.size(); ++st) {
+        const int nt = (int)step_tiles[st].size();
+        double units_el = 0;
+        for (auto& T : step_tiles[st]) units_el += T.npos;
+        LaunchTimer lt(ctx, F_LEVEL, units_el, nullptr, 8.0 * k);
+        CK(launch_level_pass(k, bufs, step_q[st], d_tiles + off, nt, d_cd, medr, H->perm0, d_status + off * stride,
+                             d_ctr + st, d_err, s));
+        off += nt;
+    }
+    if (!units.empty()) {
+        LaunchTimer lt(ctx, F_FINISH, (double)M, nullptr,
+                       4.0 * (2 * k - 1) + 8.0 + (want_l ? 4 : 0) + (want_r ? 4 : 0) + (want_d ? 1 : 0));
+        CK(launch_finish(bufs, k, d_units, (int)units.size(), d_cd, H->perm0, smax, d_err, s));
+    }
+    CKS(check_device_err(ctx, d_err));
+    if (any_host) {
+        for (int i = 0; i < count; ++i) {
+            if (outs[i].on_device || cd[i].m == 0) continue;
+            const size_t mi = (size_t)cd[i].m;
+            CK(cudaMemcpyAsync(outs[i].node_tuple, st_node + cd[i].off, mi * 4, cudaMemcpyDeviceToHost, s));
+            if (outs[i].left) CK(cudaMemcpyAsync(outs[i].left, st_left + cd[i].off, mi * 4, cudaMemcpyDeviceToHost, s));
+            if (outs[i].right)
+                CK(cudaMemcpyAsync(outs[i].right, st_right + cd[i].off, mi * 4, cudaMemcpyDeviceToHost, s));
+            if (outs[i].dim) CK(cudaMemcpyAsync(outs[i].dim, st_dim + cd[i].off, mi, cudaMemcpyDeviceToHost, s));
+        }
+        CK(cudaStreamSynchronize(s));
+    }
+    return KD_OK;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+kd_status kd_create(kd_ctx** out, const kd_config* cfg) {
+    if (!out) return KD_EINVAL;
+    *out = nullptr;
+    kd_config c{};
+    if (cfg) c = *cfg;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return KD_EDEVICE;
+    }
+    if (c.device < 0 || c.device >= ndev) return KD_EINVAL;
+    std::unique_ptr<kd_ctx> ctx(new kd_ctx());
+    ctx->device = c.device;
+    ctx->budget = c.mem_budget_bytes;
+    ctx->debug = c.debug;
+    ctx->smax_override = c.switch_threshold;
+    if (cudaSetDevice(c.device) != cudaSuccess) return KD_EDEVICE;
+    if (c.cuda_stream) {
+        ctx->stream = (cudaStream_t)c.cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) return KD_EDEVICE;
+        ctx->own_stream = true;
+    }
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = c.device;
+    if (cudaMemPoolCreate(&ctx->pool, &props) != cudaSuccess) return KD_EDEVICE;
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    *out = ctx.release();
+    return KD_OK;
+}
+
+kd_status kd_presort(kd_ctx* ctx, const kd_cloud* cloud, kd_handle* out) {
+    if (!ctx || !out) return KD_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    cudaSetDevice(ctx->device);
+    ctx->last_error.clear();
+    kd_status st = presort_batch(ctx, cloud, 1, out);
+    if (st == KD_OK && (ctx->debug & 2)) collect_timing(ctx);
+    return st;
+}
+
+kd_status kd_handle_info(kd_handle h, int64_t* n, int32_t* m, int* k) {
+    if (!h) return KD_EINVAL;
+    if (n) *n = h->N;
+    if (m) *m = (int32_t)h->M;
+    if (k) *k = h->k;
+    return KD_OK;
+}
+
+kd_status kd_handle_arrays(kd_ctx* ctx, kd_handle h, int32_t* out, int on_device) {
+    if (!ctx || !h || (!out && h->M > 0)) return KD_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    cudaSetDevice(ctx->device);
+    if (h->count != 1) return fail(ctx, KD_EINVAL, "index arrays are available for single-cloud handles only");
+    if (h->M == 0) return KD_OK;
+    const size_t bytes = (size_t)h->M * h->k * 4;
+    Scratch S(ctx);
+    int32_t* dst = out;
+    if (!on_device) CKS(S.get(&dst, bytes));
+    if (h->k == 1) {
+        CK(cudaMemcpyAsync(dst, h->perm0, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    } else {
+        LaunchTimer lt(ctx, F_OTHER, (double)h->M);
+        CK(launch_arrays_out(h->d_m, h->M, h->k, h->rec, h->perm0, dst, ctx->stream));
+    }
+    if (!on_device) CK(cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return KD_OK;
+}
+
+kd_status kd_build(kd_ctx* ctx, kd_handle h, kd_tree* out) {
+    if (!ctx || !h) return KD_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    cudaSetDevice(ctx->device);
+    ctx->last_error.clear();
+    kd_status st = out ? build_batch(ctx, h, out) : fail(ctx, KD_EINVAL, "tree output is NULL");
+    release_handle(ctx, h);
+    if (st == KD_OK && (ctx->debug & 2)) collect_timing(ctx);
+    return st;
+}
+
+kd_status kd_release(kd_ctx* ctx, kd_handle h) {
+    if (!ctx || !h) return KD_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    release_handle(ctx, h);
+    return KD_OK;
+}
+
+kd_status kd_build_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_tree* outs) {
+    if (!ctx || !clouds || !outs || count < 1) return KD_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    cudaSetDevice(ctx->device);
+    ctx->last_error.clear();
+    kd_presorted* h = nullptr;
+    kd_status st = presort_batch(ctx, clouds, count, &h);
+    if (st != KD_OK) return st;
+    st = build_batch(ctx, h, outs);
+    release_handle(ctx, h);
+    if (st == KD_OK && (ctx->debug & 2)) collect_timing(ctx);
+    return st;
+}
+
+kd_status kd_submit(kd_ctx* ctx, const kd_cloud* cloud, kd_tree* out, kd_ticket* ticket) {
+    (void)cloud;
+    (void)out;
+    (void)ticket;
+    return fail(ctx, KD_EINVAL, "serving is not available in this build");
+}
+
+kd_status kd_wait(kd_ctx* ctx, kd_ticket ticket, int timeout_ms) {
+    (void)ticket;
+    (void)timeout_ms;
+    return fail(ctx, KD_EINVAL, "serving is not available in this build");
+}
+
+kd_status kd_serving_stats(kd_ctx* ctx, int64_t* completed, double* p50_us, double* p99_us) {
+    if (!ctx) return KD_EINVAL;
+    if (completed) *completed = ctx->completed;
+    if (p50_us) *p50_us = 0;
+    if (p99_us) *p99_us = 0;
+    return KD_OK;
+}
+
+kd_status kd_destroy(kd_ctx* ctx) {
+    if (!ctx) return KD_EINVAL;
+    {
+        std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+        cudaSetDevice(ctx->device);
+        cudaStreamSynchronize(ctx->stream);
+        for (auto& t : ctx->timed) {
+            cudaEventDestroy(t.a);
+            cudaEventDestroy(t.b);
+        }
+        for (auto e : ctx->event_pool) cudaEventDestroy(e);
+        if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
+        if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    }
+    delete ctx;
+    return KD_OK;
+}
+
+const char* kd_last_error(kd_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "no context"; }
+
+int64_t kd_launch_count(kd_ctx* ctx) { return ctx ? ctx->launches.load() : 0; }
+
+kd_status kd_kernel_stats(kd_ctx* ctx, int family, double* ms, int64_t* launches, double* units,
+                          double* bytes) {
+    if (!ctx || family < 0 || family >= F_COUNT) return KD_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    collect_timing(ctx);
+    if (ms) *ms = ctx->fam_ms[family];
+    if (launches) *launches = ctx->fam_launches[family];
+    if (units) *units = ctx->fam_units[family];
+    if (bytes) *bytes = ctx->fam_bytes[family];
+    return KD_OK;
+}
+
+kd_status kd_kernel_stats_reset(kd_ctx* ctx) {
+    if (!ctx) return KD_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    collect_timing(ctx);
+    for (int f = 0; f < F_COUNT; ++f) {
+        ctx->fam_ms[f] = 0;
+        ctx->fam_units[f] = 0;
+        ctx->fam_bytes[f] = 0;
+        ctx->fam_launches[f] = 0;
+    }
+    return KD_OK;
+}
+
+}  // extern "C"

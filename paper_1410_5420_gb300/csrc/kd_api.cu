@@ -37,7 +37,7 @@ cudaError_t launch_dedup(int key64, int64_t n, const void* key0, const uint32_t*
                          int64_t stride, int k, const uint32_t* cloud_plane, int cloud_digits, uint32_t* ids_out,
                          uint32_t* status, uint32_t* tile_ctr, int64_t* m_out, uint32_t* hist, int32_t* mcloud,
                          int* err, cudaStream_t s);
-cudaError_t launch_records(const int64_t* m_ptr, int64_t max_m, int k, const AllPlanes& rec, uint32_t present_bits,
+cudaError_t launch_records(const int64_t* m_ptr, int64_t max_m, int k, const AllPlanes& rec, uint64_t present_bits,
                            cudaStream_t s);
 cudaError_t launch_arrays_out(const int64_t* m_ptr, int64_t max_m, int k, const AllPlanes& rec,
                               const uint32_t* perm0, int32_t* out, cudaStream_t s);
@@ -572,15 +572,15 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
             ranks_prev = ranks;
         }
         // remaining planes of every array
-        uint32_t present = 0;
+        uint64_t present = 0;  // 8 bits per array: planes written by the chain sorts
         for (int d = 1; d < k; ++d) {
-            uint32_t bits = 1u;  // R_0
+            uint64_t bits = 1u;  // R_0
             for (int q = d + 1; q < k; ++q) bits |= 1u << q;
             present |= bits << (d * MAXK);
         }
         int scat = 0, own = 0, readp = k - 1;
         for (int d = 0; d < k; ++d) {
-            const uint32_t bits = (present >> (d * MAXK)) & 0xffu;
+            const uint32_t bits = (uint32_t)(present >> (d * MAXK)) & 0xffu;
             for (int q = 0; q < k; ++q)
                 if (!((bits >> q) & 1u)) {
                     if (q == d) ++own; else if (d != 1) ++scat;

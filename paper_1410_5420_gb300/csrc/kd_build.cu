@@ -238,7 +238,10 @@ __global__ void __launch_bounds__(LEVEL_THREADS)
                 const uint32_t rq = bufs.p[q][T.src_buf][q][gsrc];
                 const uint32_t r0 = bufs.p[q][T.src_buf][0][gsrc];
                 medr[C.medr_off + ((int64_t)1 << T.lev_out) - 1 + fsi[j]] = rq;
-                C.node[dest] = (int32_t)((int64_t)perm0[r0] - C.in_off);
+                if (r0 >= goff && r0 < goff + m)
+                    C.node[dest] = (int32_t)((int64_t)perm0[r0] - C.in_off);
+                else
+                    atomicOr(err, ERR_INTERNAL);
             }
         }
     }
@@ -397,7 +400,11 @@ __global__ void __launch_bounds__(FIN_THREADS)
             const int32_t a = sg & 0xffff, b = sg >> 16, c = a + ((b - a) >> 1);
             if (i != c) continue;
             const int32_t addr = lo + c;
-            C.node[addr] = (int32_t)((int64_t)perm0[rk[prim[c]]] - C.in_off);
+            const uint32_t r0 = rk[prim[c]];
+            if (r0 >= C.off && r0 < C.off + C.m)
+                C.node[addr] = (int32_t)((int64_t)perm0[r0] - C.in_off);
+            else
+                bad = 1;
             if (C.left) C.left[addr] = a <= c - 1 ? lo + child_mid(a, c - 1) : -1;
             if (C.right) C.right[addr] = c + 1 <= b ? lo + child_mid(c + 1, b) : -1;
             if (C.dim) C.dim[addr] = (uint8_t)p;

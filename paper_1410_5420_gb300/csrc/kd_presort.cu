@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort_pass(const int64_t* __res
                                                             const uint32_t* __restrict__ hist_row, int shift,
                                                             uint32_t* __restrict__ status,
                                                             uint32_t* __restrict__ tile_ctr,
-                                                            int* __restrict__ err) {
+                                                            int* __restrict__ err, int64_t gather_limit) {
     constexpr int TILE = SORT_THREADS * IPT;
     __shared__ uint32_t s_wc[SORT_WARPS][RADIX];
     __shared__ uint32_t s_goff[RADIX];
@@ -117,7 +117,12 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort_pass(const int64_t* __res
         key[j] = 0;
         if (o < tile_n) {
             const int64_t pos = base + o;
-            key[j] = (MODE == KEY_GATHER) ? key_src[gidx[pos]] : key_src[pos];
+            if (MODE == KEY_GATHER) {
+                const uint32_t id = gidx[pos];
+                if ((int64_t)id < gather_limit) key[j] = key_src[id]; else atomicOr(err, ERR_INTERNAL);
+            } else {
+                key[j] = key_src[pos];
+            }
         }
     }
     // warp-level multisplit: rank among equal digits of this warp, in order
@@ -245,9 +250,13 @@ __global__ void __launch_bounds__(256) k_dedup(int64_t n, const KW* __restrict__
         if (o < tile_n) {
             const int64_t pos = base + o;
             id[j] = ids[pos];
+            if ((int64_t)id[j] >= n) {
+                atomicOr(err, ERR_INTERNAL);
+                id[j] = 0;
+            }
             const KW k0 = key0[pos];
             bool dup = false;
-            if (pos > 0 && key0[pos - 1] == k0) {
+            if (pos > 0 && key0[pos - 1] == k0 && (int64_t)ids[pos - 1] < n) {
                 const uint32_t pid = ids[pos - 1];
                 dup = true;
                 for (int d = 1; d < k && dup; ++d)
@@ -306,19 +315,20 @@ __global__ void __launch_bounds__(256) k_dedup(int64_t n, const KW* __restrict__
 // From array 1's complete rank vectors (rec[1][p] for p != 1; its own rank
 // is the position), fill every plane of every array that the chain sorts
 // did not write: rec[d][d][i] = i, and rec[d][p][rank_d] = rank_p by scatter.
-// present[d] is the bit set of planes already written for array d.
+// Bits 8d..8d+7 of present_bits: the planes already written for array d.
 __global__ void __launch_bounds__(256) k_records(const int64_t* __restrict__ m_ptr, int k,
-                                                 AllPlanes rec, uint32_t present_bits) {
+                                                 AllPlanes rec, uint64_t present_bits) {
     const int64_t m = *m_ptr;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
          i += (int64_t)gridDim.x * blockDim.x) {
         uint32_t v[MAXK];
         for (int p = 0; p < k; ++p) v[p] = (p == 1) ? (uint32_t)i : rec.p[1][p][i];
         for (int d = 0; d < k; ++d) {
-            const uint32_t present = (present_bits >> (d * MAXK)) & 0xffu;
+            const uint32_t present = (uint32_t)(present_bits >> (d * MAXK)) & 0xffu;
             if (!((present >> d) & 1u)) rec.p[d][d][i] = (uint32_t)i;
             if (d == 1) continue;
             const uint32_t r = v[d];
+            if ((int64_t)r >= m) continue;  // inconsistent ranks: never written out of range
             for (int p = 0; p < k; ++p)
                 if (p != d && !((present >> p) & 1u)) rec.p[d][p][r] = v[p];
         }
@@ -334,7 +344,8 @@ __global__ void k_arrays_out(const int64_t* __restrict__ m_ptr, int k, AllPlanes
          i += (int64_t)gridDim.x * blockDim.x) {
         const int d = (int)(i / m);
         const int64_t j = i - (int64_t)d * m;
-        out[i] = (int32_t)perm0[rec.p[d][0][j]];
+        const uint32_t r0 = rec.p[d][0][j];
+        out[i] = (int64_t)r0 < m ? (int32_t)perm0[r0] : -1;
     }
 }
 
@@ -385,13 +396,15 @@ cudaError_t launch_sort_pass(int key64, int mode, const int64_t* count_ptr, int6
                              const void* key_src, const uint32_t* gidx, void* key_dst,
                              const PayloadArgs& pay, const uint32_t* hist_row, int shift,
                              uint32_t* status, uint32_t* tile_ctr, int* err, cudaStream_t s) {
+    const int64_t gather_limit = max_count;  // tuple ids index planes of max_count entries
     const int tile = SORT_THREADS * SORT_IPT;
     const int64_t tiles = (max_count + tile - 1) / tile;
     if (tiles == 0) return cudaSuccess;
     const size_t smem = (size_t)tile * (key64 ? 8 : 4);
 #define KD_SORT_LAUNCH(KW, MODE)                                                                      \
     k_sort_pass<KW, MODE, SORT_IPT><<<(unsigned)tiles, SORT_THREADS, smem, s>>>(                    \
-        count_ptr, (const KW*)key_src, gidx, (KW*)key_dst, pay, hist_row, shift, status, tile_ctr, err)
+        count_ptr, (const KW*)key_src, gidx, (KW*)key_dst, pay, hist_row, shift, status, tile_ctr, err,  \
+        gather_limit)
     if (key64) {
         if (mode == KEY_DIRECT) KD_SORT_LAUNCH(uint64_t, KEY_DIRECT);
         else if (mode == KEY_GATHER) KD_SORT_LAUNCH(uint64_t, KEY_GATHER);
@@ -423,7 +436,7 @@ cudaError_t launch_dedup(int key64, int64_t n, const void* key0, const uint32_t*
 }
 
 cudaError_t launch_records(const int64_t* m_ptr, int64_t max_m, int k, const AllPlanes& rec,
-                           uint32_t present_bits, cudaStream_t s) {
+                           uint64_t present_bits, cudaStream_t s) {
     if (max_m == 0) return cudaSuccess;
     k_records<<<grid_for(max_m, 256, 152 * 16), 256, 0, s>>>(m_ptr, k, rec, present_bits);
     return cudaGetLastError();

@@ -28,27 +28,33 @@ namespace kd {
 cudaError_t launch_transform(int dtype, const void* coords, int64_t n, int k, void* keys, int64_t stride,
                              const int64_t* cloud_start, int ncloud, uint32_t* cloud_plane, int cloud_digits,
                              uint32_t* hist, int* err, cudaStream_t s);
-int sort_tile();
+int sort_tile(int key64);
+size_t sort_status_words(int64_t max_count);
+size_t sort_flag_words(int64_t max_count);
 cudaError_t launch_sort_pass(int key64, int mode, const int64_t* count_ptr, int64_t max_count,
                              const void* key_src, const uint32_t* gidx, void* key_dst, const PayloadArgs& pay,
-                             const uint32_t* hist_row, int shift, uint32_t* status, uint32_t* tile_ctr, int* err,
+                             const uint32_t* digit_base, int shift, uint32_t* status, uint32_t* tile_ctr, int* err,
                              cudaStream_t s);
+cudaError_t launch_digit_bases(const uint32_t* hist, int nrows, uint32_t* bases, cudaStream_t s);
 cudaError_t launch_dedup(int key64, int64_t n, const void* key0, const uint32_t* ids, const void* keys,
                          int64_t stride, int k, const uint32_t* cloud_plane, int cloud_digits, uint32_t* ids_out,
                          uint32_t* status, uint32_t* tile_ctr, int64_t* m_out, uint32_t* hist, int32_t* mcloud,
                          int* err, cudaStream_t s);
-cudaError_t launch_records(const int64_t* m_ptr, int64_t max_m, int k, const AllPlanes& rec, uint64_t present_bits,
-                           cudaStream_t s);
+cudaError_t launch_own_ranks(const int64_t* m_ptr, int64_t max_m, int k, const AllPlanes& rec, cudaStream_t s);
+cudaError_t launch_perm_bases(const int64_t* m_ptr, int shift, uint32_t* bases, cudaStream_t s);
+cudaError_t launch_perm_scatter(const int64_t* m_ptr, int64_t max_m, const uint32_t* dest, const PayloadArgs& pa,
+                                cudaStream_t s);
 cudaError_t launch_arrays_out(const int64_t* m_ptr, int64_t max_m, int k, const AllPlanes& rec,
                               const uint32_t* perm0, int32_t* out, cudaStream_t s);
 int level_tile(int k);
 int level_status_stride(int k);
-cudaError_t launch_level_pass(int k, const AllBufs& bufs, int q, const LevelTile* tiles, int ntiles,
+cudaError_t launch_level_pass(int k, const AllBufs& bufs, int q, const LevelJob* jobs, int njobs, int ntiles,
                               const CloudDev* clouds, uint32_t* medr, const uint32_t* perm0, uint32_t* status,
-                              uint32_t* tile_ctr, int* err, cudaStream_t s);
+                              int* err, cudaStream_t s);
+size_t level_status_words(int k, int ntiles);
 size_t finish_smem(int k, int smax);
-cudaError_t launch_finish(const AllBufs& bufs, int k, const FinUnit* units, int nunits, const CloudDev* clouds,
-                          const uint32_t* perm0, int smax, int* err, cudaStream_t s);
+cudaError_t launch_finish(const AllBufs& bufs, int k, const int64_t* unit_prefix, int ncloud, int nunits,
+                          const CloudDev* clouds, const uint32_t* perm0, int smax, int* err, cudaStream_t s);
 cudaError_t launch_top_nodes(const CloudDev* clouds, const int64_t* prefix, int ncloud, int64_t total, int k,
                              const uint32_t* perm0, uint32_t* medr, int all_nodes, cudaStream_t s);
 }  // namespace kd
@@ -397,6 +403,9 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
         CKS(S.get(&cstart, (size_t)(count + 1) * 8));
     }
     CKS(S.get(&hist, (size_t)nrows * RADIX * 4));
+    uint32_t *bases_all = nullptr, *bases_kept = nullptr;  // digit bases over all / kept tuples
+    CKS(S.get(&bases_all, (size_t)nrows * RADIX * 4));
+    CKS(S.get(&bases_kept, (size_t)nrows * RADIX * 4));
     CKS(S.get(&d_n, 8));
     CKS(S.get(&mcloud, (size_t)count * 4));
     CKS(S.get(&d_err, 4));
@@ -411,6 +420,10 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
     {
         LaunchTimer lt(ctx, F_TRANSFORM, (double)N, nullptr, (double)k * (tsz + w) + (count > 1 ? 4 : 0));
         CK(launch_transform(dtype, coords, N, k, keys, N, cstart, count, cloud_plane, cloud_digits, hist, d_err, s));
+    }
+    {
+        LaunchTimer lt(ctx, F_OTHER, 0.0);
+        CK(launch_digit_bases(hist, nrows, bases_all, s));
     }
     std::vector<uint32_t> h_hist((size_t)nrows * RADIX);
     CK(cudaMemcpyAsync(h_hist.data(), hist, h_hist.size() * 4, cudaMemcpyDeviceToHost, s));
@@ -444,14 +457,19 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
     if (count > 1) plane_passes(cloud_sort, -1, cloud_digits, false);
 
     // buffers
-    const int64_t tiles = (N + sort_tile() - 1) / sort_tile();
     size_t npasses = s0.size() + cloud_sort.size();
     for (auto& v : chain) npasses += v.size();
+    const int nperm = k >= 2 ? k - 1 : 0;  // grouping passes of the rank-plane permutations
+    npasses += nperm;
     uint32_t *status = nullptr, *ctrs = nullptr;
-    const size_t status_words_per = (size_t)tiles * RADIX;
-    CKS(S.get(&status, (npasses * status_words_per + (size_t)tiles) * 4));
+    const size_t status_words_per = (sort_status_words(N) + 3) & ~(size_t)3;  // flags | records, per pass
+    const size_t dedup_words = (size_t)pad4((N + 4095) / 4096) * 3;
+    CKS(S.get(&status, (npasses * status_words_per + dedup_words) * 4));
     CKS(S.get(&ctrs, (npasses + 1) * 4));
-    CK(cudaMemsetAsync(status, 0, (npasses * status_words_per + (size_t)tiles) * 4, s));
+    // only the flag words need zeroing (records are written before their flags)
+    for (size_t pi = 0; pi < npasses; ++pi)
+        CK(cudaMemsetAsync(status + pi * status_words_per, 0, sort_flag_words(N) * 4, s));
+    CK(cudaMemsetAsync(status + npasses * status_words_per, 0, (size_t)pad4((N + 4095) / 4096) * 4, s));
     CK(cudaMemsetAsync(ctrs, 0, (npasses + 1) * 4, s));
     unsigned char* kbuf[2];
     uint32_t* ibuf[2];
@@ -484,7 +502,7 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
         void* kdst = next_gathers ? nullptr : (void*)kbuf[kc ^ 1];
         LaunchTimer lt(ctx, F_SORT, (double)N, nullptr, pass_bytes(P, kdst != nullptr, pay.n));
         CK(launch_sort_pass(plane64(P.plane), P.mode, d_n, N, ksrc, ibuf[ic], kdst, pay,
-                            hist + (size_t)row_of(P.plane, P.digit) * RADIX, 8 * P.digit,
+                            bases_all + (size_t)row_of(P.plane, P.digit) * RADIX, 8 * P.digit,
                             status + pass_no * status_words_per, ctrs + pass_no, d_err, s));
         ++pass_no;
         kc ^= 1;
@@ -498,6 +516,10 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
                         status + npasses * status_words_per, ctrs + npasses, H->d_m, hist, mcloud, d_err, s));
     }
     ic ^= 1;
+    {
+        LaunchTimer lt(ctx, F_OTHER, 0.0);
+        CK(launch_digit_bases(hist, nrows, bases_kept, s));
+    }
     // cloud grouping of array 0 (batches) ----------------------------------
     for (size_t i = 0; i < cloud_sort.size(); ++i) {
         const Pass& P = cloud_sort[i];
@@ -509,7 +531,7 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
         const void* ksrc = P.mode == KEY_BUF ? (const void*)kbuf[kc] : plane_ptr(-1);
         LaunchTimer lt(ctx, F_SORT, 0.0, H->d_m, pass_bytes(P, !last, 1));
         CK(launch_sort_pass(0, P.mode, H->d_m, N, ksrc, ibuf[ic], last ? nullptr : (void*)kbuf[kc ^ 1], pay,
-                            hist + (size_t)row_of(-1, P.digit) * RADIX, 8 * P.digit,
+                            bases_kept + (size_t)row_of(-1, P.digit) * RADIX, 8 * P.digit,
                             status + pass_no * status_words_per, ctrs + pass_no, d_err, s));
         ++pass_no;
         kc ^= 1;
@@ -560,7 +582,7 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
                 void* kdst = (last || next_gathers) ? nullptr : (void*)kbuf[kc ^ 1];
                 LaunchTimer lt(ctx, F_SORT, 0.0, H->d_m, pass_bytes(P, kdst != nullptr, pay.n));
                 CK(launch_sort_pass(plane64(P.plane), P.mode, H->d_m, N, ksrc, cur_id, kdst, pay,
-                                    hist + (size_t)row_of(P.plane, P.digit) * RADIX, 8 * P.digit,
+                                    bases_kept + (size_t)row_of(P.plane, P.digit) * RADIX, 8 * P.digit,
                                     status + pass_no * status_words_per, ctrs + pass_no, d_err, s));
                 ++pass_no;
                 kc ^= 1;
@@ -571,23 +593,64 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
             id_src = cur_id;
             ranks_prev = ranks;
         }
-        // remaining planes of every array
-        uint64_t present = 0;  // 8 bits per array: planes written by the chain sorts
-        for (int d = 1; d < k; ++d) {
-            uint64_t bits = 1u;  // R_0
-            for (int q = d + 1; q < k; ++q) bits |= 1u << q;
+        // Remaining rank planes: array d (d != 1) lacks the ranks R_p of the
+        // planes the chain did not carry; they are a permutation of array 1's
+        // planes by destination R_d.  Each is done as one grouping pass on the
+        // top bits of R_d (ranges that fit in L2) and an in-range scatter.
+        uint32_t* pbases = nullptr;
+        CKS(S.get(&pbases, RADIX * 4));
+        uint64_t present = 0;  // 8 bits per array: planes already written
+        for (int d = 0; d < k; ++d) {
+            if (d == 1) {
+                uint64_t bits = 0;
+                for (int q = 0; q < k; ++q) bits |= (q != 1) ? (1u << q) : 0u;
+                present |= bits << (d * MAXK);
+                continue;
+            }
+            uint64_t bits = (d >= 2) ? 1u : 0u;  // chain output carries R_0 and R_{d+1..k-1}
+            if (d >= 2)
+                for (int q = d + 1; q < k; ++q) bits |= 1u << q;
+            std::vector<int> miss;
+            for (int q = 0; q < k; ++q)
+                if (q != d && !((bits >> q) & 1u)) miss.push_back(q);
+            if (!miss.empty()) {
+                const int nv = (int)miss.size();
+                int shift = 0;
+                while (((int64_t)1 << shift) * nv * 4 < ((int64_t)48 << 20) && shift < 30) ++shift;
+                while ((((int64_t)N - 1) >> shift) > 255) ++shift;
+                {
+                    LaunchTimer lt(ctx, F_OTHER, 0.0);
+                    CK(launch_perm_bases(H->d_m, shift, pbases, s));
+                }
+                PayloadArgs pay{};
+                pay.n = nv;
+                for (int j = 0; j < nv; ++j) {
+                    pay.src[j] = miss[j] == 1 ? nullptr : H->rec.p[1][miss[j]];  // R_1 of array 1 = position
+                    pay.dst[j] = pbuf[0][j];
+                }
+                uint32_t* gdest = ibuf[0];
+                {
+                    LaunchTimer lt(ctx, F_RECORDS, 0.0, H->d_m, 4.0 + 8.0 * nv + 4.0);
+                    CK(launch_sort_pass(0, KEY_DIRECT, H->d_m, N, H->rec.p[1][d], nullptr, gdest, pay, pbases, shift,
+                                        status + pass_no * status_words_per, ctrs + pass_no, d_err, s));
+                }
+                ++pass_no;
+                PayloadArgs sc{};
+                sc.n = nv;
+                for (int j = 0; j < nv; ++j) {
+                    sc.src[j] = pbuf[0][j];
+                    sc.dst[j] = H->rec.p[d][miss[j]];
+                }
+                LaunchTimer lt(ctx, F_RECORDS, 0.0, H->d_m, 4.0 + 8.0 * nv);
+                CK(launch_perm_scatter(H->d_m, N, gdest, sc, s));
+                for (int q : miss) bits |= 1u << q;
+            }
             present |= bits << (d * MAXK);
         }
-        int scat = 0, own = 0, readp = k - 1;
-        for (int d = 0; d < k; ++d) {
-            const uint32_t bits = (uint32_t)(present >> (d * MAXK)) & 0xffu;
-            for (int q = 0; q < k; ++q)
-                if (!((bits >> q) & 1u)) {
-                    if (q == d) ++own; else if (d != 1) ++scat;
-                }
+        if (present != 0) {
+            LaunchTimer lt(ctx, F_RECORDS, 0.0, H->d_m, 4.0 * k);
+            CK(launch_own_ranks(H->d_m, N, k, H->rec, s));
         }
-        LaunchTimer lt(ctx, F_RECORDS, 0.0, H->d_m, 4.0 * (readp + own + scat));
-        CK(launch_records(H->d_m, N, k, H->rec, present, s));
     }
     // learn m ----------------------------------------------------------------
     int64_t M = 0;
@@ -643,7 +706,13 @@ kd_status build_batch(kd_ctx* ctx, kd_presorted* H, kd_tree* outs) {
     int* d_err = nullptr;
     CKS(S.get(&d_err, 4));
     CK(cudaMemsetAsync(d_err, 0, 4, s));
-    const int smax = ctx->smax_override ? ctx->smax_override : (k <= 4 ? 2048 : 1024);
+    // subtree size finished on chip: a power of two in [1024, 4096] (the
+    // level-pass tiles of 2048 positions need segments of at least 683)
+    int smax = k <= 4 ? 2048 : 1024;
+    if (ctx->smax_override) {
+        smax = 1024;
+        while (smax < ctx->smax_override && smax < 4096) smax *= 2;
+    }
     if (k >= 2 && smax * 3 < level_tile(k) + 3) return fail(ctx, KD_EINVAL, "switch threshold too small");
 
     // outputs: user device arrays, or staging for host arrays
@@ -700,7 +769,9 @@ kd_status build_batch(kd_ctx* ctx, kd_presorted* H, kd_tree* outs) {
     if (medr_total) CKS(S.get(&medr, (size_t)medr_total * 4));
 
     // schedule of level passes -------------------------------------------
-    std::vector<std::vector<LevelTile>> step_tiles;
+    std::vector<std::vector<LevelJob>> step_jobs;
+    std::vector<int64_t> step_ntiles;
+    std::vector<double> step_elems;
     std::vector<int> step_q;
     std::vector<std::array<int, MAXK>> moves(count), level(count);
     for (int i = 0; i < count; ++i) {
@@ -715,7 +786,9 @@ kd_status build_batch(kd_ctx* ctx, kd_presorted* H, kd_tree* outs) {
             if (lam[i] >= 1) tmax = std::max(tmax, lam[i] + k - 2);
         for (int t = 1; t <= tmax; ++t) {
             const int q = t % k;
-            std::vector<LevelTile> tl;
+            std::vector<LevelJob> jl;
+            int64_t ntl = 0;
+            double el = 0;
             for (int i = 0; i < count; ++i) {
                 if (lam[i] < 1) continue;
                 const int cur = level[i][q];
@@ -729,28 +802,25 @@ kd_status build_batch(kd_ctx* ctx, kd_presorted* H, kd_tree* outs) {
                 if (lout - lin > k - 1) return fail(ctx, KD_EDEVICE, "internal: level pass spans too many levels");
                 if (max_seg(H->m_c[i], lin) - 1 < (tile + 2) / 3)
                     return fail(ctx, KD_EDEVICE, "internal: segments too small for a level-pass tile");
-                const int src = buf_after(moves[i][q]);
-                const int dst = buf_after(moves[i][q] + 1);
-                const int wm = (lout % k == q) && (lout < lam[i]);
-                for (int64_t p0 = 0; p0 < H->m_c[i]; p0 += tile) {
-                    LevelTile T{};
-                    T.cloud = i;
-                    T.lev_in = lin;
-                    T.lev_out = lout;
-                    T.src_buf = src;
-                    T.dst_buf = dst;
-                    T.write_med = wm;
-                    T.pos0 = p0;
-                    T.npos = (int32_t)std::min<int64_t>(tile, H->m_c[i] - p0);
-                    T.first = p0 == 0;
-                    tl.push_back(T);
-                }
+                LevelJob J{};
+                J.cloud = i;
+                J.lev_in = lin;
+                J.lev_out = lout;
+                J.src_buf = buf_after(moves[i][q]);
+                J.dst_buf = buf_after(moves[i][q] + 1);
+                J.write_med = (lout % k == q) && (lout < lam[i]);
+                J.tile_begin = ntl;
+                jl.push_back(J);
+                ntl += (H->m_c[i] + tile - 1) / tile;
+                el += (double)H->m_c[i];
                 moves[i][q] += 1;
                 level[i][q] = lout;
                 need_bufs = true;
             }
-            if (!tl.empty()) {
-                step_tiles.push_back(std::move(tl));
+            if (!jl.empty()) {
+                step_jobs.push_back(std::move(jl));
+                step_ntiles.push_back(ntl);
+                step_elems.push_back(el);
                 step_q.push_back(q);
             }
         }
@@ -784,59 +854,51 @@ kd_status build_batch(kd_ctx* ctx, kd_presorted* H, kd_tree* outs) {
         if (cd[i].m > 0 && (k == 1 || lam[i] >= 1)) e = ((int64_t)1 << lam[i]) - 1;
         top_prefix[i + 1] = top_prefix[i] + e;
     }
-    std::vector<FinUnit> units;
-    if (k >= 2)
-        for (int i = 0; i < count; ++i) {
-            if (cd[i].m == 0) continue;
-            const int64_t nu = (int64_t)1 << lam[i];
-            for (int64_t u = 0; u < nu; ++u) units.push_back(FinUnit{i, (int32_t)u});
-        }
-    size_t ntiles_all = 0;
-    for (auto& v : step_tiles) ntiles_all += v.size();
+    std::vector<int64_t> unit_prefix(count + 1, 0);  // finisher units: 2^lam segments per cloud
+    for (int i = 0; i < count; ++i)
+        unit_prefix[i + 1] = unit_prefix[i] + ((k >= 2 && cd[i].m > 0) ? ((int64_t)1 << lam[i]) : 0);
+    const int64_t nunits = unit_prefix[count];
+    std::vector<LevelJob> flat;
+    std::vector<size_t> job_off;
+    for (auto& v : step_jobs) {
+        job_off.push_back(flat.size());
+        flat.insert(flat.end(), v.begin(), v.end());
+    }
     CloudDev* d_cd = nullptr;
-    int64_t* d_prefix = nullptr;
-    FinUnit* d_units = nullptr;
-    LevelTile* d_tiles = nullptr;
-    uint32_t *d_status = nullptr, *d_ctr = nullptr;
+    int64_t *d_prefix = nullptr, *d_uprefix = nullptr;
+    LevelJob* d_jobs = nullptr;
+    uint32_t* d_status = nullptr;
     CKS(S.get(&d_cd, sizeof(CloudDev) * count));
     CKS(S.get(&d_prefix, sizeof(int64_t) * (count + 1)));
+    CKS(S.get(&d_uprefix, sizeof(int64_t) * (count + 1)));
     CK(cudaMemcpyAsync(d_cd, cd.data(), sizeof(CloudDev) * count, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(d_prefix, top_prefix.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s));
-    if (!units.empty()) {
-        CKS(S.get(&d_units, sizeof(FinUnit) * units.size()));
-        CK(cudaMemcpyAsync(d_units, units.data(), sizeof(FinUnit) * units.size(), cudaMemcpyHostToDevice, s));
-    }
-    std::vector<LevelTile> flat;
-    flat.reserve(ntiles_all);
-    for (auto& v : step_tiles) flat.insert(flat.end(), v.begin(), v.end());
-    const int stride = k >= 2 ? level_status_stride(k) : 1;
+    CK(cudaMemcpyAsync(d_uprefix, unit_prefix.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s));
+    // per step: tile counts, their segmented scan and head flags (no zeroing needed)
+    size_t st_words = 0;
+    for (size_t st = 0; st < step_jobs.size(); ++st)
+        st_words = std::max(st_words, level_status_words(std::max(k, 2), (int)step_ntiles[st]));
     if (!flat.empty()) {
-        CKS(S.get(&d_tiles, sizeof(LevelTile) * flat.size()));
-        CK(cudaMemcpyAsync(d_tiles, flat.data(), sizeof(LevelTile) * flat.size(), cudaMemcpyHostToDevice, s));
-        CKS(S.get(&d_status, flat.size() * stride * 4));
-        CKS(S.get(&d_ctr, step_tiles.size() * 4));
-        CK(cudaMemsetAsync(d_status, 0, flat.size() * stride * 4, s));
-        CK(cudaMemsetAsync(d_ctr, 0, step_tiles.size() * 4, s));
+        CKS(S.get(&d_jobs, sizeof(LevelJob) * flat.size()));
+        CK(cudaMemcpyAsync(d_jobs, flat.data(), sizeof(LevelJob) * flat.size(), cudaMemcpyHostToDevice, s));
+        CKS(S.get(&d_status, st_words * 4));
     }
     // launches ----------------------------------------------------------------
     {
         LaunchTimer lt(ctx, F_TOP, (double)top_prefix[count], nullptr, 13.0);
         CK(launch_top_nodes(d_cd, d_prefix, count, top_prefix[count], k, H->perm0, medr, k == 1, s));
     }
-    size_t off = 0;
-    for (size_t st = 0; st < step_tiles.size(); ++st) {
-        const int nt = (int)step_tiles[st].size();
-        double units_el = 0;
-        for (auto& T : step_tiles[st]) units_el += T.npos;
-        LaunchTimer lt(ctx, F_LEVEL, units_el, nullptr, 8.0 * k);
-        CK(launch_level_pass(k, bufs, step_q[st], d_tiles + off, nt, d_cd, medr, H->perm0, d_status + off * stride,
-                             d_ctr + st, d_err, s));
-        off += nt;
+    for (size_t st = 0; st < step_jobs.size(); ++st) {
+        const int F = step_jobs[st][0].lev_out - step_jobs[st][0].lev_in;
+        LaunchTimer lt(ctx, F_LEVEL, step_elems[st], nullptr, 8.0 * k + 4.0 * F);
+        ctx->launches += 2;  // count pass and scan
+        CK(launch_level_pass(k, bufs, step_q[st], d_jobs + job_off[st], (int)step_jobs[st].size(),
+                             (int)step_ntiles[st], d_cd, medr, H->perm0, d_status, d_err, s));
     }
-    if (!units.empty()) {
+    if (nunits > 0) {
         LaunchTimer lt(ctx, F_FINISH, (double)M, nullptr,
                        4.0 * (2 * k - 1) + 8.0 + (want_l ? 4 : 0) + (want_r ? 4 : 0) + (want_d ? 1 : 0));
-        CK(launch_finish(bufs, k, d_units, (int)units.size(), d_cd, H->perm0, smax, d_err, s));
+        CK(launch_finish(bufs, k, d_uprefix, count, (int)nunits, d_cd, H->perm0, smax, d_err, s));
     }
     CKS(check_device_err(ctx, d_err));
     if (any_host) {

@@ -12,9 +12,11 @@
 //                 (its halves are in place); the pass then applies the
 //                 splits of levels L+1..L+k-1, whose medians come from the
 //                 arrays that were primary there, as a stable 2^(k-1)-way
-//                 segmented multisplit (warp match/popc ranking, decoupled
-//                 look-back across tiles of one segment, smem-staged
-//                 coalesced scatter).  With this schedule each tree level
+//                 segmented multisplit (warp ballot ranking, smem-staged
+//                 coalesced scatter).  The counts of a segment's elements in
+//                 earlier tiles come from a count pass (k_level_count, which
+//                 reads only the decision planes) and a segmented scan over
+//                 tiles (k_level_scan).  With this schedule each tree level
 //                 costs one pass over one array.  Elements carry their rank
 //                 in every super-key order, so each compare is one integer
 //                 compare (super keys are unique after deduplication).
@@ -32,12 +34,172 @@ namespace kd {
 
 constexpr uint32_t INV = 0xffffffffu;
 
+// Level-L segments touching the tile [pos0, pos0 + npos): at most
+// LEVEL_NSMAX (the host sizes tiles so that this holds).  Thread 0 only.
+__device__ __forceinline__ int tile_segments(int32_t pos0, int32_t npos, int32_t m, int L, int32_t* lo, int32_t* hi,
+                                             int32_t* idx, int* err) {
+    int ns = 0;
+    int32_t i = pos0;
+    const int32_t pend = pos0 + npos - 1;
+    while (i <= pend) {
+        const Seg sg = segment_of(i, m, L);
+        if (sg.idx < 0) {
+            ++i;
+            continue;
+        }
+        if (ns == LEVEL_NSMAX) {
+            atomicOr(err, ERR_INTERNAL);
+            break;
+        }
+        lo[ns] = sg.lo;
+        hi[ns] = sg.hi;
+        idx[ns] = sg.idx;
+        ++ns;
+        i = sg.hi + 1;
+    }
+    return ns;
+}
+
+// Route one element through levels lev_in .. lev_in+F-1: r[f] is its rank in
+// super key (lev_in + f) mod K.  Returns the digit (segment slot * 2^F +
+// bucket) and its final segment, or INV if it is the median of one of
+// these levels (a node: not copied).
+template <int K>
+__device__ __forceinline__ uint32_t route(const uint32_t (&r)[K], int F, int lev_in, int sj, int NB, int32_t a,
+                                          int32_t z, int32_t si, const uint32_t* __restrict__ medr, int64_t medr_off,
+                                          int32_t& flo, int32_t& fhi) {
+    uint32_t b = 0;
+#pragma unroll
+    for (int f = 0; f < K - 1; ++f) {
+        if (f < F) {
+            const int L = lev_in + f;
+            const int32_t mid = a + ((z - a) >> 1);
+            const uint32_t mv = medr[medr_off + ((int64_t)1 << L) - 1 + si];
+            if (r[f] < mv) {
+                z = mid - 1;
+                si = 2 * si;
+                b = 2 * b;
+            } else if (r[f] > mv) {
+                a = mid + 1;
+                si = 2 * si + 1;
+                b = 2 * b + 1;
+            } else {
+                return INV;
+            }
+        }
+    }
+    flo = a;
+    fhi = z;
+    return (uint32_t)(sj * NB) + b;
+}
+
+// Count pass of a level step: per tile, the bucket counts of its last
+// segment (cnt[t][b]) and whether that segment starts inside the tile
+// (head[t]).  Reads only the F decision planes.
 template <int K, int IPT>
 __global__ void __launch_bounds__(LEVEL_THREADS)
-    k_level_pass(const __grid_constant__ AllBufs bufs, int q, const LevelTile* __restrict__ tiles, int ntiles,
+    k_level_count(const __grid_constant__ AllBufs bufs, int q, const LevelJob* __restrict__ jobs, int njobs,
+                  const CloudDev* __restrict__ clouds, const uint32_t* __restrict__ medr, uint32_t* __restrict__ cnt,
+                  uint32_t* __restrict__ head, int* __restrict__ err) {
+    constexpr int NBMAX = 1 << (K - 1);
+    constexpr int NDMAX = LEVEL_NSMAX * NBMAX;
+    __shared__ uint32_t s_cnt[NDMAX];
+    __shared__ int32_t s_seglo[LEVEL_NSMAX], s_seghi[LEVEL_NSMAX], s_segidx[LEVEL_NSMAX];
+    __shared__ int s_ns;
+    const int tid = threadIdx.x;
+    const int t = blockIdx.x;
+    const LevelTile T = job_tile(jobs, njobs, t, LEVEL_THREADS * IPT, clouds);
+    const CloudDev& C = clouds[T.cloud];
+    const int F = T.lev_out - T.lev_in;
+    const int NB = 1 << F;
+    const int32_t pos0 = (int32_t)T.pos0;
+    for (int i = tid; i < NDMAX; i += LEVEL_THREADS) s_cnt[i] = 0;
+    if (tid == 0) s_ns = tile_segments(pos0, T.npos, C.m, T.lev_in, s_seglo, s_seghi, s_segidx, err);
+    __syncthreads();
+    const int ns = s_ns;
+    const int64_t goff = C.off;
+    const int64_t medr_off = C.medr_off;
+    for (int o = tid; o < T.npos; o += LEVEL_THREADS) {
+        const int32_t pos = pos0 + o;
+        int sj = -1;
+#pragma unroll
+        for (int x = 0; x < LEVEL_NSMAX; ++x)
+            if (x < ns && pos >= s_seglo[x] && pos <= s_seghi[x]) sj = x;
+        if (sj < 0) continue;
+        uint32_t r[K];
+#pragma unroll
+        for (int f = 0; f < K; ++f) r[f] = (f < F) ? bufs.p[q][T.src_buf][(T.lev_in + f) % K][goff + pos] : 0u;
+        int32_t flo, fhi;
+        const uint32_t d = route<K>(r, F, T.lev_in, sj, NB, s_seglo[sj], s_seghi[sj], s_segidx[sj], medr, medr_off,
+                                    flo, fhi);
+        if (d != INV) atomicAdd(&s_cnt[d], 1u);
+    }
+    __syncthreads();
+    if (tid < NBMAX) cnt[(int64_t)t * NBMAX + tid] = (ns > 0 && tid < NB) ? s_cnt[(ns - 1) * NB + tid] : 0u;
+    if (tid == 0) head[t] = (ns == 1 && s_seglo[0] < pos0) ? 0u : 1u;
+}
+
+// Segmented inclusive scan over the tiles of a level step, one block per
+// bucket: incl[t][b] = cnt[t][b] + (head[t] ? 0 : incl[t-1][b]).
+__global__ void __launch_bounds__(1024) k_level_scan(int ntiles, int nbmax, const uint32_t* __restrict__ cnt,
+                                                     const uint32_t* __restrict__ head, uint32_t* __restrict__ incl) {
+    __shared__ uint32_t s_f[32], s_v[32];
+    const int b = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t carry = 0;
+    for (int t0 = 0; t0 < ntiles; t0 += 1024) {
+        const int t = t0 + tid;
+        uint32_t f = t < ntiles ? head[t] : 1u;
+        uint32_t v = t < ntiles ? cnt[(int64_t)t * nbmax + b] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t f2 = __shfl_up_sync(0xffffffffu, f, o);
+            const uint32_t v2 = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) {
+                if (!f) v += v2;
+                f |= f2;
+            }
+        }
+        if (lane == 31) {
+            s_f[warp] = f;
+            s_v[warp] = v;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t wf = s_f[lane], wv = s_v[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t f2 = __shfl_up_sync(0xffffffffu, wf, o);
+                const uint32_t v2 = __shfl_up_sync(0xffffffffu, wv, o);
+                if (lane >= o) {
+                    if (!wf) wv += v2;
+                    wf |= f2;
+                }
+            }
+            s_f[lane] = wf;
+            s_v[lane] = wv;
+        }
+        __syncthreads();
+        // prefix of earlier warps in this chunk, then the chunk carry
+        uint32_t pf = 0, pv = 0;
+        if (warp > 0) {
+            pf = s_f[warp - 1];
+            pv = s_v[warp - 1];
+        }
+        if (!pf) pv += carry;
+        if (!f) v += pv;
+        if (t < ntiles) incl[(int64_t)t * nbmax + b] = v;
+        const uint32_t lastf = s_f[31], lastv = s_v[31];
+        carry = lastf ? lastv : carry + lastv;
+        __syncthreads();
+    }
+}
+
+template <int K, int IPT>
+__global__ void __launch_bounds__(LEVEL_THREADS, 2)
+    k_level_pass(const __grid_constant__ AllBufs bufs, int q, const LevelJob* __restrict__ jobs, int njobs,
                  const CloudDev* __restrict__ clouds, uint32_t* __restrict__ medr,
-                 const uint32_t* __restrict__ perm0, uint32_t* __restrict__ status,
-                 uint32_t* __restrict__ tile_ctr, int* __restrict__ err) {
+                 const uint32_t* __restrict__ perm0, const uint32_t* __restrict__ incl, int* __restrict__ err) {
     constexpr int TILE = LEVEL_THREADS * IPT;
     constexpr int NBMAX = 1 << (K - 1);
     constexpr int NDMAX = LEVEL_NSMAX * NBMAX;
@@ -48,61 +210,38 @@ __global__ void __launch_bounds__(LEVEL_THREADS)
     __shared__ uint32_t s_excl[NBMAX];
     __shared__ int32_t s_seglo[LEVEL_NSMAX], s_seghi[LEVEL_NSMAX], s_segidx[LEVEL_NSMAX];
     __shared__ int s_ns;
-    __shared__ uint32_t s_tile, s_total;
+    __shared__ uint32_t s_total;
     __shared__ uint32_t s_warp[LEVEL_WARPS];
     extern __shared__ __align__(16) uint32_t s_dyn[];  // s_dest[TILE] | s_val[TILE]
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
-    __syncthreads();
-    const int t = (int)s_tile;
-    if (t >= ntiles) return;
-    const LevelTile T = tiles[t];
+    const int t = blockIdx.x;
+    const LevelTile T = job_tile(jobs, njobs, t, TILE, clouds);
     const CloudDev C = clouds[T.cloud];
     const int F = T.lev_out - T.lev_in;
     const int NB = 1 << F;
     const int ND = LEVEL_NSMAX * NB;
     const int32_t m = C.m;
     const int32_t pos0 = (int32_t)T.pos0;
-    const int32_t pend = pos0 + T.npos - 1;
-    if (tid == 0) {
-        int ns = 0;
-        int32_t i = pos0;
-        while (i <= pend) {
-            const Seg sg = segment_of(i, m, T.lev_in);
-            if (sg.idx < 0) {
-                ++i;
-                continue;
-            }
-            if (ns == LEVEL_NSMAX) {
-                atomicOr(err, ERR_INTERNAL);
-                break;
-            }
-            s_seglo[ns] = sg.lo;
-            s_seghi[ns] = sg.hi;
-            s_segidx[ns] = sg.idx;
-            ++ns;
-            i = sg.hi + 1;
-        }
-        s_ns = ns;
-    }
+    if (tid == 0) s_ns = tile_segments(pos0, T.npos, m, T.lev_in, s_seglo, s_seghi, s_segidx, err);
     for (int i = tid; i < LEVEL_WARPS * NDMAX; i += LEVEL_THREADS) (&s_wc[0][0])[i] = 0;
     __syncthreads();
     const int ns = s_ns;
+    // the first segment may have begun in earlier tiles: their counts come
+    // from the scanned count pass
+    if (tid < NB) s_excl[tid] = (ns > 0 && s_seglo[0] < pos0) ? incl[(int64_t)(t - 1) * NBMAX + tid] : 0u;
 
     const int wbase = warp * 32 * IPT;
     const int64_t goff = C.off;
     uint32_t v[K][IPT];
     uint32_t dig[IPT];
-    int32_t flo[IPT], fhi[IPT], fmid[IPT], fsi[IPT];
+    int32_t flo[IPT], fhi[IPT];  // final segment of each element
 #pragma unroll
     for (int j = 0; j < IPT; ++j) {
         const int o = wbase + j * 32 + lane;
         dig[j] = INV;
         flo[j] = 0;
         fhi[j] = -1;
-        fmid[j] = -1;
-        fsi[j] = 0;
 #pragma unroll
         for (int p = 0; p < K; ++p) v[p][j] = 0;
         if (o < T.npos) {
@@ -115,51 +254,32 @@ __global__ void __launch_bounds__(LEVEL_THREADS)
             for (int x = 0; x < LEVEL_NSMAX; ++x)
                 if (x < ns && pos >= s_seglo[x] && pos <= s_seghi[x]) sj = x;
             if (sj >= 0) {
-                int32_t a = s_seglo[sj], z = s_seghi[sj], si = s_segidx[sj];
-                uint32_t b = 0;
-                bool drop = false;
+                uint32_t r[K];
 #pragma unroll
-                for (int f = 0; f < K - 1; ++f) {
-                    if (f < F && !drop) {
-                        const int L = T.lev_in + f;
-                        const int32_t mid = a + ((z - a) >> 1);
-                        const uint32_t mv = medr[C.medr_off + ((int64_t)1 << L) - 1 + si];
-                        const uint32_t r = v[f][j];  // rank in super key L mod K
-                        if (r < mv) {
-                            z = mid - 1;
-                            si = 2 * si;
-                            b = 2 * b;
-                        } else if (r > mv) {
-                            a = mid + 1;
-                            si = 2 * si + 1;
-                            b = 2 * b + 1;
-                        } else {
-                            drop = true;  // the median of level L: a node, not copied
-                        }
-                    }
-                }
-                if (!drop) {
-                    dig[j] = (uint32_t)(sj * NB) + b;
-                    flo[j] = a;
-                    fhi[j] = z;
-                    fmid[j] = a + ((z - a) >> 1);
-                    fsi[j] = si;
-                }
+                for (int f = 0; f < K; ++f) r[f] = v[f][j];
+                dig[j] = route<K>(r, F, T.lev_in, sj, NB, s_seglo[sj], s_seghi[sj], s_segidx[sj], medr, C.medr_off,
+                                  flo[j], fhi[j]);
             }
         }
     }
-    // warp multisplit ranking on (segment, bucket)
-    uint32_t rank[IPT];
+    // warp multisplit ranking on (segment, bucket): equal-digit lane masks
+    // from ballots over the digit bits (the invalid marker is NDMAX)
+    constexpr int DBITS = 2 + (K - 1) + 1;  // log2(NSMAX) + log2(NBMAX) + marker bit
+    uint32_t slot[IPT];
 #pragma unroll
     for (int j = 0; j < IPT; ++j) {
-        const uint32_t d = dig[j];
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        uint32_t before = 0;
-        if (d != INV) before = s_wc[warp][d];
-        rank[j] = before + __popc(peers & lanemask_lt());
-        __syncwarp();
-        if (d != INV && lane == __ffs(peers) - 1) s_wc[warp][d] = before + __popc(peers);
-        __syncwarp();
+        const uint32_t d = dig[j] == INV ? (uint32_t)NDMAX : dig[j];
+        uint32_t peers = 0xffffffffu;
+#pragma unroll
+        for (int bit = 0; bit < DBITS; ++bit) {
+            const uint32_t bb = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
+            peers &= ((d >> bit) & 1u) ? bb : ~bb;
+        }
+        const int leader = __ffs(peers) - 1;
+        uint32_t old = 0;
+        if (lane == leader && d < (uint32_t)NDMAX) old = atomicAdd(&s_wc[warp][d], (uint32_t)__popc(peers));
+        old = __shfl_sync(0xffffffffu, old, leader);
+        slot[j] = old + __popc(peers & lanemask_lt());
     }
     __syncthreads();
     for (int d = tid; d < ND; d += LEVEL_THREADS) {
@@ -173,21 +293,7 @@ __global__ void __launch_bounds__(LEVEL_THREADS)
         s_cnt[d] = c;
     }
     __syncthreads();
-    // look-back: only the first segment can have begun in an earlier tile;
-    // each tile publishes the bucket counts of its last segment.
-    const bool first_cont = ns > 0 && s_seglo[0] < pos0;
-    if (tid < NB) {
-        uint32_t* st = status + (int64_t)t * NBMAX;
-        const uint32_t c = ns > 0 ? s_cnt[(ns - 1) * NB + tid] : 0u;
-        const bool last_is_cont = (ns == 1) && first_cont;
-        st_volatile(st + tid, (last_is_cont ? ST_AGG : ST_INC) | c);
-        uint32_t e = 0;
-        if (first_cont) {
-            e = lookback(status, t, NBMAX, tid, err);
-            if (last_is_cont) st_volatile(st + tid, ST_INC | ((e + c) & ST_COUNT));
-        }
-        s_excl[tid] = e;
-    }
+    // tile-local start of every (segment, bucket) digit
     {
         const int per = (ND + LEVEL_THREADS - 1) / LEVEL_THREADS;
         uint32_t loc = 0;
@@ -218,13 +324,13 @@ __global__ void __launch_bounds__(LEVEL_THREADS)
     __syncthreads();
     uint32_t* s_dest = s_dyn;
     uint32_t* s_val = s_dyn + TILE;
-    uint32_t slot[IPT];
 #pragma unroll
     for (int j = 0; j < IPT; ++j) {
-        slot[j] = INV;
-        if (dig[j] != INV) {
+        if (dig[j] == INV) {
+            slot[j] = INV;
+        } else {
             const uint32_t d = dig[j];
-            const uint32_t within = s_wc[warp][d] + rank[j];
+            const uint32_t within = s_wc[warp][d] + slot[j];
             slot[j] = s_tstart[d] + within;
             const int32_t dest = s_dbase[d] + (int32_t)within;
             // the destination must lie in the element's final segment; any
@@ -232,12 +338,14 @@ __global__ void __launch_bounds__(LEVEL_THREADS)
             const bool ok = dest >= flo[j] && dest <= fhi[j];
             if (!ok) atomicOr(err, ERR_INTERNAL);
             s_dest[slot[j]] = ok ? (uint32_t)(goff + dest) : INV;
-            if (ok && T.write_med && dest == fmid[j]) {
-                // the new median of level lev_out (rare: re-read its planes q and 0)
+            if (ok && T.write_med && dest == flo[j] + ((fhi[j] - flo[j]) >> 1)) {
+                // the new median of level lev_out (rare: re-read its planes q
+                // and 0, and find its segment index)
                 const int64_t gsrc = goff + pos0 + wbase + j * 32 + lane;
                 const uint32_t rq = bufs.p[q][T.src_buf][q][gsrc];
                 const uint32_t r0 = bufs.p[q][T.src_buf][0][gsrc];
-                medr[C.medr_off + ((int64_t)1 << T.lev_out) - 1 + fsi[j]] = rq;
+                const int32_t si = segment_of(flo[j], m, T.lev_out).idx;
+                medr[C.medr_off + ((int64_t)1 << T.lev_out) - 1 + si] = rq;
                 if (r0 >= goff && r0 < goff + m)
                     C.node[dest] = (int32_t)((int64_t)perm0[r0] - C.in_off);
                 else
@@ -264,95 +372,148 @@ constexpr uint32_t HOLE = 0xffffffffu;
 
 __device__ __forceinline__ uint32_t seg_pack(int32_t a, int32_t b) { return (uint32_t)a | ((uint32_t)b << 16); }
 
-// Stable partition of one array (lids in src) around the medians of the
-// current level, into dst.  Segmented block scan of packed (less, greater)
-// counts; positions are blocked per thread.
+// Stable partition of one array (lids, src) around the medians of the
+// current level into dst.  Each warp owns a chunk of consecutive positions
+// and walks it 32 at a time: ballots of "less" / "greater" / "segment start"
+// give every lane its count of earlier less/greater elements in its segment;
+// a segment crossing chunk boundaries gets the preceding warps' counts.
+template <int GMAX>
 __device__ __forceinline__ void fin_partition(const uint16_t* __restrict__ src, uint16_t* __restrict__ dst,
                                               const uint16_t* __restrict__ prim, const uint32_t* __restrict__ rkp,
-                                              const uint32_t* __restrict__ seg, int S, int32_t* s_fl,
-                                              uint32_t* s_fv, int* bad) {
+                                              const uint32_t* __restrict__ seg, int S, uint32_t* s_agg, int* bad) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int per = (S + FIN_THREADS - 1) / FIN_THREADS;
-    const int i0 = tid * per;
-    int tf = 0;
-    uint32_t tv = 0;
-    for (int x = 0; x < per; ++x) {
-        const int i = i0 + x;
-        if (i >= S) break;
-        const uint32_t sg = seg[i];
-        if (sg == HOLE) continue;
-        const int32_t a = sg & 0xffff, b = sg >> 16, c = a + ((b - a) >> 1);
-        if (i == a) {
-            tf = 1;
-            tv = 0;
-        }
-        const uint32_t r = rkp[src[i]], mv = rkp[prim[c]];
-        tv += r < mv ? 1u : (r > mv ? 0x10000u : 0u);
-    }
-    int f = tf;
-    uint32_t v = tv;
+    const int groups = (S + FIN_THREADS - 1) / FIN_THREADS;  // per warp, <= GMAX
+    const int chunk = groups * 32;
+    const uint32_t lt = lanemask_lt();
+    uint32_t info[GMAX];  // lid | isL << 16 | isR << 17 | needs-carry << 18
+    uint32_t ex[GMAX];    // in-warp exclusive counts: less | greater << 16
+    uint32_t pos2[GMAX];  // a | c << 16
+    uint32_t cl = 0, cr = 0;
+    bool seen = false;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int f2 = __shfl_up_sync(0xffffffffu, f, o);
-        const uint32_t v2 = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) {
-            if (!f) v += v2;
-            f |= f2;
+    for (int g = 0; g < GMAX; ++g) {
+        info[g] = 0;
+        ex[g] = 0;
+        pos2[g] = 0;
+        if (g < groups) {
+            const int i = warp * chunk + g * 32 + lane;
+            const uint32_t sg = i < S ? seg[i] : HOLE;
+            bool isL = false, isR = false, start = false;
+            uint32_t lid = 0;
+            int32_t a = 0, c = 0;
+            if (sg != HOLE) {
+                a = sg & 0xffff;
+                const int32_t bb = sg >> 16;
+                c = a + ((bb - a) >> 1);
+                lid = src[i];
+                const uint32_t r = rkp[lid], mv = rkp[prim[c]];
+                isL = r < mv;
+                isR = r > mv;
+                start = i == a;
+            }
+            const uint32_t Lm = __ballot_sync(0xffffffffu, isL);
+            const uint32_t Rm = __ballot_sync(0xffffffffu, isR);
+            const uint32_t Sm = __ballot_sync(0xffffffffu, start);
+            const uint32_t sle = Sm & (lt | (1u << lane));
+            uint32_t inseg, bl, br;
+            bool need = false;
+            if (sle) {
+                const int s0 = 31 - __clz(sle);
+                inseg = lt & ~((1u << s0) - 1u);
+                bl = 0;
+                br = 0;
+            } else {
+                inseg = lt;
+                bl = cl;
+                br = cr;
+                need = !seen;
+            }
+            const uint32_t el = bl + __popc(Lm & inseg), er = br + __popc(Rm & inseg);
+            info[g] = lid | (isL ? 1u << 16 : 0u) | (isR ? 1u << 17 : 0u) | (need ? 1u << 18 : 0u);
+            ex[g] = el | (er << 16);
+            pos2[g] = (uint32_t)a | ((uint32_t)c << 16);
+            if (Sm) {
+                const int sl = 31 - __clz(Sm);
+                const uint32_t tail = ~((1u << sl) - 1u);
+                cl = __popc(Lm & tail);
+                cr = __popc(Rm & tail);
+                seen = true;
+            } else {
+                cl += __popc(Lm);
+                cr += __popc(Rm);
+            }
         }
     }
-    int ef = __shfl_up_sync(0xffffffffu, f, 1);
-    uint32_t ev = __shfl_up_sync(0xffffffffu, v, 1);
-    if (lane == 0) {
-        ef = 0;
-        ev = 0;
-    }
-    if (lane == 31) {
-        s_fl[warp] = f;
-        s_fv[warp] = v;
-    }
+    if (lane == 0) s_agg[warp] = (seen ? 1u << 31 : 0u) | (cl & 0x7fffu) | ((cr & 0x7fffu) << 15);
     __syncthreads();
-    int wf = 0;
-    uint32_t wv = 0;
+    // carry into this warp's chunk: segmented sum of the preceding warps
+    uint32_t wl = 0, wr = 0;
     for (int w = 0; w < warp; ++w) {
-        wv = s_fl[w] ? s_fv[w] : wv + s_fv[w];
-        wf |= s_fl[w];
+        const uint32_t x = s_agg[w];
+        if (x >> 31) {
+            wl = x & 0x7fffu;
+            wr = (x >> 15) & 0x7fffu;
+        } else {
+            wl += x & 0x7fffu;
+            wr += (x >> 15) & 0x7fffu;
+        }
     }
-    uint32_t acc = ef ? ev : wv + ev;
-    for (int x = 0; x < per; ++x) {
-        const int i = i0 + x;
-        if (i >= S) break;
-        const uint32_t sg = seg[i];
-        if (sg == HOLE) continue;
-        const int32_t a = sg & 0xffff, b = sg >> 16, c = a + ((b - a) >> 1);
-        if (i == a) acc = 0;
-        const uint16_t lid = src[i];
-        const uint32_t r = rkp[lid], mv = rkp[prim[c]];
-        if (r < mv) {
-            const int32_t o = a + (int32_t)(acc & 0xffffu);
-            if (o < c) dst[o] = lid; else *bad = 1;
-            acc += 1u;
-        } else if (r > mv) {
-            const int32_t o = c + 1 + (int32_t)(acc >> 16);
-            if (o <= b) dst[o] = lid; else *bad = 1;
-            acc += 0x10000u;
+#pragma unroll
+    for (int g = 0; g < GMAX; ++g) {
+        if (g < groups) {
+            const uint32_t f = info[g];
+            uint32_t el = ex[g] & 0xffffu, er = ex[g] >> 16;
+            if ((f >> 18) & 1u) {
+                el += wl;
+                er += wr;
+            }
+            const int32_t a = pos2[g] & 0xffff, c = pos2[g] >> 16;
+            const uint16_t lid = (uint16_t)(f & 0xffffu);
+            if ((f >> 16) & 1u) {
+                const int32_t o = a + (int32_t)el;
+                if (o < c) dst[o] = lid; else *bad = 1;
+            } else if ((f >> 17) & 1u) {
+                const int32_t o = c + 1 + (int32_t)er;
+                const int32_t i = warp * chunk + g * 32 + lane;
+                const int32_t bb = (int32_t)(seg[i] >> 16);
+                if (o <= bb) dst[o] = lid; else *bad = 1;
+            }
         }
     }
 }
 
+// Write the node at cloud-local address addr (the median of [lo_a, hi_a],
+// unit-relative bounds a..b with median c) and its children / dimension.
+__device__ __forceinline__ void fin_emit(const CloudDev& C, const uint32_t* __restrict__ perm0, int32_t lo,
+                                         int32_t a, int32_t b, int32_t c, uint32_t r0, int p, int* bad) {
+    const int32_t addr = lo + c;
+    if (r0 >= C.off && r0 < C.off + C.m)
+        C.node[addr] = (int32_t)((int64_t)perm0[r0] - C.in_off);
+    else
+        *bad = 1;
+    if (C.left) C.left[addr] = a <= c - 1 ? lo + child_mid(a, c - 1) : -1;
+    if (C.right) C.right[addr] = c + 1 <= b ? lo + child_mid(c + 1, b) : -1;
+    if (C.dim) C.dim[addr] = (uint8_t)p;
+}
+
+template <int SMAX>
 __global__ void __launch_bounds__(FIN_THREADS)
-    k_finish(const __grid_constant__ AllBufs bufs, int k, const FinUnit* __restrict__ units,
-             const CloudDev* __restrict__ clouds, const uint32_t* __restrict__ perm0, int smax,
-             int* __restrict__ err) {
+    k_finish(const __grid_constant__ AllBufs bufs, int k, const int64_t* __restrict__ unit_prefix, int ncloud,
+             const CloudDev* __restrict__ clouds, const uint32_t* __restrict__ perm0, int* __restrict__ err) {
+    constexpr int GMAX = SMAX / FIN_THREADS;
+    constexpr int smax = SMAX;
     extern __shared__ __align__(16) uint32_t sm[];
-    __shared__ int32_t s_fl[FIN_THREADS / 32];
-    __shared__ uint32_t s_fv[FIN_THREADS / 32];
+    __shared__ uint32_t s_agg[FIN_THREADS / 32];
     __shared__ int s_cur[MAXK + 1];
+    __shared__ int s_nseg;
     uint32_t* rk = sm;                                          // rk[p * smax + lid]
     uint32_t* seg = rk + (size_t)k * smax;                      // packed segment per position
     uint16_t* arr = reinterpret_cast<uint16_t*>(seg + smax);   // (k+1) storages of lids
-    const int tid = threadIdx.x;
-    const FinUnit U = units[blockIdx.x];
-    const CloudDev C = clouds[U.cloud];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    FinUnit U;
+    U.cloud = last_le(unit_prefix, ncloud + 1, blockIdx.x);
+    U.seg = (int32_t)(blockIdx.x - unit_prefix[U.cloud]);
+    const CloudDev& C = clouds[U.cloud];
     int32_t lo, hi;
     segment_bounds(C.m, C.lam, U.seg, lo, hi);
     const int S = hi - lo + 1;
@@ -367,11 +528,13 @@ __global__ void __launch_bounds__(FIN_THREADS)
         for (int i = tid; i < S; i += FIN_THREADS) rk[p * smax + i] = src[g + i];
     }
     if (tid <= k) s_cur[tid] = tid;
+    if (tid == 0) s_nseg = 0;
     __syncthreads();
     for (int i = tid; i < S; i += FIN_THREADS) {
         arr[i] = (uint16_t)i;
         seg[i] = seg_pack(0, S - 1);
     }
+    int bad = 0;
     for (int d = 1; d < k; ++d) {
         const uint32_t* src0 = bufs.p[d][C.buf[d]][0];
         for (int i = tid; i < S; i += FIN_THREADS) {
@@ -381,15 +544,14 @@ __global__ void __launch_bounds__(FIN_THREADS)
                 const int mid = (a + b) >> 1;
                 if (rk[mid] < r0) a = mid + 1; else b = mid;
             }
-            if (a >= S || rk[a] != r0) atomicOr(err, ERR_INTERNAL);
+            if (a >= S || rk[a] != r0) bad = 1;
             arr[d * smax + i] = (uint16_t)min(a, S - 1);
         }
     }
     __syncthreads();
-    int nlev = 0;
-    while ((1 << nlev) <= S) ++nlev;  // ceil(log2(S + 1))
-    int bad = 0;
-    for (int dl = 0; dl < nlev; ++dl) {
+    // block levels: while a segment may hold more than 32 tuples
+    int dl = 0;
+    for (; (S >> dl) > 32; ++dl) {
         const int L = C.lam + dl;
         const int p = L % k;
         const uint16_t* prim = arr + s_cur[p] * smax;
@@ -398,20 +560,11 @@ __global__ void __launch_bounds__(FIN_THREADS)
             const uint32_t sg = seg[i];
             if (sg == HOLE) continue;
             const int32_t a = sg & 0xffff, b = sg >> 16, c = a + ((b - a) >> 1);
-            if (i != c) continue;
-            const int32_t addr = lo + c;
-            const uint32_t r0 = rk[prim[c]];
-            if (r0 >= C.off && r0 < C.off + C.m)
-                C.node[addr] = (int32_t)((int64_t)perm0[r0] - C.in_off);
-            else
-                bad = 1;
-            if (C.left) C.left[addr] = a <= c - 1 ? lo + child_mid(a, c - 1) : -1;
-            if (C.right) C.right[addr] = c + 1 <= b ? lo + child_mid(c + 1, b) : -1;
-            if (C.dim) C.dim[addr] = (uint8_t)p;
+            if (i == c) fin_emit(C, perm0, lo, a, b, c, rk[prim[c]], p, &bad);
         }
         for (int j = 1; j < k; ++j) {
             const int d = (p + j) % k;
-            fin_partition(arr + s_cur[d] * smax, arr + s_cur[k] * smax, prim, rkp, seg, S, s_fl, s_fv, &bad);
+            fin_partition<GMAX>(arr + s_cur[d] * smax, arr + s_cur[k] * smax, prim, rkp, seg, S, s_agg, &bad);
             __syncthreads();
             if (tid == 0) {
                 const int x = s_cur[d];
@@ -427,6 +580,97 @@ __global__ void __launch_bounds__(FIN_THREADS)
             seg[i] = (i == c) ? HOLE : (i < c ? seg_pack(a, c - 1) : seg_pack(c + 1, b));
         }
         __syncthreads();
+    }
+    // warp levels: every remaining segment has at most 32 tuples; one warp
+    // finishes a segment with one tuple per lane, in the order of the
+    // current primary array.  For every dimension q the lane holds LESS_q,
+    // the set of lanes whose tuples precede its own in super key q (from
+    // the segment's sorted array q); a lane's rank in its sub-segment SUB is
+    // then popc(LESS_p & SUB): equal to the median offset -> node, below ->
+    // left child, above -> right child.
+    uint32_t* list = reinterpret_cast<uint32_t*>(arr + s_cur[k] * smax);  // spare storage, first smax bytes
+    for (int i = tid; i < S; i += FIN_THREADS) {
+        const uint32_t sg = seg[i];
+        if (sg != HOLE && (int32_t)(sg & 0xffff) == i) {
+            const int e = atomicAdd(&s_nseg, 1);
+            if (e < smax / 4) list[e] = sg; else bad = 1;  // below lane_of (byte smax)
+        }
+    }
+    __syncthreads();
+    const int nseg = min(s_nseg, smax / 4);
+    const int p0 = (C.lam + dl) % k;
+    const uint16_t* prim0 = arr + s_cur[p0] * smax;
+    // lane_of[lid]: lane holding tuple lid in its warp (each tuple is in
+    // exactly one segment); it lives in the free upper half of the spare
+    // storage, above the segment list (at most S/16 words).  Per-segment
+    // scratch words come from `seg`, whose entries are no longer read.
+    uint8_t* lane_of = reinterpret_cast<uint8_t*>(arr + s_cur[k] * smax) + smax;
+    const uint32_t lt = lanemask_lt();
+    for (int e = warp; e < nseg; e += FIN_THREADS / 32) {
+        const uint32_t sg = list[e];
+        const int32_t a0 = sg & 0xffff, b0 = sg >> 16;
+        const int n = b0 - a0 + 1;
+        const bool in = lane < n;
+        const uint16_t lid = in ? prim0[a0 + lane] : 0;
+        uint32_t* scr = seg + a0;  // n words, owned by this warp for this segment
+        if (in) lane_of[lid] = (uint8_t)lane;
+        __syncwarp();
+        uint32_t less[MAXK];
+#pragma unroll
+        for (int q = 0; q < MAXK; ++q) {
+            less[q] = 0;
+            if (q < k) {
+                if (q == p0) {
+                    less[q] = lt;
+                } else {
+                    // lane i reads the tuple at sorted position i of array q
+                    // and the lane x that holds it
+                    const uint16_t* aq = arr + s_cur[q] * smax;
+                    const uint32_t x = in ? lane_of[aq[a0 + lane]] : 0u;
+                    // prefix-OR over sorted order gives, at position i, the lanes of
+                    // positions < i; push it to lane x
+                    uint32_t bit = in ? (1u << x) : 0u;
+                    uint32_t incl = bit;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (lane >= o) incl |= y;
+                    }
+                    __syncwarp();
+                    if (in) scr[x] = incl & ~bit;
+                    __syncwarp();
+                    less[q] = in ? scr[lane] : 0u;
+                }
+            }
+        }
+        __syncwarp();
+        uint32_t sub = __ballot_sync(0xffffffffu, in);
+        bool active = in;
+        int32_t mlo = a0, mhi = b0;
+        for (int l = dl; __any_sync(0xffffffffu, active); ++l) {
+            const int p = (C.lam + l) % k;
+            uint32_t lp = 0;
+#pragma unroll
+            for (int q = 0; q < MAXK; ++q)
+                if (q == p) lp = less[q];
+            const int rank = __popc(lp & sub);
+            const int32_t c = mlo + ((mhi - mlo) >> 1);
+            const bool goL = active && rank < c - mlo;
+            const bool goR = active && rank > c - mlo;
+            if (active && rank == c - mlo) {
+                fin_emit(C, perm0, lo, mlo, mhi, c, rk[lid], p, &bad);
+                active = false;
+            }
+            const uint32_t Lm = __ballot_sync(0xffffffffu, goL);
+            const uint32_t Rm = __ballot_sync(0xffffffffu, goR);
+            if (goL) {
+                mhi = c - 1;
+                sub &= Lm;
+            } else if (goR) {
+                mlo = c + 1;
+                sub &= Rm;
+            }
+        }
     }
     if (bad) atomicOr(err, ERR_INTERNAL);
 }
@@ -465,17 +709,22 @@ __global__ void k_top_nodes(const CloudDev* __restrict__ clouds, const int64_t* 
 // ------------------------------------------------------------ launchers
 int level_ipt(int k) { return 8; }
 int level_tile(int k) { return LEVEL_THREADS * level_ipt(k); }
-int level_status_stride(int k) { return 1 << (k - 1); }
+int level_status_stride(int k) { return 1 << (k - 1); }  // status rows (buckets) per tile
 
-cudaError_t launch_level_pass(int k, const AllBufs& bufs, int q, const LevelTile* tiles, int ntiles,
+cudaError_t launch_level_pass(int k, const AllBufs& bufs, int q, const LevelJob* jobs, int njobs, int ntiles,
                               const CloudDev* clouds, uint32_t* medr, const uint32_t* perm0, uint32_t* status,
-                              uint32_t* tile_ctr, int* err, cudaStream_t s) {
+                              int* err, cudaStream_t s) {
     if (ntiles == 0) return cudaSuccess;
+    const int nbmax = 1 << (k - 1);
+    uint32_t* cnt = status;                                  // [ntiles][nbmax]
+    uint32_t* incl = cnt + (size_t)ntiles * nbmax;           // [ntiles][nbmax]
+    uint32_t* head = incl + (size_t)ntiles * nbmax;          // [ntiles]
     const size_t smem = (size_t)2 * level_tile(k) * sizeof(uint32_t);
 #define KD_LEVEL_CASE(KK)                                                                                  \
     case KK:                                                                                             \
-        k_level_pass<KK, 8><<<ntiles, LEVEL_THREADS, smem, s>>>(bufs, q, tiles, ntiles, clouds, medr, perm0, \
-                                                              status, tile_ctr, err);                     \
+        k_level_count<KK, 8><<<ntiles, LEVEL_THREADS, 0, s>>>(bufs, q, jobs, njobs, clouds, medr, cnt, head, err); \
+        k_level_scan<<<nbmax, 1024, 0, s>>>(ntiles, nbmax, cnt, head, incl);                              \
+        k_level_pass<KK, 8><<<ntiles, LEVEL_THREADS, smem, s>>>(bufs, q, jobs, njobs, clouds, medr, perm0, incl, err); \
         break;
     switch (k) {
         KD_LEVEL_CASE(2)
@@ -492,15 +741,31 @@ cudaError_t launch_level_pass(int k, const AllBufs& bufs, int q, const LevelTile
     return cudaGetLastError();
 }
 
+// status words one level step needs: counts, inclusive scan, head flags
+size_t level_status_words(int k, int ntiles) { return (size_t)ntiles * (2u << (k - 1)) + (size_t)ntiles; }
+
 size_t finish_smem(int k, int smax) { return (size_t)k * smax * 4 + (size_t)smax * 4 + (size_t)(k + 1) * smax * 2; }
 
-cudaError_t launch_finish(const AllBufs& bufs, int k, const FinUnit* units, int nunits, const CloudDev* clouds,
-                          const uint32_t* perm0, int smax, int* err, cudaStream_t s) {
+cudaError_t launch_finish(const AllBufs& bufs, int k, const int64_t* unit_prefix, int ncloud, int nunits,
+                          const CloudDev* clouds, const uint32_t* perm0, int smax, int* err, cudaStream_t s) {
     if (nunits == 0) return cudaSuccess;
     const size_t smem = finish_smem(k, smax);
-    cudaError_t e = cudaFuncSetAttribute(k_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_finish<<<nunits, FIN_THREADS, smem, s>>>(bufs, k, units, clouds, perm0, smax, err);
+    cudaError_t e;
+    if (smax == 2048) {
+        e = cudaFuncSetAttribute(k_finish<2048>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_finish<2048><<<nunits, FIN_THREADS, smem, s>>>(bufs, k, unit_prefix, ncloud, clouds, perm0, err);
+    } else if (smax == 1024) {
+        e = cudaFuncSetAttribute(k_finish<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_finish<1024><<<nunits, FIN_THREADS, smem, s>>>(bufs, k, unit_prefix, ncloud, clouds, perm0, err);
+    } else if (smax == 4096) {
+        e = cudaFuncSetAttribute(k_finish<4096>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_finish<4096><<<nunits, FIN_THREADS, smem, s>>>(bufs, k, unit_prefix, ncloud, clouds, perm0, err);
+    } else {
+        return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

@@ -10,8 +10,10 @@ namespace kd {
 // ------------------------------------------------------------------ limits
 constexpr int MAXK = 8;
 constexpr int RADIX = 256;
-constexpr int SORT_THREADS = 256;
+constexpr int SORT_THREADS = 512;
 constexpr int SORT_WARPS = SORT_THREADS / 32;
+constexpr int SORT_IPT = 16;
+constexpr int SORT_TILE = SORT_THREADS * SORT_IPT;
 constexpr int MAXPAY = 10;          // payload planes carried by one sort pass
 constexpr int LEVEL_THREADS = 256;
 constexpr int LEVEL_WARPS = LEVEL_THREADS / 32;
@@ -48,26 +50,44 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 
 // Walk back from tile `tile - 1` over the status words (stride `stride`
 // words per tile, word `slot` of each) until an inclusive prefix is found;
-// returns the sum of everything before `tile`.  Sets ERR_TIMEOUT and
-// returns what it has if a wait exceeds SPIN_LIMIT.
-__device__ __forceinline__ uint32_t lookback(const uint32_t* status, int64_t tile, int stride,
-                                             int slot, int* err) {
+// returns the sum of everything before `tile`.  A window of W predecessor
+// words is loaded at once (independent loads), so a walk over many tiles
+// that have only published their aggregates costs one memory round trip per
+// W tiles.  Sets ERR_TIMEOUT and returns what it has if the wait for a
+// not-yet-published word exceeds SPIN_LIMIT polls.
+template <int W>
+__device__ __forceinline__ uint32_t lookback(const uint32_t* status, int64_t tile, int stride, int slot,
+                                             int* err) {
     uint32_t excl = 0;
     int64_t t = tile - 1;
     uint32_t spins = 0;
     while (t >= 0) {
-        uint32_t s = ld_volatile(status + t * stride + slot);
-        if ((s & ST_FLAGS) == 0) {
+        uint32_t s[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) s[w] = (t - w >= 0) ? ld_volatile(status + (t - w) * stride + slot) : ST_INC;
+        int used = 0;
+        bool done = false, stalled = false;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            if (!done && !stalled) {
+                if ((s[w] & ST_FLAGS) == 0) {
+                    stalled = true;
+                } else {
+                    excl += s[w] & ST_COUNT;
+                    ++used;
+                    if ((s[w] & ST_FLAGS) == ST_INC) done = true;
+                }
+            }
+        }
+        if (done) break;
+        t -= used;
+        if (stalled) {
             if (++spins > SPIN_LIMIT) {
                 atomicOr(err, ERR_TIMEOUT);
                 break;
             }
-            __nanosleep(64);
-            continue;
+            __nanosleep(32);
         }
-        excl += s & ST_COUNT;
-        if ((s & ST_FLAGS) == ST_INC) break;
-        --t;
     }
     return excl;
 }
@@ -97,6 +117,208 @@ __device__ __forceinline__ uint32_t block_excl_scan256(uint32_t v, uint32_t* s_w
     uint32_t excl = x - v + (warp > 0 ? s_warp[warp - 1] : 0u);
     if (total) *total = s_warp[7];
     __syncthreads();
+    return excl;
+}
+
+// Vector look-backs over slot-major status rows (row[tile], rows padded to
+// a multiple of 4 tiles and 16-byte aligned), so one 16-byte load reads 4
+// consecutive tiles' words.
+__device__ __forceinline__ uint4 ld_volatile_v4(const uint32_t* p) {
+    uint4 v;
+    asm volatile("ld.volatile.global.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+__device__ __forceinline__ uint32_t v4_get(const uint4& v, int e) {
+    return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
+}
+
+// One thread per slot: walk back from tile-1 reading 4*NV predecessor words
+// per round trip.  Returns the sum of the slot's counts over all earlier
+// tiles.  Bounded wait as lookback().
+template <int NV>
+__device__ __forceinline__ uint32_t lookback_row(const uint32_t* row, int64_t tile, int* err) {
+    uint32_t excl = 0;
+    int64_t hi = tile - 1;
+    uint32_t spins = 0;
+    while (hi >= 0) {
+        const int64_t c0 = hi >> 2;
+        uint4 v[NV];
+#pragma unroll
+        for (int i = 0; i < NV; ++i)
+            v[i] = (c0 - i >= 0) ? ld_volatile_v4(row + 4 * (c0 - i)) : make_uint4(ST_INC, ST_INC, ST_INC, ST_INC);
+        bool done = false, stalled = false;
+        int64_t next = 4 * (c0 - NV + 1) - 1;
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+#pragma unroll
+            for (int e = 3; e >= 0; --e) {
+                const int64_t te = 4 * (c0 - i) + e;
+                if (done || stalled || te > hi) continue;
+                const uint32_t w = v4_get(v[i], e);
+                if ((w & ST_FLAGS) == 0) {
+                    stalled = true;
+                    next = te;
+                } else {
+                    excl += w & ST_COUNT;
+                    if ((w & ST_FLAGS) == ST_INC) done = true;
+                }
+            }
+        }
+        if (done) break;
+        hi = next;
+        if (stalled) {
+            if (++spins > SPIN_LIMIT) {
+                atomicOr(err, ERR_TIMEOUT);
+                break;
+            }
+            __nanosleep(32);
+        }
+    }
+    return excl;
+}
+
+// A whole warp walks back one slot's row: lane l reads the 4 tiles of chunk
+// (hi/4 - l), so one round trip covers 128 predecessors.  Every lane returns
+// the same sum.  Bounded wait as lookback().
+__device__ __forceinline__ uint32_t warp_lookback_row(const uint32_t* row, int64_t tile, int* err) {
+    const int lane = threadIdx.x & 31;
+    uint32_t excl = 0;
+    int64_t hi = tile - 1;
+    uint32_t spins = 0;
+    while (hi >= 0) {
+        const int64_t c = (hi >> 2) - lane;
+        const uint4 v = c >= 0 ? ld_volatile_v4(row + 4 * c) : make_uint4(ST_INC, ST_INC, ST_INC, ST_INC);
+        uint32_t sum = 0;
+        bool inc = false, notready = false;
+#pragma unroll
+        for (int e = 3; e >= 0; --e) {
+            const int64_t te = 4 * c + e;
+            if (te > hi || inc || notready) continue;
+            const uint32_t w = v4_get(v, e);
+            if ((w & ST_FLAGS) == 0) {
+                notready = true;
+            } else {
+                sum += w & ST_COUNT;
+                if ((w & ST_FLAGS) == ST_INC) inc = true;
+            }
+        }
+        const uint32_t binc = __ballot_sync(0xffffffffu, inc);
+        const uint32_t bnr = __ballot_sync(0xffffffffu, notready);
+        const int L = binc ? __ffs(binc) - 1 : 32;  // nearest lane holding an inclusive prefix
+        const uint32_t upto = L >= 31 ? 0xffffffffu : ((2u << L) - 1u);
+        if (bnr & upto) {  // a word between us and that prefix is not published yet
+            if (++spins > SPIN_LIMIT) {
+                if (lane == 0) atomicOr(err, ERR_TIMEOUT);
+                break;
+            }
+            __nanosleep(32);
+            continue;
+        }
+        uint32_t part = (lane <= L) ? sum : 0u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        excl += part;
+        if (L < 32) break;
+        hi = 4 * ((hi >> 2) - 31) - 1;
+    }
+    return excl;
+}
+
+// Exclusive scan of one value per thread over an NT-thread block.
+template <int NT>
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* s_warp, uint32_t* total) {
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < NW ? s_warp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < NW) s_warp[lane] = w;
+    }
+    __syncthreads();
+    uint32_t excl = x - v + (warp > 0 ? s_warp[warp - 1] : 0u);
+    if (total) *total = s_warp[NW - 1];
+    __syncthreads();
+    return excl;
+}
+
+__host__ __device__ __forceinline__ int64_t pad4(int64_t x) { return (x + 3) & ~(int64_t)3; }
+
+// ---------------------------------------------- tile-major look-back
+// Each tile publishes a flag word (0 nothing, 1 aggregate, 2 inclusive) and
+// two count records: its own counts (aggregate) and, once known, the counts
+// of every tile up to and including itself (inclusive).  A record is written
+// before its flag (fence in between); a reader loads the flag, fences, then
+// the record.  Walking back, warp 0 reads 32 predecessor flags per round
+// trip; the nearest inclusive record plus the aggregates above it give the
+// exclusive prefix.  Records are rows of `nslot` words, so every slot's
+// read is coalesced across the block.
+constexpr uint32_t FLAG_AGG = 1u;
+constexpr uint32_t FLAG_INC = 2u;
+
+__device__ __forceinline__ void publish_flag(uint32_t* flags, int64_t tile, uint32_t f) {
+    __threadfence();
+    st_volatile(flags + tile, f);
+}
+
+// Called by the whole block (uniform control flow).  Thread `tid < nslot`
+// receives the exclusive prefix of slot tid in *excl.  AggT is the word type
+// of aggregate records.  s_ctl: one shared word.  Bounded wait.
+template <typename AggT>
+__device__ __forceinline__ uint32_t block_lookback(const uint32_t* flags, const AggT* aggrec, const uint32_t* increc,
+                                                   int nslot, int64_t tile, uint32_t* s_ctl, int* err,
+                                                   int stride = 0) {
+    if (stride == 0) stride = nslot;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t excl = 0;
+    int64_t hi = tile - 1;
+    uint32_t spins = 0;
+    while (hi >= 0) {
+        if (warp == 0) {
+            const int64_t u = hi - lane;
+            const uint32_t f = u >= 0 ? ld_volatile(flags + u) : FLAG_INC;
+            const uint32_t binc = __ballot_sync(0xffffffffu, f == FLAG_INC && u >= 0);
+            const uint32_t bnr = __ballot_sync(0xffffffffu, f == 0u);
+            const int L = binc ? __ffs(binc) - 1 : 32;
+            const uint32_t upto = L >= 31 ? 0xffffffffu : ((2u << L) - 1u);
+            if (lane == 0) *s_ctl = (bnr & upto) ? 0xffffffffu : (uint32_t)L;
+        }
+        __syncthreads();
+        const uint32_t L = *s_ctl;
+        __syncthreads();
+        if (L == 0xffffffffu) {
+            if (++spins > SPIN_LIMIT) {
+                if (tid == 0) atomicOr(err, ERR_TIMEOUT);
+                break;
+            }
+            __nanosleep(32);
+            continue;
+        }
+        __threadfence();
+        if (tid < nslot) {
+            const int nagg = (int)(L < 32 ? L : 32);
+            for (int i = 0; i < nagg; ++i) {
+                const int64_t u = hi - i;
+                if (u >= 0) excl += (uint32_t)(*reinterpret_cast<const volatile AggT*>(aggrec + u * stride + tid));
+            }
+            if (L < 32) excl += *reinterpret_cast<const volatile uint32_t*>(increc + (hi - (int64_t)L) * stride + tid);
+        }
+        if (L < 32) break;
+        hi -= 32;
+    }
     return excl;
 }
 
@@ -196,6 +418,49 @@ struct FinUnit {
     int32_t cloud;
     int32_t seg;  // segment index at level lam of the cloud
 };
+
+// One cloud's share of a level step: its tiles are tile_begin ..
+// tile_begin + ceil(m / tile) - 1 of the launch.
+struct LevelJob {
+    int32_t cloud;
+    int32_t lev_in, lev_out;
+    int32_t src_buf, dst_buf;
+    int32_t write_med;
+    int64_t tile_begin;
+};
+
+// Index of the last entry of a non-decreasing prefix array <= x.
+__device__ __forceinline__ int last_le(const int64_t* __restrict__ a, int n, int64_t x) {
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] <= x) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Tile t of a level step, from the step's jobs (tile_begin ascending).
+__device__ __forceinline__ LevelTile job_tile(const LevelJob* __restrict__ jobs, int njobs, int t, int tile,
+                                              const CloudDev* __restrict__ clouds) {
+    int lo = 0, hi = njobs;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (jobs[mid].tile_begin <= t) lo = mid; else hi = mid;
+    }
+    const LevelJob J = jobs[lo];
+    LevelTile T;
+    T.cloud = J.cloud;
+    T.lev_in = J.lev_in;
+    T.lev_out = J.lev_out;
+    T.src_buf = J.src_buf;
+    T.dst_buf = J.dst_buf;
+    T.write_med = J.write_med;
+    T.pos0 = (int64_t)(t - J.tile_begin) * tile;
+    const int64_t rem = clouds[J.cloud].m - T.pos0;
+    T.npos = (int32_t)(rem < tile ? rem : tile);
+    T.first = T.pos0 == 0;
+    return T;
+}
 
 // rec[d][p]: plane p (ranks in super-key-p order) of index array d.
 struct AllPlanes {

@@ -80,23 +80,36 @@ __global__ void __launch_bounds__(256) k_transform(const T* __restrict__ coords,
 //   MODE KEY_DIRECT: key = key_src[pos]           (a key plane, identity order)
 //   MODE KEY_GATHER: key = key_src[gidx[pos]]     (a key plane, by tuple id)
 // Payload planes move with the key; a null source emits the source position.
-// hist_row holds the 256 digit counts over all elements of this sort.
-template <typename KW, int MODE, int IPT>
-__global__ void __launch_bounds__(SORT_THREADS) k_sort_pass(const int64_t* __restrict__ count_ptr,
-                                                            const KW* __restrict__ key_src,
-                                                            const uint32_t* __restrict__ gidx,
-                                                            KW* __restrict__ key_dst, PayloadArgs pay,
-                                                            const uint32_t* __restrict__ hist_row, int shift,
-                                                            uint32_t* __restrict__ status,
-                                                            uint32_t* __restrict__ tile_ctr,
-                                                            int* __restrict__ err, int64_t gather_limit) {
+// digit_base holds, per digit, the number of elements of this sort with a
+// smaller digit (exclusive prefix of the digit histogram).
+// Tile pipeline (8192 keys, 512 threads): load; warp multisplit ranking
+// (equal-digit lane masks from 9 ballots, per-warp digit counters advanced
+// by one shared-memory atomic per group); publish the tile's digit counts;
+// tile-local prefix and staging of keys in digit order; look-back over
+// tile-major count records; then every digit's run is written with
+// consecutive addresses, keys first, then each payload plane.
+struct SortStatus {
+    uint32_t* flags;     // [tiles]
+    uint16_t* aggrec;    // [tiles][256]
+    uint32_t* increc;    // [tiles][256]
+};
+
+template <typename KW, int MODE>
+__global__ void __launch_bounds__(SORT_THREADS, 2)
+    k_sort_pass(const int64_t* __restrict__ count_ptr, const KW* __restrict__ key_src,
+                const uint32_t* __restrict__ gidx, KW* __restrict__ key_dst, const __grid_constant__ PayloadArgs pay,
+                const uint32_t* __restrict__ digit_base, int shift, SortStatus st,
+                uint32_t* __restrict__ tile_ctr, int* __restrict__ err, int64_t gather_limit) {
+    constexpr int IPT = sizeof(KW) == 8 ? SORT_IPT / 2 : SORT_IPT;  // 64-bit keys: half tiles
     constexpr int TILE = SORT_THREADS * IPT;
     __shared__ uint32_t s_wc[SORT_WARPS][RADIX];
     __shared__ uint32_t s_goff[RADIX];
     __shared__ uint32_t s_tstart[RADIX];
     __shared__ uint32_t s_warp[SORT_WARPS];
-    __shared__ uint32_t s_tile;
+    __shared__ uint32_t s_tile, s_ctl;
+    // s_dyn: [TILE * 8 bytes] keys, later dest | values;  then s_slot [TILE] u16
     extern __shared__ __align__(16) unsigned char s_dyn[];
+    uint16_t* s_slot = reinterpret_cast<uint16_t*>(s_dyn + (size_t)TILE * 8);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
@@ -125,53 +138,62 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort_pass(const int64_t* __res
             }
         }
     }
-    // warp-level multisplit: rank among equal digits of this warp, in order
+    // warp multisplit: lanes with equal digits (9 bits: 8 digit bits and the
+    // out-of-range marker) found by ballots; ranks follow item order
 #pragma unroll
     for (int j = 0; j < IPT; ++j) {
         const int o = wbase + j * 32 + lane;
         const uint32_t d = (o < tile_n) ? (uint32_t)((key[j] >> shift) & 255u) : (uint32_t)RADIX;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        uint32_t before = 0;
-        if (d < RADIX) before = s_wc[warp][d];
-        rank[j] = before + __popc(peers & lanemask_lt());
-        __syncwarp();
-        if (d < RADIX && lane == __ffs(peers) - 1) s_wc[warp][d] = before + __popc(peers);
-        __syncwarp();
-    }
-    __syncthreads();
-    // thread tid owns digit tid: exclusive prefix over warps, tile count
-    uint32_t cnt = 0;
+        uint32_t peers = 0xffffffffu;
 #pragma unroll
-    for (int w = 0; w < SORT_WARPS; ++w) {
-        const uint32_t c = s_wc[w][tid];
-        s_wc[w][tid] = cnt;
-        cnt += c;
+        for (int bit = 0; bit < 9; ++bit) {
+            const uint32_t bb = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
+            peers &= ((d >> bit) & 1u) ? bb : ~bb;
+        }
+        const int leader = __ffs(peers) - 1;
+        uint32_t old = 0;
+        if (lane == leader && d < RADIX) old = atomicAdd(&s_wc[warp][d], (uint32_t)__popc(peers));
+        old = __shfl_sync(0xffffffffu, old, leader);
+        rank[j] = old + __popc(peers & lanemask_lt());
     }
-    uint32_t* st = status + tile * RADIX;
-    st_volatile(st + tid, (tile == 0 ? ST_INC : ST_AGG) | cnt);
-    const uint32_t hbase = block_excl_scan256(hist_row[tid], s_warp, nullptr);
-    const uint32_t tstart = block_excl_scan256(cnt, s_warp, nullptr);
-    uint32_t excl = 0;
-    if (tile > 0) {
-        excl = lookback(status, tile, RADIX, tid, err);
-        st_volatile(st + tid, ST_INC | ((excl + cnt) & ST_COUNT));
-    }
-    s_tstart[tid] = tstart;
-    s_goff[tid] = hbase + excl - tstart;  // dest = s_goff[digit] + slot (mod 2^32)
     __syncthreads();
-
-    // stage keys in tile order (sorted by digit), then write runs out
+    // threads < 256 own digit tid: tile count, published at once
+    uint32_t cnt = 0;
+    if (tid < RADIX) {
+#pragma unroll
+        for (int w = 0; w < SORT_WARPS; ++w) {
+            const uint32_t c = s_wc[w][tid];
+            s_wc[w][tid] = cnt;
+            cnt += c;
+        }
+        if (tile == 0) st.increc[tid] = cnt;
+        else st.aggrec[tile * RADIX + tid] = (uint16_t)cnt;
+    }
+    __syncthreads();
+    if (tid == 0) publish_flag(st.flags, tile, tile == 0 ? FLAG_INC : FLAG_AGG);
+    const uint32_t tstart = block_excl_scan<SORT_THREADS>(cnt, s_warp, nullptr);
+    if (tid < RADIX) s_tstart[tid] = tstart;
+    __syncthreads();
+    // stage keys in tile order (sorted by digit); remember each item's slot
     KW* s_key = reinterpret_cast<KW*>(s_dyn);
-    uint32_t slot[IPT];
 #pragma unroll
     for (int j = 0; j < IPT; ++j) {
         const int o = wbase + j * 32 + lane;
         if (o < tile_n) {
             const uint32_t d = (uint32_t)((key[j] >> shift) & 255u);
-            slot[j] = s_tstart[d] + s_wc[warp][d] + rank[j];
-            s_key[slot[j]] = key[j];
+            const uint32_t slot = s_tstart[d] + s_wc[warp][d] + rank[j];
+            s_key[slot] = key[j];
+            s_slot[o] = (uint16_t)slot;
         }
     }
+    uint32_t excl = 0;
+    if (tile > 0) {
+        excl = block_lookback<uint16_t>(st.flags, st.aggrec, st.increc, RADIX, tile, &s_ctl, err);
+        if (tid < RADIX) st.increc[tile * RADIX + tid] = excl + cnt;
+        __syncthreads();
+        if (tid == 0) publish_flag(st.flags, tile, FLAG_INC);
+    }
+    if (tid < RADIX) s_goff[tid] = digit_base[tid] + excl - tstart;  // dest = s_goff[digit] + slot (mod 2^32)
     __syncthreads();
     // A destination outside [0, count) can only come from an inconsistent
     // histogram; it is reported and never written.
@@ -191,26 +213,37 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort_pass(const int64_t* __res
             }
         }
     }
-    uint32_t* s_val = reinterpret_cast<uint32_t*>(s_dyn);
+    if (pay.n == 0) return;
+    __syncthreads();
+    uint32_t* s_dest = reinterpret_cast<uint32_t*>(s_dyn);
+    uint32_t* s_val = reinterpret_cast<uint32_t*>(s_dyn + (size_t)TILE * 4);
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) s_dest[i * SORT_THREADS + tid] = dest[i];
     for (int p = 0; p < pay.n; ++p) {
-        __syncthreads();
         const uint32_t* src = pay.src[p];
 #pragma unroll
         for (int j = 0; j < IPT; ++j) {
             const int o = wbase + j * 32 + lane;
             if (o < tile_n) {
                 const int64_t pos = base + o;
-                s_val[slot[j]] = src ? src[pos] : (uint32_t)pos;
+                s_val[s_slot[o]] = src ? src[pos] : (uint32_t)pos;
             }
         }
         __syncthreads();
         uint32_t* dst = pay.dst[p];
-#pragma unroll
-        for (int i = 0; i < IPT; ++i) {
-            const int s = i * SORT_THREADS + tid;
-            if (s < tile_n && dest[i] != 0xffffffffu) dst[dest[i]] = s_val[s];
+        for (int s = tid; s < tile_n; s += SORT_THREADS) {
+            const uint32_t dd = s_dest[s];
+            if (dd != 0xffffffffu) dst[dd] = s_val[s];
         }
+        __syncthreads();
     }
+}
+
+// Exclusive prefix of each 256-bin histogram row: bases[r][d].
+__global__ void k_digit_bases(const uint32_t* __restrict__ hist, uint32_t* __restrict__ bases) {
+    __shared__ uint32_t s_warp[8];
+    const int r = blockIdx.x;
+    bases[r * RADIX + threadIdx.x] = block_excl_scan256(hist[r * RADIX + threadIdx.x], s_warp, nullptr);
 }
 
 // ---------------------------------------------------------------- dedup
@@ -230,7 +263,7 @@ __global__ void __launch_bounds__(256) k_dedup(int64_t n, const KW* __restrict__
     constexpr int IPT = 16;
     constexpr int TILE = 256 * IPT;
     constexpr int D = sizeof(KW);
-    __shared__ uint32_t s_tile, s_excl, s_wsum[8], s_total;
+    __shared__ uint32_t s_tile, s_excl, s_wsum[8], s_ctl;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
     __syncthreads();
@@ -285,19 +318,31 @@ __global__ void __launch_bounds__(256) k_dedup(int64_t n, const KW* __restrict__
     }
     if (lane == 0) s_wsum[warp] = wcount;
     __syncthreads();
+    uint32_t acc = 0;
+    for (int w = 0; w < 8; ++w) acc += s_wsum[w];
+    // status: flags [tiles] | aggregate [tiles] | inclusive [tiles]
+    const int64_t ntiles = (n + TILE - 1) / TILE;
+    uint32_t* flags = status;
+    uint32_t* aggrec = status + pad4(ntiles);
+    uint32_t* increc = aggrec + pad4(ntiles);
     if (tid == 0) {
-        uint32_t acc = 0;
+        if (tile == 0) increc[0] = acc; else aggrec[tile] = acc;
+        publish_flag(flags, tile, tile == 0 ? FLAG_INC : FLAG_AGG);
+    }
+    uint32_t excl = 0;
+    if (tile > 0) {
+        excl = block_lookback<uint32_t>(flags, aggrec, increc, 1, tile, &s_ctl, err);
+        if (tid == 0) {
+            increc[tile] = excl + acc;
+            publish_flag(flags, tile, FLAG_INC);
+        }
+    }
+    if (tid == 0) {
+        uint32_t run = 0;
         for (int w = 0; w < 8; ++w) {
             const uint32_t c = s_wsum[w];
-            s_wsum[w] = acc;
-            acc += c;
-        }
-        s_total = acc;
-        st_volatile(status + tile, (tile == 0 ? ST_INC : ST_AGG) | acc);
-        uint32_t excl = 0;
-        if (tile > 0) {
-            excl = lookback(status, tile, 1, 0, err);
-            st_volatile(status + tile, ST_INC | ((excl + acc) & ST_COUNT));
+            s_wsum[w] = run;
+            run += c;
         }
         s_excl = excl;
         if (base + tile_n == n) *m_out = (int64_t)excl + acc;
@@ -312,26 +357,37 @@ __global__ void __launch_bounds__(256) k_dedup(int64_t n, const KW* __restrict__
 }
 
 // -------------------------------------------------------------- records
-// From array 1's complete rank vectors (rec[1][p] for p != 1; its own rank
-// is the position), fill every plane of every array that the chain sorts
-// did not write: rec[d][d][i] = i, and rec[d][p][rank_d] = rank_p by scatter.
-// Bits 8d..8d+7 of present_bits: the planes already written for array d.
-__global__ void __launch_bounds__(256) k_records(const int64_t* __restrict__ m_ptr, int k,
-                                                 AllPlanes rec, uint64_t present_bits) {
+// rec[d][p][i]: rank in super-key-p order of the tuple at position i of index
+// array d.  After deduplication super keys are unique, so comparing super
+// keys equals comparing these ranks.  The chain sorts write most planes,
+// the permutation below the rest; an array's own plane is its position.
+__global__ void __launch_bounds__(256) k_own_ranks(const int64_t* __restrict__ m_ptr, int k, AllPlanes rec) {
     const int64_t m = *m_ptr;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t v[MAXK];
-        for (int p = 0; p < k; ++p) v[p] = (p == 1) ? (uint32_t)i : rec.p[1][p][i];
-        for (int d = 0; d < k; ++d) {
-            const uint32_t present = (uint32_t)(present_bits >> (d * MAXK)) & 0xffu;
-            if (!((present >> d) & 1u)) rec.p[d][d][i] = (uint32_t)i;
-            if (d == 1) continue;
-            const uint32_t r = v[d];
-            if ((int64_t)r >= m) continue;  // inconsistent ranks: never written out of range
-            for (int p = 0; p < k; ++p)
-                if (p != d && !((present >> p) & 1u)) rec.p[d][p][r] = v[p];
-        }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+        for (int d = 0; d < k; ++d) rec.p[d][d][i] = (uint32_t)i;
+}
+
+// Permutation by destination index, in two streaming steps: a sort pass on
+// the top bits of the destination (digit bases below) groups the elements
+// into destination ranges small enough to stay in L2, then k_perm_scatter
+// writes each element to its destination.  Destinations are a permutation
+// of [0, m), so range d holds min(2^shift, m - d * 2^shift) elements.
+__global__ void k_perm_bases(const int64_t* __restrict__ m_ptr, int shift, uint32_t* __restrict__ bases) {
+    __shared__ uint32_t s_warp[8];
+    const int64_t m = *m_ptr;
+    const int64_t lo = (int64_t)threadIdx.x << shift;
+    const int64_t c = m - lo < 0 ? 0 : (m - lo > ((int64_t)1 << shift) ? ((int64_t)1 << shift) : m - lo);
+    bases[threadIdx.x] = block_excl_scan256((uint32_t)c, s_warp, nullptr);
+}
+
+__global__ void __launch_bounds__(256) k_perm_scatter(const int64_t* __restrict__ m_ptr,
+                                                      const uint32_t* __restrict__ dest, int nval,
+                                                      const __grid_constant__ PayloadArgs pa) {
+    const int64_t m = *m_ptr;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t d = dest[i];
+        if ((int64_t)d >= m) continue;  // inconsistent input: never written out of range
+        for (int j = 0; j < nval; ++j) pa.dst[j][d] = pa.src[j][i];
     }
 }
 
@@ -389,22 +445,40 @@ cudaError_t launch_transform(int dtype, const void* coords, int64_t n, int k, vo
     return cudaGetLastError();
 }
 
-constexpr int SORT_IPT = 16;
-int sort_tile() { return SORT_THREADS * SORT_IPT; }
+int sort_tile(int key64) { return key64 ? SORT_TILE / 2 : SORT_TILE; }
+// Status words of one pass: flags [tiles] | aggregate records [tiles][256]
+// u16 | inclusive records [tiles][256] u32.  Only the flags need zeroing.
+// Sized for the smaller (64-bit key) tiles, which covers both key widths.
+static int64_t sort_tiles_max(int64_t max_count) { return (max_count + SORT_TILE / 2 - 1) / (SORT_TILE / 2); }
+size_t sort_status_words(int64_t max_count) {
+    const int64_t tiles = sort_tiles_max(max_count);
+    return (size_t)pad4(tiles) + (size_t)tiles * RADIX / 2 + (size_t)tiles * RADIX;
+}
+size_t sort_flag_words(int64_t max_count) { return (size_t)pad4(sort_tiles_max(max_count)); }
 
 cudaError_t launch_sort_pass(int key64, int mode, const int64_t* count_ptr, int64_t max_count,
                              const void* key_src, const uint32_t* gidx, void* key_dst,
-                             const PayloadArgs& pay, const uint32_t* hist_row, int shift,
+                             const PayloadArgs& pay, const uint32_t* digit_base, int shift,
                              uint32_t* status, uint32_t* tile_ctr, int* err, cudaStream_t s) {
     const int64_t gather_limit = max_count;  // tuple ids index planes of max_count entries
-    const int tile = SORT_THREADS * SORT_IPT;
+    const int tile = sort_tile(key64);
     const int64_t tiles = (max_count + tile - 1) / tile;
     if (tiles == 0) return cudaSuccess;
-    const size_t smem = (size_t)tile * (key64 ? 8 : 4);
-#define KD_SORT_LAUNCH(KW, MODE)                                                                      \
-    k_sort_pass<KW, MODE, SORT_IPT><<<(unsigned)tiles, SORT_THREADS, smem, s>>>(                    \
-        count_ptr, (const KW*)key_src, gidx, (KW*)key_dst, pay, hist_row, shift, status, tile_ctr, err,  \
-        gather_limit)
+    const int64_t tmax = sort_tiles_max(max_count);
+    SortStatus st;
+    st.flags = status;
+    st.aggrec = reinterpret_cast<uint16_t*>(status + pad4(tmax));
+    st.increc = status + pad4(tmax) + tmax * RADIX / 2;
+    const size_t smem = (size_t)tile * 8 + (size_t)tile * 2;
+#define KD_SORT_LAUNCH(KW, MODE)                                                                          \
+    do {                                                                                                  \
+        auto kf = k_sort_pass<KW, MODE>;                                                                  \
+        cudaError_t e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        if (e != cudaSuccess) return e;                                                                   \
+        kf<<<(unsigned)tiles, SORT_THREADS, smem, s>>>(count_ptr, (const KW*)key_src, gidx, (KW*)key_dst, \
+                                                       pay, digit_base, shift, st, tile_ctr, err,         \
+                                                       gather_limit);                                     \
+    } while (0)
     if (key64) {
         if (mode == KEY_DIRECT) KD_SORT_LAUNCH(uint64_t, KEY_DIRECT);
         else if (mode == KEY_GATHER) KD_SORT_LAUNCH(uint64_t, KEY_GATHER);
@@ -415,6 +489,12 @@ cudaError_t launch_sort_pass(int key64, int mode, const int64_t* count_ptr, int6
         else KD_SORT_LAUNCH(uint32_t, KEY_BUF);
     }
 #undef KD_SORT_LAUNCH
+    return cudaGetLastError();
+}
+
+cudaError_t launch_digit_bases(const uint32_t* hist, int nrows, uint32_t* bases, cudaStream_t s) {
+    if (nrows == 0) return cudaSuccess;
+    k_digit_bases<<<nrows, RADIX, 0, s>>>(hist, bases);
     return cudaGetLastError();
 }
 
@@ -435,10 +515,21 @@ cudaError_t launch_dedup(int key64, int64_t n, const void* key0, const uint32_t*
     return cudaGetLastError();
 }
 
-cudaError_t launch_records(const int64_t* m_ptr, int64_t max_m, int k, const AllPlanes& rec,
-                           uint64_t present_bits, cudaStream_t s) {
+cudaError_t launch_own_ranks(const int64_t* m_ptr, int64_t max_m, int k, const AllPlanes& rec, cudaStream_t s) {
     if (max_m == 0) return cudaSuccess;
-    k_records<<<grid_for(max_m, 256, 152 * 16), 256, 0, s>>>(m_ptr, k, rec, present_bits);
+    k_own_ranks<<<grid_for(max_m, 256, 152 * 16), 256, 0, s>>>(m_ptr, k, rec);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_perm_bases(const int64_t* m_ptr, int shift, uint32_t* bases, cudaStream_t s) {
+    k_perm_bases<<<1, 256, 0, s>>>(m_ptr, shift, bases);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_perm_scatter(const int64_t* m_ptr, int64_t max_m, const uint32_t* dest, const PayloadArgs& pa,
+                                cudaStream_t s) {
+    if (max_m == 0) return cudaSuccess;
+    k_perm_scatter<<<grid_for(max_m, 256, 152 * 8), 256, 0, s>>>(m_ptr, dest, pa.n, pa);
     return cudaGetLastError();
 }
 

@@ -51,6 +51,11 @@ def parse():
     ap.add_argument("--n", type=int, default=N_POINTS, help="points per cloud (default 2^26)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1 << 21, help="oracle sample size (points)")
+    ap.add_argument("--mode", default="plain", choices=["plain", "batched", "served"],
+                    help="plain: the 2^26 build (default line); batched: 4096 uneven clouds in one call "
+                         "vs per-cloud calls; served: a Poisson request stream through kd_submit")
+    ap.add_argument("--clouds", type=int, default=4096)
+    ap.add_argument("--requests", type=int, default=2000)
     return ap.parse_args()
 
 
@@ -185,9 +190,108 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_batched(args):
+    """4096 clouds, sizes floor(2^U(6,16)), float32 unit cube, 0.5% duplicates:
+    one kd_build_batch call vs one kd_presort + kd_build per cloud."""
+    import torch
+    import kdgen
+    from paper_1410_5420_gb300 import api
+    clouds = kdgen.batch_clouds(count=args.clouds, seed=4)
+    pts = sum(c.shape[0] for c in clouds)
+    dev = [torch.from_numpy(c).cuda() for c in clouds]
+    stream = torch.cuda.current_stream()
+    ctx = api.kd_create(0, stream=stream)
+
+    def batched():
+        return api.kd_build_batch(ctx, dev)
+
+    def plain():
+        return [api.build_tree(ctx, x) for x in dev]
+
+    out = {}
+    for name, fn, reps in (("batched", batched, args.steps), ("plain_per_cloud", plain, 1)):
+        for _ in range(max(1, min(args.warmup, 2))):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            res = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[name] = {"ms": ms, "points_per_s": pts / (ms / 1000.0)}
+    same = all(torch.equal(a["node_tuple"], b["node_tuple"]) for a, b in zip(batched(), plain()))
+    line = {"metric": METRIC, "mode": "batched", "value": out["batched"]["points_per_s"], "unit": UNIT,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["batched"]["ms"],
+            "higher_is_better": True, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"batched: {args.clouds} clouds, sizes floor(2^U(6,16)), k=3 float32 unit "
+                                   f"cube, 0.5% duplicates (seed 4)", "points": pts},
+            "plain_per_cloud": out["plain_per_cloud"], "trees_identical": bool(same),
+            "speedup_vs_plain": out["batched"]["points_per_s"] / out["plain_per_cloud"]["points_per_s"]}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def run_served(args):
+    """Poisson stream of build requests through kd_submit / kd_wait: sizes
+    log-uniform in [2^8, 2^16] (scaled from 2^20), k in {2,3,4}, int32 or
+    float32 mixture; arrival rate 0.8x the measured serial plain throughput."""
+    import threading
+    import torch
+    import kdgen
+    from paper_1410_5420_gb300 import api
+    reqs = kdgen.serving_requests(count=args.requests, seed=5, lo_log2=8.0, hi_log2=16.0)
+    clouds = [kdgen.serving_cloud(*r) for r in reqs]
+    pts = sum(c.shape[0] for c in clouds)
+    ctx = api.kd_create(0, mem_budget_bytes=64 << 30)
+    # serial plain builds (host in, host out) on the same GPU
+    for c in clouds[:20]:
+        api.build_tree(ctx, c)
+    t0 = time.perf_counter()
+    for c in clouds:
+        api.build_tree(ctx, c)
+    serial_s = time.perf_counter() - t0
+    serial_pps = pts / serial_s
+    rate = 0.8 * len(clouds) / serial_s
+    arrivals = kdgen.poisson_arrivals(len(clouds), rate, seed=5)
+    tickets = [None] * len(clouds)
+    t0 = time.perf_counter()
+    for i, c in enumerate(clouds):
+        delay = arrivals[i] - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        tickets[i] = api.kd_submit(ctx, c)
+    for t in tickets:
+        api.kd_wait(ctx, t)
+    served_s = time.perf_counter() - t0
+    st = api.kd_serving_stats(ctx)
+    # saturation: everything submitted at once
+    t1 = time.perf_counter()
+    ts = [api.kd_submit(ctx, c) for c in clouds]
+    for t in ts:
+        api.kd_wait(ctx, t)
+    sat_s = time.perf_counter() - t1
+    line = {"metric": METRIC, "mode": "served", "value": pts / sat_s, "unit": UNIT, "n_gpus": 1,
+            "higher_is_better": True, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"served: {len(clouds)} Poisson requests, sizes log-U[2^8,2^16], k in {{2,3,4}}, "
+                                   f"int32 U[0,2^24) or float32 mixture (seed 5)", "points": pts,
+                       "rate_per_s": rate},
+            "poisson": {"points_per_s": pts / served_s, "p50_us": st["p50_us"], "p99_us": st["p99_us"],
+                        "completed": st["completed"]},
+            "saturation_points_per_s": pts / sat_s, "serial_plain_points_per_s": serial_pps,
+            "speedup_vs_serial_plain": (pts / sat_s) / serial_pps}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.mode != "plain" and args.impl == "gb300":
+        if rank == 0:
+            (run_batched if args.mode == "batched" else run_served)(args)
+        return
     if world > 1:
         import torch.distributed as dist
         backend = "nccl" if args.impl == "gb300" else "gloo"

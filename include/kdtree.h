@@ -134,10 +134,14 @@ kd_status kd_build_batch(kd_ctx *ctx, const kd_cloud *clouds, int count, kd_tree
 
 /*
  * Serving: enqueue one build request.  The coordinates are copied before
- * the call returns; out's arrays must stay valid until kd_wait reports the
- * ticket done.  A background scheduler admits queued requests while
- * earlier ones run, within cfg->mem_budget_bytes, and co-batches requests of
- * equal k and dtype.  KD_EBUSY when the queue is full.
+ * the call returns.  *out (host arrays; on_device must be 0) must stay
+ * valid until kd_wait reports the ticket done: the arrays receive the tree
+ * and out->m / out->root are set on completion.  Two worker threads, each
+ * with its own stream and half of cfg->mem_budget_bytes, take batches from
+ * the queue head (requests of equal k and dtype, within the budget): work
+ * admitted while another batch runs overlaps it on the device.  KD_EBUSY
+ * when the queue is full.  Each served tree equals the tree of the same
+ * cloud built alone.
  */
 kd_status kd_submit(kd_ctx *ctx, const kd_cloud *cloud, kd_tree *out, kd_ticket *ticket);
 

@@ -111,18 +111,18 @@ struct kd_ctx {
     // pinned host scratch for small uploads
     void* pinned = nullptr;
     size_t pinned_bytes = 0;
-    // serving
-    std::thread server;
+    // serving (kd_submit / kd_wait): worker threads, each with a sub-context
+    kd_config cfg{};
+    std::vector<std::thread> workers;
+    std::vector<kd_ctx*> worker_ctx;
     std::mutex qmu;
     std::condition_variable qcv, donecv;
     std::deque<std::shared_ptr<Request>> queue;
     std::unordered_map<kd_ticket, std::shared_ptr<Request>> tickets;
     bool stopping = false;
-    bool server_started = false;
     kd_ticket next_ticket = 1;
     std::vector<double> latencies_us;
     int64_t completed = 0;
-    size_t serve_in_flight_bytes = 0;
 };
 
 namespace {
@@ -131,7 +131,9 @@ struct Request {
     kd_cloud cloud{};
     std::vector<unsigned char> coords;  // host copy
     kd_tree out{};
+    kd_tree* user_out = nullptr;  // receives m and root when the request completes
     kd_status status = KD_OK;
+    std::string error;
     bool done = false;
     std::chrono::steady_clock::time_point t_submit, t_done;
     size_t est_bytes = 0;
@@ -916,6 +918,98 @@ kd_status build_batch(kd_ctx* ctx, kd_presorted* H, kd_tree* outs) {
     return KD_OK;
 }
 
+// ---------------------------------------------------------------- serving
+constexpr size_t SERVE_QUEUE_MAX = 1 << 20;
+constexpr int SERVE_WORKERS = 2;              // batches in flight on the device at once
+constexpr int64_t SERVE_BATCH_POINTS = 1 << 26;
+constexpr int SERVE_BATCH_CLOUDS = 8192;
+
+// Device bytes a request needs while it is built (presort buffers, rank
+// records and the build's ping-pong copies), with slack for status words.
+size_t serve_estimate(int64_t n, int k, int dtype) {
+    const size_t s = dtype_size(dtype), w = dtype == KD_I64 ? 8 : 4;
+    const size_t per = k * s + k * w + 2 * w + 8 + 8 * (k + 1) + 4 + 12 * (size_t)k * k + 64;
+    return (size_t)n * per + (1u << 16);
+}
+
+void serve_worker(kd_ctx* ctx, kd_ctx* wctx) {
+    const size_t budget = wctx->budget;
+    for (;;) {
+        std::vector<std::shared_ptr<Request>> batch;
+        {
+            std::unique_lock<std::mutex> lk(ctx->qmu);
+            ctx->qcv.wait(lk, [&] { return ctx->stopping || !ctx->queue.empty(); });
+            if (ctx->stopping && ctx->queue.empty()) return;
+            // admit from the queue head: same k and dtype, within this
+            // worker's memory budget and the batch caps
+            const int k = ctx->queue.front()->cloud.k, dt = ctx->queue.front()->cloud.dtype;
+            size_t bytes = 0;
+            int64_t pts = 0;
+            for (auto it = ctx->queue.begin(); it != ctx->queue.end();) {
+                const auto& r = *it;
+                if (r->cloud.k != k || r->cloud.dtype != dt) {
+                    ++it;
+                    continue;
+                }
+                if (!batch.empty() && ((budget && bytes + r->est_bytes > budget) ||
+                                       pts + r->cloud.n > SERVE_BATCH_POINTS ||
+                                       (int)batch.size() >= SERVE_BATCH_CLOUDS))
+                    break;
+                bytes += r->est_bytes;
+                pts += r->cloud.n;
+                batch.push_back(r);
+                it = ctx->queue.erase(it);
+            }
+        }
+        std::vector<kd_cloud> clouds;
+        std::vector<kd_tree> outs;
+        for (auto& r : batch) {
+            clouds.push_back(r->cloud);
+            outs.push_back(r->out);
+        }
+        kd_status st = kd_build_batch(wctx, clouds.data(), (int)clouds.size(), outs.data());
+        const std::string err = st == KD_OK ? std::string() : std::string(kd_last_error(wctx));
+        const auto now = std::chrono::steady_clock::now();
+        {
+            std::lock_guard<std::mutex> lk(ctx->qmu);
+            for (size_t i = 0; i < batch.size(); ++i) {
+                auto& r = batch[i];
+                r->status = st;
+                r->error = err;
+                if (st == KD_OK) {
+                    r->out.m = outs[i].m;
+                    r->out.root = outs[i].root;
+                    r->user_out->m = outs[i].m;
+                    r->user_out->root = outs[i].root;
+                }
+                r->t_done = now;
+                r->done = true;
+                ctx->latencies_us.push_back(
+                    std::chrono::duration<double, std::micro>(now - r->t_submit).count());
+                ctx->completed++;
+            }
+        }
+        ctx->donecv.notify_all();
+    }
+}
+
+kd_status start_serving(kd_ctx* ctx) {
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    if (!ctx->workers.empty()) return KD_OK;
+    for (int i = 0; i < SERVE_WORKERS; ++i) {
+        kd_config c = ctx->cfg;
+        c.cuda_stream = nullptr;  // each worker orders its batches on its own stream
+        c.debug = 0;
+        c.mem_budget_bytes = ctx->budget ? ctx->budget / SERVE_WORKERS : 0;
+        kd_ctx* w = nullptr;
+        kd_status st = kd_create(&w, &c);
+        if (st != KD_OK) return fail(ctx, st, "cannot create a serving worker context");
+        ctx->worker_ctx.push_back(w);
+    }
+    for (kd_ctx* w : ctx->worker_ctx) ctx->workers.emplace_back(serve_worker, ctx, w);
+    return KD_OK;
+}
+
 }  // namespace
 
 // =================================================================== C ABI
@@ -933,6 +1027,7 @@ kd_status kd_create(kd_ctx** out, const kd_config* cfg) {
     }
     if (c.device < 0 || c.device >= ndev) return KD_EINVAL;
     std::unique_ptr<kd_ctx> ctx(new kd_ctx());
+    ctx->cfg = c;
     ctx->device = c.device;
     ctx->budget = c.mem_budget_bytes;
     ctx->debug = c.debug;
@@ -1028,28 +1123,88 @@ kd_status kd_build_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_tree
 }
 
 kd_status kd_submit(kd_ctx* ctx, const kd_cloud* cloud, kd_tree* out, kd_ticket* ticket) {
-    (void)cloud;
-    (void)out;
-    (void)ticket;
-    return fail(ctx, KD_EINVAL, "serving is not available in this build");
+    if (!ctx || !cloud || !out || !ticket) return KD_EINVAL;
+    {
+        std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+        CKS(validate_cloud(ctx, cloud));
+        if (out->on_device) return fail(ctx, KD_EINVAL, "served trees are returned in host memory");
+        if (cloud->n > 0 && !out->node_tuple) return fail(ctx, KD_EINVAL, "node_tuple output is NULL");
+    }
+    auto r = std::make_shared<Request>();
+    r->cloud = *cloud;
+    const size_t bytes = (size_t)cloud->n * cloud->k * dtype_size(cloud->dtype);
+    r->coords.resize(bytes);
+    if (bytes) {
+        if (cloud->on_device) {
+            std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+            cudaSetDevice(ctx->device);
+            CK(cudaMemcpyAsync(r->coords.data(), cloud->coords, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+        } else {
+            memcpy(r->coords.data(), cloud->coords, bytes);
+        }
+    }
+    r->cloud.coords = r->coords.data();
+    r->cloud.on_device = 0;
+    r->out = *out;
+    r->user_out = out;
+    r->est_bytes = serve_estimate(cloud->n, cloud->k, cloud->dtype);
+    r->t_submit = std::chrono::steady_clock::now();
+    {
+        std::lock_guard<std::mutex> lk(ctx->qmu);
+        if (ctx->queue.size() >= SERVE_QUEUE_MAX) return fail(ctx, KD_EBUSY, "serving queue is full");
+        *ticket = ctx->next_ticket++;
+        ctx->tickets[*ticket] = r;
+        ctx->queue.push_back(r);
+    }
+    kd_status st = start_serving(ctx);
+    if (st != KD_OK) return st;
+    ctx->qcv.notify_one();
+    return KD_OK;
 }
 
 kd_status kd_wait(kd_ctx* ctx, kd_ticket ticket, int timeout_ms) {
-    (void)ticket;
-    (void)timeout_ms;
-    return fail(ctx, KD_EINVAL, "serving is not available in this build");
+    if (!ctx) return KD_EINVAL;
+    std::unique_lock<std::mutex> lk(ctx->qmu);
+    auto it = ctx->tickets.find(ticket);
+    if (it == ctx->tickets.end()) return fail(ctx, KD_EINVAL, "unknown ticket");
+    std::shared_ptr<Request> r = it->second;
+    auto ready = [&] { return r->done; };
+    if (timeout_ms < 0)
+        ctx->donecv.wait(lk, ready);
+    else if (!ctx->donecv.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready))
+        return fail(ctx, KD_ETIMEOUT, "request still pending");
+    ctx->tickets.erase(ticket);
+    if (r->status != KD_OK) ctx->last_error = r->error;
+    return r->status;
 }
 
 kd_status kd_serving_stats(kd_ctx* ctx, int64_t* completed, double* p50_us, double* p99_us) {
     if (!ctx) return KD_EINVAL;
+    std::lock_guard<std::mutex> lk(ctx->qmu);
+    std::vector<double> v = ctx->latencies_us;
+    std::sort(v.begin(), v.end());
+    auto pct = [&](double p) {
+        if (v.empty()) return 0.0;
+        size_t i = (size_t)std::min<double>(v.size() - 1, std::floor(p * (v.size() - 1) + 0.5));
+        return v[i];
+    };
     if (completed) *completed = ctx->completed;
-    if (p50_us) *p50_us = 0;
-    if (p99_us) *p99_us = 0;
+    if (p50_us) *p50_us = pct(0.50);
+    if (p99_us) *p99_us = pct(0.99);
     return KD_OK;
 }
 
 kd_status kd_destroy(kd_ctx* ctx) {
     if (!ctx) return KD_EINVAL;
+    {
+        std::lock_guard<std::mutex> lk(ctx->qmu);
+        ctx->stopping = true;
+    }
+    ctx->qcv.notify_all();
+    for (auto& t : ctx->workers)
+        if (t.joinable()) t.join();
+    for (kd_ctx* w : ctx->worker_ctx) kd_destroy(w);
     {
         std::lock_guard<std::recursive_mutex> lk(ctx->mu);
         cudaSetDevice(ctx->device);

@@ -60,29 +60,41 @@ __device__ __forceinline__ int tile_segments(int32_t pos0, int32_t npos, int32_t
     return ns;
 }
 
-// Route one element through levels lev_in .. lev_in+F-1: r[f] is its rank in
-// super key (lev_in + f) mod K.  Returns the digit (segment slot * 2^F +
-// bucket) and its final segment, or INV if it is the median of one of
-// these levels (a node: not copied).
-template <int K>
-__device__ __forceinline__ uint32_t route(const uint32_t (&r)[K], int F, int lev_in, int sj, int NB, int32_t a,
-                                          int32_t z, int32_t si, const uint32_t* __restrict__ medr, int64_t medr_off,
-                                          int32_t& flo, int32_t& fhi) {
-    uint32_t b = 0;
+// Medians a tile needs: for each of its level-lev_in segments j, the
+// medians of levels lev_in .. lev_in+F-1 below it, heap-indexed (node 1 is
+// the segment itself, children of node h are 2h and 2h+1).
+template <int NBMAX>
+__device__ __forceinline__ void load_tile_medians(uint32_t (*s_med)[NBMAX], int ns, const int32_t* segidx, int F,
+                                                  int lev_in, const uint32_t* __restrict__ medr, int64_t medr_off) {
+    const int per = (1 << F) - 1;
+    for (int e = threadIdx.x; e < ns * per; e += blockDim.x) {
+        const int j = e / per;
+        const int h = e - j * per + 1;
+        const int f = 31 - __clz(h);
+        const int64_t gseg = ((int64_t)segidx[j] << f) + (h - (1 << f));
+        s_med[j][h] = medr[medr_off + ((int64_t)1 << (lev_in + f)) - 1 + gseg];
+    }
+}
+
+// Route one element of segment slot sj through F levels: r[f] is its rank in
+// super key (lev_in + f) mod K.  Returns the digit (sj * 2^F + bucket) and
+// its final segment [flo, fhi], or INV if it is the median of one of these
+// levels (a node: not copied).
+template <int K, int NBMAX>
+__device__ __forceinline__ uint32_t route(const uint32_t (&r)[K], int F, int sj, int32_t a, int32_t z,
+                                          const uint32_t (*s_med)[NBMAX], int32_t& flo, int32_t& fhi) {
+    uint32_t h = 1;
 #pragma unroll
     for (int f = 0; f < K - 1; ++f) {
         if (f < F) {
-            const int L = lev_in + f;
             const int32_t mid = a + ((z - a) >> 1);
-            const uint32_t mv = medr[medr_off + ((int64_t)1 << L) - 1 + si];
+            const uint32_t mv = s_med[sj][h];
             if (r[f] < mv) {
                 z = mid - 1;
-                si = 2 * si;
-                b = 2 * b;
+                h = 2 * h;
             } else if (r[f] > mv) {
                 a = mid + 1;
-                si = 2 * si + 1;
-                b = 2 * b + 1;
+                h = 2 * h + 1;
             } else {
                 return INV;
             }
@@ -90,8 +102,12 @@ __device__ __forceinline__ uint32_t route(const uint32_t (&r)[K], int F, int lev
     }
     flo = a;
     fhi = z;
-    return (uint32_t)(sj * NB) + b;
+    return ((uint32_t)sj << F) + (h - (1u << F));
 }
+
+// Per-tile segment list written by the count pass for the move pass:
+// [0] ns, [1..4] lo, [5..8] hi, [9..12] segment index.
+constexpr int TILEINFO = 16;
 
 // Count pass of a level step: per tile, the bucket counts of its last
 // segment (cnt[t][b]) and whether that segment starts inside the tile
@@ -100,10 +116,11 @@ template <int K, int IPT>
 __global__ void __launch_bounds__(LEVEL_THREADS)
     k_level_count(const __grid_constant__ AllBufs bufs, int q, const LevelJob* __restrict__ jobs, int njobs,
                   const CloudDev* __restrict__ clouds, const uint32_t* __restrict__ medr, uint32_t* __restrict__ cnt,
-                  uint32_t* __restrict__ head, int* __restrict__ err) {
+                  uint32_t* __restrict__ head, int32_t* __restrict__ tinfo, int* __restrict__ err) {
     constexpr int NBMAX = 1 << (K - 1);
     constexpr int NDMAX = LEVEL_NSMAX * NBMAX;
     __shared__ uint32_t s_cnt[NDMAX];
+    __shared__ uint32_t s_med[LEVEL_NSMAX][NBMAX];
     __shared__ int32_t s_seglo[LEVEL_NSMAX], s_seghi[LEVEL_NSMAX], s_segidx[LEVEL_NSMAX];
     __shared__ int s_ns;
     const int tid = threadIdx.x;
@@ -114,11 +131,25 @@ __global__ void __launch_bounds__(LEVEL_THREADS)
     const int NB = 1 << F;
     const int32_t pos0 = (int32_t)T.pos0;
     for (int i = tid; i < NDMAX; i += LEVEL_THREADS) s_cnt[i] = 0;
-    if (tid == 0) s_ns = tile_segments(pos0, T.npos, C.m, T.lev_in, s_seglo, s_seghi, s_segidx, err);
+    if (tid == 0) {
+        const int ns = tile_segments(pos0, T.npos, C.m, T.lev_in, s_seglo, s_seghi, s_segidx, err);
+        s_ns = ns;
+        int32_t* ti = tinfo + (int64_t)t * TILEINFO;
+        ti[0] = ns;
+        for (int x = 0; x < LEVEL_NSMAX; ++x) {
+            ti[1 + x] = x < ns ? s_seglo[x] : 0;
+            ti[5 + x] = x < ns ? s_seghi[x] : -1;
+            ti[9 + x] = x < ns ? s_segidx[x] : 0;
+        }
+    }
     __syncthreads();
     const int ns = s_ns;
+    load_tile_medians<NBMAX>(s_med, ns, s_segidx, F, T.lev_in, medr, C.medr_off);
+    __syncthreads();
     const int64_t goff = C.off;
-    const int64_t medr_off = C.medr_off;
+    const uint32_t* planes[K];
+#pragma unroll
+    for (int f = 0; f < K; ++f) planes[f] = bufs.p[q][T.src_buf][(T.lev_in + f) % K];
     for (int o = tid; o < T.npos; o += LEVEL_THREADS) {
         const int32_t pos = pos0 + o;
         int sj = -1;
@@ -128,10 +159,9 @@ __global__ void __launch_bounds__(LEVEL_THREADS)
         if (sj < 0) continue;
         uint32_t r[K];
 #pragma unroll
-        for (int f = 0; f < K; ++f) r[f] = (f < F) ? bufs.p[q][T.src_buf][(T.lev_in + f) % K][goff + pos] : 0u;
+        for (int f = 0; f < K; ++f) r[f] = (f < F) ? planes[f][goff + pos] : 0u;
         int32_t flo, fhi;
-        const uint32_t d = route<K>(r, F, T.lev_in, sj, NB, s_seglo[sj], s_seghi[sj], s_segidx[sj], medr, medr_off,
-                                    flo, fhi);
+        const uint32_t d = route<K, NBMAX>(r, F, sj, s_seglo[sj], s_seghi[sj], s_med, flo, fhi);
         if (d != INV) atomicAdd(&s_cnt[d], 1u);
     }
     __syncthreads();
@@ -196,43 +226,39 @@ __global__ void __launch_bounds__(1024) k_level_scan(int ntiles, int nbmax, cons
 }
 
 template <int K, int IPT>
-__global__ void __launch_bounds__(LEVEL_THREADS, 2)
+__global__ void __launch_bounds__(LEVEL_THREADS, 3)
     k_level_pass(const __grid_constant__ AllBufs bufs, int q, const LevelJob* __restrict__ jobs, int njobs,
                  const CloudDev* __restrict__ clouds, uint32_t* __restrict__ medr,
-                 const uint32_t* __restrict__ perm0, const uint32_t* __restrict__ incl, int* __restrict__ err) {
-    constexpr int TILE = LEVEL_THREADS * IPT;
+                 const uint32_t* __restrict__ perm0, const uint32_t* __restrict__ incl,
+                 const int32_t* __restrict__ tinfo, int* __restrict__ err) {
     constexpr int NBMAX = 1 << (K - 1);
     constexpr int NDMAX = LEVEL_NSMAX * NBMAX;
+    constexpr int DBITS = 2 + (K - 1) + 1;  // log2(NSMAX) + log2(NBMAX) + marker bit
     __shared__ uint32_t s_wc[LEVEL_WARPS][NDMAX];
-    __shared__ uint32_t s_cnt[NDMAX];
-    __shared__ uint32_t s_tstart[NDMAX];
     __shared__ int32_t s_dbase[NDMAX];
-    __shared__ uint32_t s_excl[NBMAX];
-    __shared__ int32_t s_seglo[LEVEL_NSMAX], s_seghi[LEVEL_NSMAX], s_segidx[LEVEL_NSMAX];
-    __shared__ int s_ns;
-    __shared__ uint32_t s_total;
-    __shared__ uint32_t s_warp[LEVEL_WARPS];
-    extern __shared__ __align__(16) uint32_t s_dyn[];  // s_dest[TILE] | s_val[TILE]
+    __shared__ uint32_t s_med[LEVEL_NSMAX][NBMAX];
+    __shared__ int32_t s_ti[TILEINFO];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int t = blockIdx.x;
-    const LevelTile T = job_tile(jobs, njobs, t, TILE, clouds);
-    const CloudDev C = clouds[T.cloud];
+    const LevelTile T = job_tile(jobs, njobs, t, LEVEL_THREADS * IPT, clouds);
+    const CloudDev& C = clouds[T.cloud];
     const int F = T.lev_out - T.lev_in;
     const int NB = 1 << F;
-    const int ND = LEVEL_NSMAX * NB;
     const int32_t m = C.m;
     const int32_t pos0 = (int32_t)T.pos0;
-    if (tid == 0) s_ns = tile_segments(pos0, T.npos, m, T.lev_in, s_seglo, s_seghi, s_segidx, err);
+    const int64_t goff = C.off;
+    if (tid < TILEINFO) s_ti[tid] = tinfo[(int64_t)t * TILEINFO + tid];
     for (int i = tid; i < LEVEL_WARPS * NDMAX; i += LEVEL_THREADS) (&s_wc[0][0])[i] = 0;
     __syncthreads();
-    const int ns = s_ns;
-    // the first segment may have begun in earlier tiles: their counts come
-    // from the scanned count pass
-    if (tid < NB) s_excl[tid] = (ns > 0 && s_seglo[0] < pos0) ? incl[(int64_t)(t - 1) * NBMAX + tid] : 0u;
+    const int ns = s_ti[0];
+    load_tile_medians<NBMAX>(s_med, ns, s_ti + 9, F, T.lev_in, medr, C.medr_off);
+    __syncthreads();
 
+    const uint32_t* planes[K];
+#pragma unroll
+    for (int f = 0; f < K; ++f) planes[f] = bufs.p[q][T.src_buf][(T.lev_in + f) % K];
     const int wbase = warp * 32 * IPT;
-    const int64_t goff = C.off;
     uint32_t v[K][IPT];
     uint32_t dig[IPT];
     int32_t flo[IPT], fhi[IPT];  // final segment of each element
@@ -243,29 +269,27 @@ __global__ void __launch_bounds__(LEVEL_THREADS, 2)
         flo[j] = 0;
         fhi[j] = -1;
 #pragma unroll
-        for (int p = 0; p < K; ++p) v[p][j] = 0;
+        for (int f = 0; f < K; ++f) v[f][j] = 0;
         if (o < T.npos) {
             const int32_t pos = pos0 + o;
             // plane order rotated so that level lev_in + f reads v[f] (compile-time index)
 #pragma unroll
-            for (int f = 0; f < K; ++f) v[f][j] = bufs.p[q][T.src_buf][(T.lev_in + f) % K][goff + pos];
+            for (int f = 0; f < K; ++f) v[f][j] = planes[f][goff + pos];
             int sj = -1;
 #pragma unroll
             for (int x = 0; x < LEVEL_NSMAX; ++x)
-                if (x < ns && pos >= s_seglo[x] && pos <= s_seghi[x]) sj = x;
+                if (x < ns && pos >= s_ti[1 + x] && pos <= s_ti[5 + x]) sj = x;
             if (sj >= 0) {
                 uint32_t r[K];
 #pragma unroll
                 for (int f = 0; f < K; ++f) r[f] = v[f][j];
-                dig[j] = route<K>(r, F, T.lev_in, sj, NB, s_seglo[sj], s_seghi[sj], s_segidx[sj], medr, C.medr_off,
-                                  flo[j], fhi[j]);
+                dig[j] = route<K, NBMAX>(r, F, sj, s_ti[1 + sj], s_ti[5 + sj], s_med, flo[j], fhi[j]);
             }
         }
     }
     // warp multisplit ranking on (segment, bucket): equal-digit lane masks
     // from ballots over the digit bits (the invalid marker is NDMAX)
-    constexpr int DBITS = 2 + (K - 1) + 1;  // log2(NSMAX) + log2(NBMAX) + marker bit
-    uint32_t slot[IPT];
+    uint32_t rank[IPT];
 #pragma unroll
     for (int j = 0; j < IPT; ++j) {
         const uint32_t d = dig[j] == INV ? (uint32_t)NDMAX : dig[j];
@@ -279,10 +303,14 @@ __global__ void __launch_bounds__(LEVEL_THREADS, 2)
         uint32_t old = 0;
         if (lane == leader && d < (uint32_t)NDMAX) old = atomicAdd(&s_wc[warp][d], (uint32_t)__popc(peers));
         old = __shfl_sync(0xffffffffu, old, leader);
-        slot[j] = old + __popc(peers & lanemask_lt());
+        rank[j] = old + __popc(peers & lanemask_lt());
     }
     __syncthreads();
-    for (int d = tid; d < ND; d += LEVEL_THREADS) {
+    // per digit: prefix over warps, and its base position: the final
+    // segment's start plus, for the first segment, the count of its elements
+    // in earlier tiles (scanned count pass)
+    const bool first_cont = ns > 0 && s_ti[1] < pos0;
+    for (int d = tid; d < LEVEL_NSMAX * NB; d += LEVEL_THREADS) {
         uint32_t c = 0;
 #pragma unroll
         for (int w = 0; w < LEVEL_WARPS; ++w) {
@@ -290,80 +318,55 @@ __global__ void __launch_bounds__(LEVEL_THREADS, 2)
             s_wc[w][d] = c;
             c += x;
         }
-        s_cnt[d] = c;
+        const int sj = d >> F;
+        const int b = d - (sj << F);
+        // start of bucket b below segment sj: walk the shape F levels
+        int32_t a = sj < ns ? s_ti[1 + sj] : 0, z = sj < ns ? s_ti[5 + sj] : -1;
+        for (int f = F - 1; f >= 0; --f) {
+            const int32_t mid = a + ((z - a) >> 1);
+            if ((b >> f) & 1) a = mid + 1; else z = mid - 1;
+        }
+        s_dbase[d] = a + ((sj == 0 && first_cont) ? (int32_t)incl[(int64_t)(t - 1) * NBMAX + b] : 0);
     }
     __syncthreads();
-    // tile-local start of every (segment, bucket) digit
-    {
-        const int per = (ND + LEVEL_THREADS - 1) / LEVEL_THREADS;
-        uint32_t loc = 0;
-        for (int x = 0; x < per; ++x) {
-            const int d = tid * per + x;
-            if (d < ND) loc += s_cnt[d];
-        }
-        uint32_t tot = 0;
-        uint32_t ex = block_excl_scan256(loc, s_warp, &tot);
-        for (int x = 0; x < per; ++x) {
-            const int d = tid * per + x;
-            if (d < ND) {
-                s_tstart[d] = ex;
-                ex += s_cnt[d];
-            }
-        }
-        if (tid == 0) s_total = tot;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < IPT; ++j)
-        if (dig[j] != INV) {
-            const uint32_t d = dig[j];
-            const int sj = (int)d / NB;
-            const int b = (int)d - sj * NB;
-            s_dbase[d] = flo[j] + (sj == 0 ? (int32_t)s_excl[b] : 0);
-        }
-    __syncthreads();
-    uint32_t* s_dest = s_dyn;
-    uint32_t* s_val = s_dyn + TILE;
+    int32_t dest[IPT];
 #pragma unroll
     for (int j = 0; j < IPT; ++j) {
-        if (dig[j] == INV) {
-            slot[j] = INV;
-        } else {
+        dest[j] = -1;
+        if (dig[j] != INV) {
             const uint32_t d = dig[j];
-            const uint32_t within = s_wc[warp][d] + slot[j];
-            slot[j] = s_tstart[d] + within;
-            const int32_t dest = s_dbase[d] + (int32_t)within;
+            const int32_t dd = s_dbase[d] + (int32_t)(s_wc[warp][d] + rank[j]);
             // the destination must lie in the element's final segment; any
             // other value means inconsistent inputs and is never written
-            const bool ok = dest >= flo[j] && dest <= fhi[j];
-            if (!ok) atomicOr(err, ERR_INTERNAL);
-            s_dest[slot[j]] = ok ? (uint32_t)(goff + dest) : INV;
-            if (ok && T.write_med && dest == flo[j] + ((fhi[j] - flo[j]) >> 1)) {
-                // the new median of level lev_out (rare: re-read its planes q
-                // and 0, and find its segment index)
-                const int64_t gsrc = goff + pos0 + wbase + j * 32 + lane;
-                const uint32_t rq = bufs.p[q][T.src_buf][q][gsrc];
-                const uint32_t r0 = bufs.p[q][T.src_buf][0][gsrc];
-                const int32_t si = segment_of(flo[j], m, T.lev_out).idx;
-                medr[C.medr_off + ((int64_t)1 << T.lev_out) - 1 + si] = rq;
-                if (r0 >= goff && r0 < goff + m)
-                    C.node[dest] = (int32_t)((int64_t)perm0[r0] - C.in_off);
-                else
-                    atomicOr(err, ERR_INTERNAL);
+            if (dd >= flo[j] && dd <= fhi[j]) {
+                dest[j] = dd;
+                if (T.write_med && dd == flo[j] + ((fhi[j] - flo[j]) >> 1)) {
+                    // the new median of level lev_out: its rank in super key
+                    // q and tuple (plane 0), and its segment index
+                    const int sj = (int)(d >> F);
+                    const int32_t si = (s_ti[9 + sj] << F) + (int32_t)(d - ((uint32_t)sj << F));
+                    const int64_t gsrc = goff + pos0 + wbase + j * 32 + lane;
+                    const uint32_t rq = bufs.p[q][T.src_buf][q][gsrc];
+                    const uint32_t r0 = bufs.p[q][T.src_buf][0][gsrc];
+                    medr[C.medr_off + ((int64_t)1 << T.lev_out) - 1 + si] = rq;
+                    if (r0 >= goff && r0 < goff + m)
+                        C.node[dd] = (int32_t)((int64_t)perm0[r0] - C.in_off);
+                    else
+                        atomicOr(err, ERR_INTERNAL);
+                }
+            } else {
+                atomicOr(err, ERR_INTERNAL);
             }
         }
     }
-    const int nvalid = (int)s_total;
+    // each run of equal digits goes to consecutive addresses: stores from
+    // registers, coalesced per run
 #pragma unroll
     for (int f = 0; f < K; ++f) {
-        __syncthreads();
+        uint32_t* dp = bufs.p[q][T.dst_buf][(T.lev_in + f) % K] + goff;
 #pragma unroll
         for (int j = 0; j < IPT; ++j)
-            if (slot[j] != INV) s_val[slot[j]] = v[f][j];
-        __syncthreads();
-        uint32_t* dp = bufs.p[q][T.dst_buf][(T.lev_in + f) % K];
-        for (int s = tid; s < nvalid; s += LEVEL_THREADS)
-            if (s_dest[s] != INV) dp[s_dest[s]] = s_val[s];
+            if (dest[j] >= 0) dp[dest[j]] = v[f][j];
     }
 }
 
@@ -719,12 +722,14 @@ cudaError_t launch_level_pass(int k, const AllBufs& bufs, int q, const LevelJob*
     uint32_t* cnt = status;                                  // [ntiles][nbmax]
     uint32_t* incl = cnt + (size_t)ntiles * nbmax;           // [ntiles][nbmax]
     uint32_t* head = incl + (size_t)ntiles * nbmax;          // [ntiles]
-    const size_t smem = (size_t)2 * level_tile(k) * sizeof(uint32_t);
-#define KD_LEVEL_CASE(KK)                                                                                  \
-    case KK:                                                                                             \
-        k_level_count<KK, 8><<<ntiles, LEVEL_THREADS, 0, s>>>(bufs, q, jobs, njobs, clouds, medr, cnt, head, err); \
-        k_level_scan<<<nbmax, 1024, 0, s>>>(ntiles, nbmax, cnt, head, incl);                              \
-        k_level_pass<KK, 8><<<ntiles, LEVEL_THREADS, smem, s>>>(bufs, q, jobs, njobs, clouds, medr, perm0, incl, err); \
+    int32_t* tinfo = reinterpret_cast<int32_t*>(head + ntiles);  // [ntiles][TILEINFO]
+#define KD_LEVEL_CASE(KK)                                                                                    \
+    case KK:                                                                                               \
+        k_level_count<KK, 8><<<ntiles, LEVEL_THREADS, 0, s>>>(bufs, q, jobs, njobs, clouds, medr, cnt, head,   \
+                                                              tinfo, err);                                 \
+        k_level_scan<<<nbmax, 1024, 0, s>>>(ntiles, nbmax, cnt, head, incl);                                \
+        k_level_pass<KK, 8><<<ntiles, LEVEL_THREADS, 0, s>>>(bufs, q, jobs, njobs, clouds, medr, perm0, incl,  \
+                                                             tinfo, err);                                  \
         break;
     switch (k) {
         KD_LEVEL_CASE(2)
@@ -741,8 +746,10 @@ cudaError_t launch_level_pass(int k, const AllBufs& bufs, int q, const LevelJob*
     return cudaGetLastError();
 }
 
-// status words one level step needs: counts, inclusive scan, head flags
-size_t level_status_words(int k, int ntiles) { return (size_t)ntiles * (2u << (k - 1)) + (size_t)ntiles; }
+// status words one level step needs: counts, inclusive scan, head flags, tile segment lists
+size_t level_status_words(int k, int ntiles) {
+    return (size_t)ntiles * (2u << (k - 1)) + (size_t)ntiles + (size_t)ntiles * TILEINFO;
+}
 
 size_t finish_smem(int k, int smax) { return (size_t)k * smax * 4 + (size_t)smax * 4 + (size_t)(k + 1) * smax * 2; }
 

@@ -179,8 +179,18 @@ int64_t kd_launch_count(kd_ctx *ctx);
 kd_status kd_kernel_stats(kd_ctx *ctx, int family, double *ms, int64_t *launches, double *units,
                           double *bytes);
 
-/* Zero the kernel timing sums. */
+/* Zero the kernel timing sums and trace counters. */
 kd_status kd_kernel_stats_reset(kd_ctx *ctx);
+
+/*
+ * Trace counters (instrumentation; active when cfg->debug & 4): the
+ * on-chip finisher's phases, summed over its thread blocks in nanoseconds
+ * (block time, not wall time): [0] loading a subtree's rank table and
+ * index arrays, [1] levels with segments above 32 tuples, [2] levels
+ * finished one warp per segment, [3] resolving node tuples.  Copies
+ * min(n, 8) values into out.
+ */
+kd_status kd_trace_counters(kd_ctx *ctx, double *out, int n);
 
 #ifdef __cplusplus
 }

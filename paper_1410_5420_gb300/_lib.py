@@ -23,7 +23,7 @@ FAMILIES = ["transform", "sort_pass", "dedup", "records", "level_pass", "finish"
 
 EXPORTS = ["kd_create", "kd_presort", "kd_handle_info", "kd_handle_arrays", "kd_build", "kd_release",
            "kd_build_batch", "kd_submit", "kd_wait", "kd_serving_stats", "kd_destroy", "kd_last_error",
-           "kd_launch_count", "kd_kernel_stats", "kd_kernel_stats_reset"]
+           "kd_launch_count", "kd_kernel_stats", "kd_kernel_stats_reset", "kd_trace_counters"]
 
 
 class KdConfig(ctypes.Structure):
@@ -74,6 +74,7 @@ def load():
         "kd_kernel_stats": ([vp, ctypes.c_int, P(ctypes.c_double), P(i64), P(ctypes.c_double),
                              P(ctypes.c_double)], ctypes.c_int),
         "kd_kernel_stats_reset": ([vp], ctypes.c_int),
+        "kd_trace_counters": ([vp, P(ctypes.c_double), ctypes.c_int], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)

@@ -230,6 +230,13 @@ def kd_kernel_stats(ctx: Context) -> dict:
     return out
 
 
+def kd_trace_counters(ctx: Context) -> list:
+    """Finisher phase block-time sums in ns (context created with debug & 4)."""
+    out = (ctypes.c_double * 8)()
+    ctx.check(_lib.load().kd_trace_counters(ctx.ptr, out, 8))
+    return list(out)
+
+
 def kd_kernel_stats_reset(ctx: Context) -> None:
     ctx.check(_lib.load().kd_kernel_stats_reset(ctx.ptr))
 

@@ -36,10 +36,13 @@ cudaError_t launch_sort_pass(int key64, int mode, const int64_t* count_ptr, int6
                              const uint32_t* digit_base, int shift, uint32_t* status, uint32_t* tile_ctr, int* err,
                              cudaStream_t s);
 cudaError_t launch_digit_bases(const uint32_t* hist, int nrows, uint32_t* bases, cudaStream_t s);
+cudaError_t launch_gather(int key64, const int64_t* count_ptr, int64_t max_count, const void* plane,
+                          const uint32_t* ids, void* out, int* err, cudaStream_t s);
+size_t dedup_scratch_words(int64_t n);
 cudaError_t launch_dedup(int key64, int64_t n, const void* key0, const uint32_t* ids, const void* keys,
                          int64_t stride, int k, const uint32_t* cloud_plane, int cloud_digits, uint32_t* ids_out,
-                         uint32_t* status, uint32_t* tile_ctr, int64_t* m_out, uint32_t* hist, int32_t* mcloud,
-                         int* err, cudaStream_t s);
+                         uint32_t* scratch, int64_t* m_out, uint32_t* hist, int32_t* mcloud, int* err,
+                         cudaStream_t s);
 cudaError_t launch_own_ranks(const int64_t* m_ptr, int64_t max_m, int k, const AllPlanes& rec, cudaStream_t s);
 cudaError_t launch_perm_bases(const int64_t* m_ptr, int shift, uint32_t* bases, cudaStream_t s);
 cudaError_t launch_perm_scatter(const int64_t* m_ptr, int64_t max_m, const uint32_t* dest, const PayloadArgs& pa,
@@ -53,8 +56,12 @@ cudaError_t launch_level_pass(int k, const AllBufs& bufs, int q, const LevelJob*
                               int* err, cudaStream_t s);
 size_t level_status_words(int k, int ntiles);
 size_t finish_smem(int k, int smax);
+cudaError_t init_presort_kernels();
+cudaError_t init_build_kernels();
+int finish_kmax(int smax);
 cudaError_t launch_finish(const AllBufs& bufs, int k, const int64_t* unit_prefix, int ncloud, int nunits,
-                          const CloudDev* clouds, const uint32_t* perm0, int smax, int* err, cudaStream_t s);
+                          const CloudDev* clouds, const uint32_t* perm0, int smax, int* err,
+                          unsigned long long* phase_ns, cudaStream_t s);
 cudaError_t launch_top_nodes(const CloudDev* clouds, const int64_t* prefix, int ncloud, int64_t total, int k,
                              const uint32_t* perm0, uint32_t* medr, int all_nodes, cudaStream_t s);
 }  // namespace kd
@@ -107,6 +114,7 @@ struct kd_ctx {
     double fam_ms[F_COUNT] = {0};
     double fam_units[F_COUNT] = {0};
     double fam_bytes[F_COUNT] = {0};
+    double trace_ns[8] = {0};  // finisher phase block-time sums (debug bit 4)
     int64_t fam_launches[F_COUNT] = {0};
     // pinned host scratch for small uploads
     void* pinned = nullptr;
@@ -465,13 +473,12 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
     npasses += nperm;
     uint32_t *status = nullptr, *ctrs = nullptr;
     const size_t status_words_per = (sort_status_words(N) + 3) & ~(size_t)3;  // flags | records, per pass
-    const size_t dedup_words = (size_t)pad4((N + 4095) / 4096) * 3;
+    const size_t dedup_words = dedup_scratch_words(N);
     CKS(S.get(&status, (npasses * status_words_per + dedup_words) * 4));
     CKS(S.get(&ctrs, (npasses + 1) * 4));
     // only the flag words need zeroing (records are written before their flags)
     for (size_t pi = 0; pi < npasses; ++pi)
         CK(cudaMemsetAsync(status + pi * status_words_per, 0, sort_flag_words(N) * 4, s));
-    CK(cudaMemsetAsync(status + npasses * status_words_per, 0, (size_t)pad4((N + 4095) / 4096) * 4, s));
     CK(cudaMemsetAsync(ctrs, 0, (npasses + 1) * 4, s));
     unsigned char* kbuf[2];
     uint32_t* ibuf[2];
@@ -502,8 +509,15 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
         pay.dst[0] = ibuf[ic ^ 1];
         const void* ksrc = P.mode == KEY_BUF ? (const void*)kbuf[kc] : plane_ptr(P.plane);
         void* kdst = next_gathers ? nullptr : (void*)kbuf[kc ^ 1];
+        int mode = P.mode;
+        if (mode == KEY_GATHER) {  // gather the new plane's keys into order first
+            LaunchTimer lg(ctx, F_SORT, (double)N, nullptr, 4.0 + 2.0 * P.w);
+            CK(launch_gather(plane64(P.plane), d_n, N, plane_ptr(P.plane), ibuf[ic], kbuf[kc], d_err, s));
+            ksrc = kbuf[kc];
+            mode = KEY_BUF;
+        }
         LaunchTimer lt(ctx, F_SORT, (double)N, nullptr, pass_bytes(P, kdst != nullptr, pay.n));
-        CK(launch_sort_pass(plane64(P.plane), P.mode, d_n, N, ksrc, ibuf[ic], kdst, pay,
+        CK(launch_sort_pass(plane64(P.plane), mode, d_n, N, ksrc, ibuf[ic], kdst, pay,
                             bases_all + (size_t)row_of(P.plane, P.digit) * RADIX, 8 * P.digit,
                             status + pass_no * status_words_per, ctrs + pass_no, d_err, s));
         ++pass_no;
@@ -514,8 +528,9 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
     uint32_t* dedup_out = count == 1 ? H->perm0 : ibuf[ic ^ 1];
     {
         LaunchTimer lt(ctx, F_DEDUP, (double)N, nullptr, 2.0 * w + 8);
+        ctx->launches += 2;  // flags, tile scan, compaction
         CK(launch_dedup(key64, N, kbuf[kc], ibuf[ic], keys, N, k, cloud_plane, cloud_digits, dedup_out,
-                        status + npasses * status_words_per, ctrs + npasses, H->d_m, hist, mcloud, d_err, s));
+                        status + npasses * status_words_per, H->d_m, hist, mcloud, d_err, s));
     }
     ic ^= 1;
     {
@@ -531,8 +546,15 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
         pay.src[0] = ibuf[ic];
         pay.dst[0] = last ? H->perm0 : ibuf[ic ^ 1];
         const void* ksrc = P.mode == KEY_BUF ? (const void*)kbuf[kc] : plane_ptr(-1);
+        int mode = P.mode;
+        if (mode == KEY_GATHER) {
+            LaunchTimer lg(ctx, F_SORT, 0.0, H->d_m, 12.0);
+            CK(launch_gather(0, H->d_m, N, plane_ptr(-1), ibuf[ic], kbuf[kc], d_err, s));
+            ksrc = kbuf[kc];
+            mode = KEY_BUF;
+        }
         LaunchTimer lt(ctx, F_SORT, 0.0, H->d_m, pass_bytes(P, !last, 1));
-        CK(launch_sort_pass(0, P.mode, H->d_m, N, ksrc, ibuf[ic], last ? nullptr : (void*)kbuf[kc ^ 1], pay,
+        CK(launch_sort_pass(0, mode, H->d_m, N, ksrc, ibuf[ic], last ? nullptr : (void*)kbuf[kc ^ 1], pay,
                             bases_kept + (size_t)row_of(-1, P.digit) * RADIX, 8 * P.digit,
                             status + pass_no * status_words_per, ctrs + pass_no, d_err, s));
         ++pass_no;
@@ -582,8 +604,15 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
                 pay.n = np;
                 const void* ksrc = P.mode == KEY_BUF ? (const void*)kbuf[kc] : plane_ptr(P.plane);
                 void* kdst = (last || next_gathers) ? nullptr : (void*)kbuf[kc ^ 1];
+                int mode = P.mode;
+                if (mode == KEY_GATHER) {
+                    LaunchTimer lg(ctx, F_SORT, 0.0, H->d_m, 4.0 + 2.0 * P.w);
+                    CK(launch_gather(plane64(P.plane), H->d_m, N, plane_ptr(P.plane), cur_id, kbuf[kc], d_err, s));
+                    ksrc = kbuf[kc];
+                    mode = KEY_BUF;
+                }
                 LaunchTimer lt(ctx, F_SORT, 0.0, H->d_m, pass_bytes(P, kdst != nullptr, pay.n));
-                CK(launch_sort_pass(plane64(P.plane), P.mode, H->d_m, N, ksrc, cur_id, kdst, pay,
+                CK(launch_sort_pass(plane64(P.plane), mode, H->d_m, N, ksrc, cur_id, kdst, pay,
                                     bases_kept + (size_t)row_of(P.plane, P.digit) * RADIX, 8 * P.digit,
                                     status + pass_no * status_words_per, ctrs + pass_no, d_err, s));
                 ++pass_no;
@@ -715,6 +744,7 @@ kd_status build_batch(kd_ctx* ctx, kd_presorted* H, kd_tree* outs) {
         smax = 1024;
         while (smax < ctx->smax_override && smax < 4096) smax *= 2;
     }
+    while (smax > 1024 && k > finish_kmax(smax)) smax /= 2;
     if (k >= 2 && smax * 3 < level_tile(k) + 3) return fail(ctx, KD_EINVAL, "switch threshold too small");
 
     // outputs: user device arrays, or staging for host arrays
@@ -900,7 +930,18 @@ kd_status build_batch(kd_ctx* ctx, kd_presorted* H, kd_tree* outs) {
     if (nunits > 0) {
         LaunchTimer lt(ctx, F_FINISH, (double)M, nullptr,
                        4.0 * (2 * k - 1) + 8.0 + (want_l ? 4 : 0) + (want_r ? 4 : 0) + (want_d ? 1 : 0));
-        CK(launch_finish(bufs, k, d_uprefix, count, (int)nunits, d_cd, H->perm0, smax, d_err, s));
+        unsigned long long* phase = nullptr;
+        if (ctx->debug & 4) {
+            CKS(S.get(&phase, sizeof(unsigned long long) * 8));
+            CK(cudaMemsetAsync(phase, 0, sizeof(unsigned long long) * 8, s));
+        }
+        CK(launch_finish(bufs, k, d_uprefix, count, (int)nunits, d_cd, H->perm0, smax, d_err, phase, s));
+        if (phase) {
+            unsigned long long h[8];
+            CK(cudaMemcpyAsync(h, phase, sizeof(h), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            for (int i = 0; i < 8; ++i) ctx->trace_ns[i] += (double)h[i];
+        }
     }
     CKS(check_device_err(ctx, d_err));
     if (any_host) {
@@ -1033,6 +1074,19 @@ kd_status kd_create(kd_ctx** out, const kd_config* cfg) {
     ctx->debug = c.debug;
     ctx->smax_override = c.switch_threshold;
     if (cudaSetDevice(c.device) != cudaSuccess) return KD_EDEVICE;
+    // kernel attributes are per device: set them once for each device used
+    static std::mutex init_mu;
+    static bool init_done[64] = {false};
+    {
+        std::lock_guard<std::mutex> lk(init_mu);
+        if (c.device < 64 && !init_done[c.device]) {
+            if (init_presort_kernels() != cudaSuccess || init_build_kernels() != cudaSuccess) {
+                cudaGetLastError();
+                return KD_EDEVICE;
+            }
+            init_done[c.device] = true;
+        }
+    }
     if (c.cuda_stream) {
         ctx->stream = (cudaStream_t)c.cuda_stream;
     } else {
@@ -1234,6 +1288,13 @@ kd_status kd_kernel_stats(kd_ctx* ctx, int family, double* ms, int64_t* launches
     if (launches) *launches = ctx->fam_launches[family];
     if (units) *units = ctx->fam_units[family];
     if (bytes) *bytes = ctx->fam_bytes[family];
+    return KD_OK;
+}
+
+kd_status kd_trace_counters(kd_ctx* ctx, double* out, int n) {
+    if (!ctx || !out || n < 0) return KD_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    for (int i = 0; i < n && i < 8; ++i) out[i] = ctx->trace_ns[i];
     return KD_OK;
 }
 

@@ -376,14 +376,15 @@ constexpr uint32_t HOLE = 0xffffffffu;
 __device__ __forceinline__ uint32_t seg_pack(int32_t a, int32_t b) { return (uint32_t)a | ((uint32_t)b << 16); }
 
 // Stable partition of one array (lids, src) around the medians of the
-// current level into dst.  Each warp owns a chunk of consecutive positions
+// current level into dst; side[lid] says where tuple lid goes (0 less, 1
+// greater, 2 the median itself).  Each warp owns a chunk of consecutive positions
 // and walks it 32 at a time: ballots of "less" / "greater" / "segment start"
 // give every lane its count of earlier less/greater elements in its segment;
 // a segment crossing chunk boundaries gets the preceding warps' counts.
 template <int GMAX>
 __device__ __forceinline__ void fin_partition(const uint16_t* __restrict__ src, uint16_t* __restrict__ dst,
-                                              const uint16_t* __restrict__ prim, const uint32_t* __restrict__ rkp,
-                                              const uint32_t* __restrict__ seg, int S, uint32_t* s_agg, int* bad) {
+                                              const uint8_t* __restrict__ side, const uint32_t* __restrict__ seg,
+                                              int S, uint32_t* s_agg, int* bad) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int groups = (S + FIN_THREADS - 1) / FIN_THREADS;  // per warp, <= GMAX
     const int chunk = groups * 32;
@@ -409,9 +410,9 @@ __device__ __forceinline__ void fin_partition(const uint16_t* __restrict__ src, 
                 const int32_t bb = sg >> 16;
                 c = a + ((bb - a) >> 1);
                 lid = src[i];
-                const uint32_t r = rkp[lid], mv = rkp[prim[c]];
-                isL = r < mv;
-                isR = r > mv;
+                const uint32_t sd = side[lid];
+                isL = sd == 0;
+                isR = sd == 1;
                 start = i == a;
             }
             const uint32_t Lm = __ballot_sync(0xffffffffu, isL);
@@ -485,24 +486,104 @@ __device__ __forceinline__ void fin_partition(const uint16_t* __restrict__ src, 
     }
 }
 
-// Write the node at cloud-local address addr (the median of [lo_a, hi_a],
-// unit-relative bounds a..b with median c) and its children / dimension.
-__device__ __forceinline__ void fin_emit(const CloudDev& C, const uint32_t* __restrict__ perm0, int32_t lo,
-                                         int32_t a, int32_t b, int32_t c, uint32_t r0, int p, int* bad) {
+// The node at unit position c (median of unit-relative [a, b]) is tuple
+// lid: its children and dimension are written now; its tuple index is
+// resolved for all nodes of the unit at the end (nodelid[c] = lid), so that
+// the random perm0 reads are issued together rather than on every level's
+// critical path.
+__device__ __forceinline__ void fin_emit(const CloudDev& C, uint16_t* nodelid, int32_t lo, int32_t a, int32_t b,
+                                         int32_t c, uint16_t lid, int p) {
     const int32_t addr = lo + c;
-    if (r0 >= C.off && r0 < C.off + C.m)
-        C.node[addr] = (int32_t)((int64_t)perm0[r0] - C.in_off);
-    else
-        *bad = 1;
+    nodelid[c] = lid;
     if (C.left) C.left[addr] = a <= c - 1 ? lo + child_mid(a, c - 1) : -1;
     if (C.right) C.right[addr] = c + 1 <= b ? lo + child_mid(c + 1, b) : -1;
     if (C.dim) C.dim[addr] = (uint8_t)p;
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Phase tracing (optional): thread 0 adds the time since the previous
+// barrier-aligned stamp to phase_ns[ph]; block-time sums over all units.
+#define FIN_STAMP(ph)                                                              \
+    do {                                                                           \
+        if (phase_ns && tid == 0) {                                                \
+            const unsigned long long now_ = global_ns();                           \
+            atomicAdd(&phase_ns[ph], now_ - t_prev);                               \
+            t_prev = now_;                                                         \
+        }                                                                          \
+    } while (0)
+
+// A finisher unit's input: rk[p][i] = rank p of array 0's element i (array
+// 0 is sorted by rank 0), and for arrays d >= 1 the lid of each element
+// (position in array 0 of the tuple with its rank 0).  All (2K-1) loads per
+// position are in flight before the first is used.
+template <int K, int SMAX>
+__device__ __forceinline__ void fin_load_unit(const AllBufs& bufs, const CloudDev& C, int64_t g, int S,
+                                              uint32_t* rk, uint16_t* arr, int* bad) {
+    constexpr int PPT = SMAX / FIN_THREADS;
+    const int tid = threadIdx.x;
+    uint32_t v[2 * K - 1][PPT];
+#pragma unroll
+    for (int p = 0; p < 2 * K - 1; ++p) {
+        const uint32_t* src = p < K ? bufs.p[0][C.buf[0]][p] : bufs.p[p - K + 1][C.buf[p - K + 1]][0];
+#pragma unroll
+        for (int j = 0; j < PPT; ++j) {
+            const int i = tid + j * FIN_THREADS;
+            v[p][j] = i < S ? src[g + i] : 0u;
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < K; ++p)
+#pragma unroll
+        for (int j = 0; j < PPT; ++j) {
+            const int i = tid + j * FIN_THREADS;
+            if (i < S) rk[p * SMAX + i] = v[p][j];
+        }
+    __syncthreads();
+#pragma unroll
+    for (int d = 1; d < K; ++d) {
+        int pos[PPT];
+#pragma unroll
+        for (int j = 0; j < PPT; ++j) pos[j] = 0;
+#pragma unroll
+        for (int step = SMAX / 2; step >= 1; step >>= 1) {
+#pragma unroll
+            for (int j = 0; j < PPT; ++j)
+                if (pos[j] + step <= S && rk[pos[j] + step - 1] < v[K - 1 + d][j]) pos[j] += step;
+        }
+#pragma unroll
+        for (int j = 0; j < PPT; ++j) {
+            const int i = tid + j * FIN_THREADS;
+            if (i < S) {
+                if (pos[j] >= S || rk[pos[j]] != v[K - 1 + d][j]) *bad = 1;
+                arr[d * SMAX + i] = (uint16_t)min(pos[j], S - 1);
+            }
+        }
+    }
+}
+
+// Largest k each on-chip subtree size serves (the host clamps accordingly),
+// so that one kernel's registers are not sized for every k.
+__host__ __device__ constexpr int fin_kmax(int smax) { return smax >= 4096 ? 3 : (smax >= 2048 ? 4 : 8); }
+
+template <int K, int SMAX>
+__device__ __forceinline__ void fin_load_dispatch(const AllBufs& bufs, const CloudDev& C, int64_t g, int S,
+                                                  uint32_t* rk, uint16_t* arr, int* bad) {
+    if constexpr (K <= fin_kmax(SMAX))
+        fin_load_unit<K, SMAX>(bufs, C, g, S, rk, arr, bad);
+    else
+        *bad = 1;
+}
+
 template <int SMAX>
-__global__ void __launch_bounds__(FIN_THREADS)
+__global__ void __launch_bounds__(FIN_THREADS, SMAX >= 4096 ? 2 : 3)
     k_finish(const __grid_constant__ AllBufs bufs, int k, const int64_t* __restrict__ unit_prefix, int ncloud,
-             const CloudDev* __restrict__ clouds, const uint32_t* __restrict__ perm0, int* __restrict__ err) {
+             const CloudDev* __restrict__ clouds, const uint32_t* __restrict__ perm0, int* __restrict__ err,
+             unsigned long long* __restrict__ phase_ns) {
     constexpr int GMAX = SMAX / FIN_THREADS;
     constexpr int smax = SMAX;
     extern __shared__ __align__(16) uint32_t sm[];
@@ -512,6 +593,8 @@ __global__ void __launch_bounds__(FIN_THREADS)
     uint32_t* rk = sm;                                          // rk[p * smax + lid]
     uint32_t* seg = rk + (size_t)k * smax;                      // packed segment per position
     uint16_t* arr = reinterpret_cast<uint16_t*>(seg + smax);   // (k+1) storages of lids
+    uint16_t* nodelid = arr + (size_t)(k + 1) * smax;           // tuple chosen at each position
+    uint8_t* side = reinterpret_cast<uint8_t*>(nodelid + smax);  // per lid: side of this level's split
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     FinUnit U;
     U.cloud = last_le(unit_prefix, ncloud + 1, blockIdx.x);
@@ -526,56 +609,62 @@ __global__ void __launch_bounds__(FIN_THREADS)
         return;
     }
     const int64_t g = C.off + lo;
-    for (int p = 0; p < k; ++p) {
-        const uint32_t* src = bufs.p[0][C.buf[0]][p];
-        for (int i = tid; i < S; i += FIN_THREADS) rk[p * smax + i] = src[g + i];
-    }
+    unsigned long long t_prev = phase_ns && tid == 0 ? global_ns() : 0ull;
     if (tid <= k) s_cur[tid] = tid;
     if (tid == 0) s_nseg = 0;
+    int bad = 0;
+    // Load the unit at once: array 0's k rank planes (the rank table, rows
+    // sorted by rank 0) and the rank-0 plane of arrays 1..k-1; every load is
+    // issued before any is used.  Then each element of array d finds its lid
+    // (its position in array 0) by a branch-free binary search of its rank 0.
+    switch (k) {
+        case 2: fin_load_dispatch<2, SMAX>(bufs, C, g, S, rk, arr, &bad); break;
+        case 3: fin_load_dispatch<3, SMAX>(bufs, C, g, S, rk, arr, &bad); break;
+        case 4: fin_load_dispatch<4, SMAX>(bufs, C, g, S, rk, arr, &bad); break;
+        case 5: fin_load_dispatch<5, SMAX>(bufs, C, g, S, rk, arr, &bad); break;
+        case 6: fin_load_dispatch<6, SMAX>(bufs, C, g, S, rk, arr, &bad); break;
+        case 7: fin_load_dispatch<7, SMAX>(bufs, C, g, S, rk, arr, &bad); break;
+        case 8: fin_load_dispatch<8, SMAX>(bufs, C, g, S, rk, arr, &bad); break;
+        default: bad = 1;
+    }
     __syncthreads();
     for (int i = tid; i < S; i += FIN_THREADS) {
         arr[i] = (uint16_t)i;
         seg[i] = seg_pack(0, S - 1);
     }
-    int bad = 0;
-    for (int d = 1; d < k; ++d) {
-        const uint32_t* src0 = bufs.p[d][C.buf[d]][0];
-        for (int i = tid; i < S; i += FIN_THREADS) {
-            const uint32_t r0 = src0[g + i];
-            int a = 0, b = S;  // array 0 is sorted by rank 0 within the segment
-            while (a < b) {
-                const int mid = (a + b) >> 1;
-                if (rk[mid] < r0) a = mid + 1; else b = mid;
-            }
-            if (a >= S || rk[a] != r0) bad = 1;
-            arr[d * smax + i] = (uint16_t)min(a, S - 1);
-        }
-    }
     __syncthreads();
-    // block levels: while a segment may hold more than 32 tuples
+    FIN_STAMP(0);  // rank table and lids of the unit
+    // block levels: while a segment may hold more than 32 tuples.  cur
+    // packs which storage holds array d (4 bits each; storage k is spare);
+    // every thread keeps the same copy, so rotating needs no barrier.
+    uint64_t cur = 0;
+    for (int d = 0; d <= k; ++d) cur |= (uint64_t)d << (4 * d);
+    auto slot = [&](int d) { return (int)((cur >> (4 * d)) & 0xfu); };
     int dl = 0;
     for (; (S >> dl) > 32; ++dl) {
         const int L = C.lam + dl;
         const int p = L % k;
-        const uint16_t* prim = arr + s_cur[p] * smax;
-        const uint32_t* rkp = rk + p * smax;
+        const uint16_t* prim = arr + slot(p) * smax;
+        // the primary array decides every tuple's side; its medians are nodes
         for (int i = tid; i < S; i += FIN_THREADS) {
             const uint32_t sg = seg[i];
             if (sg == HOLE) continue;
             const int32_t a = sg & 0xffff, b = sg >> 16, c = a + ((b - a) >> 1);
-            if (i == c) fin_emit(C, perm0, lo, a, b, c, rk[prim[c]], p, &bad);
+            const uint16_t lid = prim[i];
+            side[lid] = i < c ? 0 : (i > c ? 1 : 2);
+            if (i == c) fin_emit(C, nodelid, lo, a, b, c, lid, p);
         }
+        __syncthreads();
+        FIN_STAMP(4);  // block levels: sides and nodes
         for (int j = 1; j < k; ++j) {
             const int d = (p + j) % k;
-            fin_partition<GMAX>(arr + s_cur[d] * smax, arr + s_cur[k] * smax, prim, rkp, seg, S, s_agg, &bad);
-            __syncthreads();
-            if (tid == 0) {
-                const int x = s_cur[d];
-                s_cur[d] = s_cur[k];
-                s_cur[k] = x;
-            }
+            fin_partition<GMAX>(arr + slot(d) * smax, arr + slot(k) * smax, side, seg, S, s_agg, &bad);
+            const int x = slot(d), y = slot(k);
+            cur = (cur & ~((uint64_t)0xf << (4 * d)) & ~((uint64_t)0xf << (4 * k))) | ((uint64_t)y << (4 * d)) |
+                  ((uint64_t)x << (4 * k));
             __syncthreads();
         }
+        FIN_STAMP(5);  // block levels: partitions
         for (int i = tid; i < S; i += FIN_THREADS) {
             const uint32_t sg = seg[i];
             if (sg == HOLE) continue;
@@ -583,7 +672,11 @@ __global__ void __launch_bounds__(FIN_THREADS)
             seg[i] = (i == c) ? HOLE : (i < c ? seg_pack(a, c - 1) : seg_pack(c + 1, b));
         }
         __syncthreads();
+        FIN_STAMP(6);  // block levels: segment update
     }
+    if (tid <= k) s_cur[tid] = slot(tid);
+    __syncthreads();
+    FIN_STAMP(1);  // levels with segments of more than 32 tuples
     // warp levels: every remaining segment has at most 32 tuples; one warp
     // finishes a segment with one tuple per lane, in the order of the
     // current primary array.  For every dimension q the lane holds LESS_q,
@@ -661,7 +754,7 @@ __global__ void __launch_bounds__(FIN_THREADS)
             const bool goL = active && rank < c - mlo;
             const bool goR = active && rank > c - mlo;
             if (active && rank == c - mlo) {
-                fin_emit(C, perm0, lo, mlo, mhi, c, rk[lid], p, &bad);
+                fin_emit(C, nodelid, lo, mlo, mhi, c, lid, p);
                 active = false;
             }
             const uint32_t Lm = __ballot_sync(0xffffffffu, goL);
@@ -675,7 +768,20 @@ __global__ void __launch_bounds__(FIN_THREADS)
             }
         }
     }
+    // tuple of every node of the unit: rank 0 -> input index, all reads in flight together
+    __syncthreads();
+    FIN_STAMP(2);  // warp levels
+#pragma unroll 4
+    for (int i = tid; i < S; i += FIN_THREADS) {
+        const uint32_t r0 = rk[nodelid[i]];
+        if (r0 >= C.off && r0 < C.off + C.m)
+            C.node[lo + i] = (int32_t)((int64_t)perm0[r0] - C.in_off);
+        else
+            bad = 1;
+    }
     if (bad) atomicOr(err, ERR_INTERNAL);
+    __syncthreads();
+    FIN_STAMP(3);  // node tuples
 }
 
 // ------------------------------------------------------------ top nodes
@@ -751,28 +857,36 @@ size_t level_status_words(int k, int ntiles) {
     return (size_t)ntiles * (2u << (k - 1)) + (size_t)ntiles + (size_t)ntiles * TILEINFO;
 }
 
-size_t finish_smem(int k, int smax) { return (size_t)k * smax * 4 + (size_t)smax * 4 + (size_t)(k + 1) * smax * 2; }
+int finish_kmax(int smax) { return fin_kmax(smax); }
+size_t finish_smem(int k, int smax) {
+    return (size_t)k * smax * 4 + (size_t)smax * 4 + (size_t)(k + 2) * smax * 2 + (size_t)smax;
+}
+
+cudaError_t init_build_kernels() {
+    cudaError_t e = cudaSuccess;
+    auto set = [&](const void* f, size_t bytes) {
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    };
+    set((const void*)k_finish<1024>, finish_smem(fin_kmax(1024), 1024));
+    set((const void*)k_finish<2048>, finish_smem(fin_kmax(2048), 2048));
+    set((const void*)k_finish<4096>, finish_smem(fin_kmax(4096), 4096));
+    return e;
+}
 
 cudaError_t launch_finish(const AllBufs& bufs, int k, const int64_t* unit_prefix, int ncloud, int nunits,
-                          const CloudDev* clouds, const uint32_t* perm0, int smax, int* err, cudaStream_t s) {
+                          const CloudDev* clouds, const uint32_t* perm0, int smax, int* err,
+                          unsigned long long* phase_ns, cudaStream_t s) {
     if (nunits == 0) return cudaSuccess;
+    if (k > fin_kmax(smax)) return cudaErrorInvalidValue;
     const size_t smem = finish_smem(k, smax);
-    cudaError_t e;
-    if (smax == 2048) {
-        e = cudaFuncSetAttribute(k_finish<2048>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_finish<2048><<<nunits, FIN_THREADS, smem, s>>>(bufs, k, unit_prefix, ncloud, clouds, perm0, err);
-    } else if (smax == 1024) {
-        e = cudaFuncSetAttribute(k_finish<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_finish<1024><<<nunits, FIN_THREADS, smem, s>>>(bufs, k, unit_prefix, ncloud, clouds, perm0, err);
-    } else if (smax == 4096) {
-        e = cudaFuncSetAttribute(k_finish<4096>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_finish<4096><<<nunits, FIN_THREADS, smem, s>>>(bufs, k, unit_prefix, ncloud, clouds, perm0, err);
-    } else {
+    if (smax == 2048)
+        k_finish<2048><<<nunits, FIN_THREADS, smem, s>>>(bufs, k, unit_prefix, ncloud, clouds, perm0, err, phase_ns);
+    else if (smax == 1024)
+        k_finish<1024><<<nunits, FIN_THREADS, smem, s>>>(bufs, k, unit_prefix, ncloud, clouds, perm0, err, phase_ns);
+    else if (smax == 4096)
+        k_finish<4096><<<nunits, FIN_THREADS, smem, s>>>(bufs, k, unit_prefix, ncloud, clouds, perm0, err, phase_ns);
+    else
         return cudaErrorInvalidValue;
-    }
     return cudaGetLastError();
 }
 

@@ -239,6 +239,37 @@ __global__ void __launch_bounds__(SORT_THREADS, 2)
     }
 }
 
+// Gather of key words by tuple id: out[pos] = plane[ids[pos]], positions in
+// [0, *count_ptr).  Each thread issues GI independent gathers, so a random
+// read of the key plane keeps many requests in flight.
+template <typename KW, int GI>
+__global__ void __launch_bounds__(256) k_gather(const int64_t* __restrict__ count_ptr, const KW* __restrict__ plane,
+                                                const uint32_t* __restrict__ ids, int64_t gather_limit,
+                                                KW* __restrict__ out, int* __restrict__ err) {
+    const int64_t count = *count_ptr;
+    const int64_t base = (int64_t)blockIdx.x * 256 * GI + threadIdx.x;
+    uint32_t id[GI];
+#pragma unroll
+    for (int j = 0; j < GI; ++j) {
+        const int64_t p = base + (int64_t)j * 256;
+        id[j] = p < count ? ids[p] : 0u;
+    }
+    KW v[GI];
+#pragma unroll
+    for (int j = 0; j < GI; ++j) {
+        const int64_t p = base + (int64_t)j * 256;
+        v[j] = 0;
+        if (p < count) {
+            if ((int64_t)id[j] < gather_limit) v[j] = plane[id[j]]; else atomicOr(err, ERR_INTERNAL);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < GI; ++j) {
+        const int64_t p = base + (int64_t)j * 256;
+        if (p < count) out[p] = v[j];
+    }
+}
+
 // Exclusive prefix of each 256-bin histogram row: bases[r][d].
 __global__ void k_digit_bases(const uint32_t* __restrict__ hist, uint32_t* __restrict__ bases) {
     __shared__ uint32_t s_warp[8];
@@ -248,44 +279,36 @@ __global__ void k_digit_bases(const uint32_t* __restrict__ hist, uint32_t* __res
 
 // ---------------------------------------------------------------- dedup
 // keep[i] = i is the first of its run of identical tuples (same cloud) in
-// the array sorted by super key 0; kept ids are compacted in order.  Each
-// dropped tuple's key bytes are subtracted from the histograms so that they
-// describe the kept tuples for the sorts that follow.
+// the array sorted by super key 0.  Three steps, no inter-tile waiting:
+// k_dedup_flags writes keep bits and per-tile keep counts (and subtracts
+// each dropped tuple's key bytes from the histograms, so that they describe
+// the kept tuples for the sorts that follow); k_tile_scan turns the counts
+// into tile offsets (and m); k_dedup_compact writes the kept ids in order.
+constexpr int DEDUP_TILE = 4096;
+
 template <typename KW>
-__global__ void __launch_bounds__(256) k_dedup(int64_t n, const KW* __restrict__ key0,
-                                               const uint32_t* __restrict__ ids, const KW* __restrict__ keys,
-                                               int64_t stride, int k,
-                                               const uint32_t* __restrict__ cloud_plane, int cloud_digits,
-                                               uint32_t* __restrict__ ids_out, uint32_t* __restrict__ status,
-                                               uint32_t* __restrict__ tile_ctr, int64_t* __restrict__ m_out,
-                                               uint32_t* __restrict__ hist, int32_t* __restrict__ mcloud,
-                                               int* __restrict__ err) {
-    constexpr int IPT = 16;
-    constexpr int TILE = 256 * IPT;
+__global__ void __launch_bounds__(256) k_dedup_flags(int64_t n, const KW* __restrict__ key0,
+                                                     const uint32_t* __restrict__ ids, const KW* __restrict__ keys,
+                                                     int64_t stride, int k, const uint32_t* __restrict__ cloud_plane,
+                                                     int cloud_digits, uint32_t* __restrict__ keepbits,
+                                                     uint32_t* __restrict__ tile_cnt, uint32_t* __restrict__ hist,
+                                                     int32_t* __restrict__ mcloud, int* __restrict__ err) {
+    constexpr int IPT = DEDUP_TILE / 256;
     constexpr int D = sizeof(KW);
-    __shared__ uint32_t s_tile, s_excl, s_wsum[8], s_ctl;
+    __shared__ uint32_t s_wsum[8];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
-    __syncthreads();
-    const int64_t tile = s_tile;
-    const int64_t base = tile * TILE;
-    if (base >= n) return;
-    const int tile_n = (int)(n - base < TILE ? n - base : (int64_t)TILE);
+    const int64_t base = (int64_t)blockIdx.x * DEDUP_TILE;
     const int wbase = warp * 32 * IPT;
-    uint32_t ball[IPT];
-    uint32_t id[IPT];
     uint32_t wcount = 0;
 #pragma unroll
     for (int j = 0; j < IPT; ++j) {
-        const int o = wbase + j * 32 + lane;
+        const int64_t pos = base + wbase + j * 32 + lane;
         bool keep = false;
-        id[j] = 0;
-        if (o < tile_n) {
-            const int64_t pos = base + o;
-            id[j] = ids[pos];
-            if ((int64_t)id[j] >= n) {
+        if (pos < n) {
+            uint32_t id = ids[pos];
+            if ((int64_t)id >= n) {
                 atomicOr(err, ERR_INTERNAL);
-                id[j] = 0;
+                id = 0;
             }
             const KW k0 = key0[pos];
             bool dup = false;
@@ -293,18 +316,18 @@ __global__ void __launch_bounds__(256) k_dedup(int64_t n, const KW* __restrict__
                 const uint32_t pid = ids[pos - 1];
                 dup = true;
                 for (int d = 1; d < k && dup; ++d)
-                    if (keys[d * stride + id[j]] != keys[d * stride + pid]) dup = false;
-                if (dup && cloud_plane && cloud_plane[id[j]] != cloud_plane[pid]) dup = false;
+                    if (keys[d * stride + id] != keys[d * stride + pid]) dup = false;
+                if (dup && cloud_plane && cloud_plane[id] != cloud_plane[pid]) dup = false;
             }
             keep = !dup;
             if (dup) {
                 for (int d = 0; d < k; ++d) {
-                    const KW kd = keys[d * stride + id[j]];
+                    const KW kd = keys[d * stride + id];
                     for (int b = 0; b < D; ++b)
                         atomicSub(&hist[(d * D + b) * RADIX + (uint32_t)((kd >> (8 * b)) & 255u)], 1u);
                 }
                 if (cloud_plane) {
-                    const uint32_t c = cloud_plane[id[j]];
+                    const uint32_t c = cloud_plane[id];
                     for (int b = 0; b < cloud_digits; ++b)
                         atomicSub(&hist[(k * D + b) * RADIX + ((c >> (8 * b)) & 255u)], 1u);
                     atomicSub(&mcloud[c], 1);
@@ -313,45 +336,60 @@ __global__ void __launch_bounds__(256) k_dedup(int64_t n, const KW* __restrict__
                 }
             }
         }
-        ball[j] = __ballot_sync(0xffffffffu, keep);
+        const uint32_t ball = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0 && base + wbase + j * 32 < n) keepbits[(base + wbase + j * 32) >> 5] = ball;
+        wcount += __popc(ball);
+    }
+    if (lane == 0) s_wsum[warp] = wcount;
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t acc = 0;
+        for (int w = 0; w < 8; ++w) acc += s_wsum[w];
+        tile_cnt[blockIdx.x] = acc;
+    }
+}
+
+// Exclusive scan of per-tile counts in one block; *total_out = sum.
+__global__ void __launch_bounds__(1024) k_tile_scan(int64_t ntiles, const uint32_t* __restrict__ cnt,
+                                                    uint32_t* __restrict__ offs, int64_t* __restrict__ total_out) {
+    __shared__ uint32_t s_warp[32];
+    uint32_t carry = 0;
+    for (int64_t t0 = 0; t0 < ntiles; t0 += 1024) {
+        const int64_t t = t0 + threadIdx.x;
+        const uint32_t v = t < ntiles ? cnt[t] : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_excl_scan<1024>(v, s_warp, &tot);
+        if (t < ntiles) offs[t] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) *total_out = carry;
+}
+
+__global__ void __launch_bounds__(256) k_dedup_compact(int64_t n, const uint32_t* __restrict__ ids,
+                                                       const uint32_t* __restrict__ keepbits,
+                                                       const uint32_t* __restrict__ offs,
+                                                       uint32_t* __restrict__ ids_out) {
+    constexpr int IPT = DEDUP_TILE / 256;
+    __shared__ uint32_t s_wsum[8];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t base = (int64_t)blockIdx.x * DEDUP_TILE;
+    const int wbase = warp * 32 * IPT;
+    uint32_t ball[IPT];
+    uint32_t wcount = 0;
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+        const int64_t row = base + wbase + j * 32;
+        ball[j] = row < n ? keepbits[row >> 5] : 0u;
         wcount += __popc(ball[j]);
     }
     if (lane == 0) s_wsum[warp] = wcount;
     __syncthreads();
-    uint32_t acc = 0;
-    for (int w = 0; w < 8; ++w) acc += s_wsum[w];
-    // status: flags [tiles] | aggregate [tiles] | inclusive [tiles]
-    const int64_t ntiles = (n + TILE - 1) / TILE;
-    uint32_t* flags = status;
-    uint32_t* aggrec = status + pad4(ntiles);
-    uint32_t* increc = aggrec + pad4(ntiles);
-    if (tid == 0) {
-        if (tile == 0) increc[0] = acc; else aggrec[tile] = acc;
-        publish_flag(flags, tile, tile == 0 ? FLAG_INC : FLAG_AGG);
-    }
-    uint32_t excl = 0;
-    if (tile > 0) {
-        excl = block_lookback<uint32_t>(flags, aggrec, increc, 1, tile, &s_ctl, err);
-        if (tid == 0) {
-            increc[tile] = excl + acc;
-            publish_flag(flags, tile, FLAG_INC);
-        }
-    }
-    if (tid == 0) {
-        uint32_t run = 0;
-        for (int w = 0; w < 8; ++w) {
-            const uint32_t c = s_wsum[w];
-            s_wsum[w] = run;
-            run += c;
-        }
-        s_excl = excl;
-        if (base + tile_n == n) *m_out = (int64_t)excl + acc;
-    }
-    __syncthreads();
-    uint32_t out = s_excl + s_wsum[warp];
+    uint32_t out = offs[blockIdx.x];
+    for (int w = 0; w < warp; ++w) out += s_wsum[w];
 #pragma unroll
     for (int j = 0; j < IPT; ++j) {
-        if ((ball[j] >> lane) & 1u) ids_out[out + __popc(ball[j] & lanemask_lt())] = id[j];
+        const int64_t pos = base + wbase + j * 32 + lane;
+        if ((ball[j] >> lane) & 1u) ids_out[out + __popc(ball[j] & lanemask_lt())] = ids[pos];
         out += __popc(ball[j]);
     }
 }
@@ -413,6 +451,10 @@ static int grid_for(int64_t work, int per_block, int cap) {
     return (int)g;
 }
 
+// Largest dynamic shared memory of k_transform: histogram rows for k = 8
+// 64-bit keys plus 2 cloud-id digit rows, and the 256-point coordinate tile.
+constexpr size_t TRANSFORM_SMEM_MAX = (size_t)(MAXK * 8 + 4) * RADIX * 4 + 256 * MAXK * 8;
+
 cudaError_t launch_transform(int dtype, const void* coords, int64_t n, int k, void* keys, int64_t stride,
                              const int64_t* cloud_start, int ncloud, uint32_t* cloud_plane,
                              int cloud_digits, uint32_t* hist, int* err, cudaStream_t s) {
@@ -420,28 +462,17 @@ cudaError_t launch_transform(int dtype, const void* coords, int64_t n, int k, vo
     const int D = dtype == 1 ? 8 : 4;
     const size_t tsz = dtype == 1 ? 8 : 4;
     const size_t smem = (size_t)(k * D + cloud_digits) * RADIX * 4 + 256 * k * tsz;
+    if (smem > TRANSFORM_SMEM_MAX) return cudaErrorInvalidValue;
     const int grid = grid_for(n, 256, 152 * 8);
-    cudaError_t e = cudaSuccess;
-    if (dtype == 0) {
-        auto kf = k_transform<int32_t, uint32_t>;
-        e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            kf<<<grid, 256, smem, s>>>((const int32_t*)coords, n, k, (uint32_t*)keys, stride, cloud_start,
-                                       ncloud, cloud_plane, cloud_digits, hist, err);
-    } else if (dtype == 1) {
-        auto kf = k_transform<int64_t, uint64_t>;
-        e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            kf<<<grid, 256, smem, s>>>((const int64_t*)coords, n, k, (uint64_t*)keys, stride, cloud_start,
-                                       ncloud, cloud_plane, cloud_digits, hist, err);
-    } else {
-        auto kf = k_transform<float, uint32_t>;
-        e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            kf<<<grid, 256, smem, s>>>((const float*)coords, n, k, (uint32_t*)keys, stride, cloud_start,
-                                       ncloud, cloud_plane, cloud_digits, hist, err);
-    }
-    if (e != cudaSuccess) return e;
+    if (dtype == 0)
+        k_transform<int32_t, uint32_t><<<grid, 256, smem, s>>>((const int32_t*)coords, n, k, (uint32_t*)keys, stride,
+                                                              cloud_start, ncloud, cloud_plane, cloud_digits, hist, err);
+    else if (dtype == 1)
+        k_transform<int64_t, uint64_t><<<grid, 256, smem, s>>>((const int64_t*)coords, n, k, (uint64_t*)keys, stride,
+                                                              cloud_start, ncloud, cloud_plane, cloud_digits, hist, err);
+    else
+        k_transform<float, uint32_t><<<grid, 256, smem, s>>>((const float*)coords, n, k, (uint32_t*)keys, stride,
+                                                            cloud_start, ncloud, cloud_plane, cloud_digits, hist, err);
     return cudaGetLastError();
 }
 
@@ -473,8 +504,6 @@ cudaError_t launch_sort_pass(int key64, int mode, const int64_t* count_ptr, int6
 #define KD_SORT_LAUNCH(KW, MODE)                                                                          \
     do {                                                                                                  \
         auto kf = k_sort_pass<KW, MODE>;                                                                  \
-        cudaError_t e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-        if (e != cudaSuccess) return e;                                                                   \
         kf<<<(unsigned)tiles, SORT_THREADS, smem, s>>>(count_ptr, (const KW*)key_src, gidx, (KW*)key_dst, \
                                                        pay, digit_base, shift, st, tile_ctr, err,         \
                                                        gather_limit);                                     \
@@ -492,26 +521,72 @@ cudaError_t launch_sort_pass(int key64, int mode, const int64_t* count_ptr, int6
     return cudaGetLastError();
 }
 
+// Dynamic shared memory limits, set once per process at their maxima (a
+// per-launch setting would race between threads launching on the same
+// kernels with different sizes).
+cudaError_t init_presort_kernels() {
+    cudaError_t e = cudaSuccess;
+    auto set = [&](const void* f, size_t bytes) {
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    };
+    set((const void*)k_transform<int32_t, uint32_t>, TRANSFORM_SMEM_MAX);
+    set((const void*)k_transform<int64_t, uint64_t>, TRANSFORM_SMEM_MAX);
+    set((const void*)k_transform<float, uint32_t>, TRANSFORM_SMEM_MAX);
+    const size_t s32 = (size_t)SORT_TILE * 10, s64 = (size_t)(SORT_TILE / 2) * 10;
+    set((const void*)k_sort_pass<uint32_t, KEY_DIRECT>, s32);
+    set((const void*)k_sort_pass<uint32_t, KEY_GATHER>, s32);
+    set((const void*)k_sort_pass<uint32_t, KEY_BUF>, s32);
+    set((const void*)k_sort_pass<uint64_t, KEY_DIRECT>, s64);
+    set((const void*)k_sort_pass<uint64_t, KEY_GATHER>, s64);
+    set((const void*)k_sort_pass<uint64_t, KEY_BUF>, s64);
+    return e;
+}
+
+cudaError_t launch_gather(int key64, const int64_t* count_ptr, int64_t max_count, const void* plane,
+                          const uint32_t* ids, void* out, int* err, cudaStream_t s) {
+    constexpr int GI = 8;
+    const int64_t blocks = (max_count + 256 * GI - 1) / (256 * GI);
+    if (blocks == 0) return cudaSuccess;
+    if (key64)
+        k_gather<uint64_t, GI><<<(unsigned)blocks, 256, 0, s>>>(count_ptr, (const uint64_t*)plane, ids, max_count,
+                                                               (uint64_t*)out, err);
+    else
+        k_gather<uint32_t, GI><<<(unsigned)blocks, 256, 0, s>>>(count_ptr, (const uint32_t*)plane, ids, max_count,
+                                                               (uint32_t*)out, err);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_digit_bases(const uint32_t* hist, int nrows, uint32_t* bases, cudaStream_t s) {
     if (nrows == 0) return cudaSuccess;
     k_digit_bases<<<nrows, RADIX, 0, s>>>(hist, bases);
     return cudaGetLastError();
 }
 
+// Scratch words dedup needs: keep bits, tile counts, tile offsets.
+size_t dedup_scratch_words(int64_t n) {
+    const int64_t tiles = (n + DEDUP_TILE - 1) / DEDUP_TILE;
+    return (size_t)((n + 31) / 32) + 2 * (size_t)tiles + 4;
+}
+
 cudaError_t launch_dedup(int key64, int64_t n, const void* key0, const uint32_t* ids, const void* keys,
-                         int64_t stride, int k, const uint32_t* cloud_plane, int cloud_digits,
-                         uint32_t* ids_out, uint32_t* status, uint32_t* tile_ctr, int64_t* m_out,
-                         uint32_t* hist, int32_t* mcloud, int* err, cudaStream_t s) {
-    const int64_t tiles = (n + 4095) / 4096;
+                         int64_t stride, int k, const uint32_t* cloud_plane, int cloud_digits, uint32_t* ids_out,
+                         uint32_t* scratch, int64_t* m_out, uint32_t* hist, int32_t* mcloud, int* err,
+                         cudaStream_t s) {
+    const int64_t tiles = (n + DEDUP_TILE - 1) / DEDUP_TILE;
     if (tiles == 0) return cudaSuccess;
+    uint32_t* keepbits = scratch;
+    uint32_t* tcnt = keepbits + (n + 31) / 32;
+    uint32_t* toff = tcnt + tiles;
     if (key64)
-        k_dedup<uint64_t><<<(unsigned)tiles, 256, 0, s>>>(n, (const uint64_t*)key0, ids, (const uint64_t*)keys,
-                                                         stride, k, cloud_plane, cloud_digits, ids_out,
-                                                         status, tile_ctr, m_out, hist, mcloud, err);
+        k_dedup_flags<uint64_t><<<(unsigned)tiles, 256, 0, s>>>(n, (const uint64_t*)key0, ids, (const uint64_t*)keys,
+                                                               stride, k, cloud_plane, cloud_digits, keepbits, tcnt,
+                                                               hist, mcloud, err);
     else
-        k_dedup<uint32_t><<<(unsigned)tiles, 256, 0, s>>>(n, (const uint32_t*)key0, ids, (const uint32_t*)keys,
-                                                         stride, k, cloud_plane, cloud_digits, ids_out,
-                                                         status, tile_ctr, m_out, hist, mcloud, err);
+        k_dedup_flags<uint32_t><<<(unsigned)tiles, 256, 0, s>>>(n, (const uint32_t*)key0, ids, (const uint32_t*)keys,
+                                                               stride, k, cloud_plane, cloud_digits, keepbits, tcnt,
+                                                               hist, mcloud, err);
+    k_tile_scan<<<1, 1024, 0, s>>>(tiles, tcnt, toff, m_out);
+    k_dedup_compact<<<(unsigned)tiles, 256, 0, s>>>(n, ids, keepbits, toff, ids_out);
     return cudaGetLastError();
 }
 

@@ -163,6 +163,40 @@ kd_status kd_destroy(kd_ctx *ctx);
  * next call on the context. */
 const char *kd_last_error(kd_ctx *ctx);
 
+/*
+ * kd_presort_noalloc -- the presort of kd_presort (Section 2.1: index arrays
+ * sorted by the k cyclic super keys, duplicate tuples removed) for one small
+ * cloud, without allocating any memory.  The paper has no counterpart: it
+ * exists for callers that cannot let a library allocate during a call, such
+ * as a process whose device memory is all owned by its own allocator, or a
+ * latency-bound loop that cannot absorb a pool growth or a device-wide
+ * synchronising free.  Its workspace is one static device array of about
+ * 1 MiB per device, sized for KD_NOALLOC_MAX_N tuples of up to KD_MAX_K
+ * coordinates.
+ *
+ *  cloud       coordinates in device memory (cloud->on_device must be 1),
+ *              n <= KD_NOALLOC_MAX_N; larger clouds return KD_EINVAL with
+ *              the limit in kd_last_error (use kd_presort for them).
+ *  arrays_out  device memory, k rows of n int32 (row stride n): row d
+ *              receives the deduplicated super-key-d order, the same values
+ *              kd_handle_arrays gives for the same cloud, in its first m
+ *              entries; the rest of the row is left untouched.
+ *  m_out       device memory, one int32: m, or KD_ENAN if a float
+ *              coordinate is NaN (arrays_out is then left untouched).
+ *
+ * Asynchronous: the work is ordered on the context's stream and the call
+ * returns without waiting; read *m_out after the stream.  Argument errors
+ * (KD_EINVAL) are found on the host before anything is enqueued.  The first
+ * call on a device does a one-time set-up (the address of the static
+ * workspace and a kernel attribute), so a caller that records its stream
+ * into a graph should make one call before it starts recording.  All calls
+ * on a device share the one workspace: calls whose work can overlap on the
+ * device (different streams, or threads without ordering between them)
+ * race and give wrong results; order them on one stream.
+ */
+#define KD_NOALLOC_MAX_N 16384
+kd_status kd_presort_noalloc(kd_ctx *ctx, const kd_cloud *cloud, int32_t *arrays_out, int32_t *m_out);
+
 /* Kernels launched by this context since creation (instrumentation). */
 int64_t kd_launch_count(kd_ctx *ctx);
 

@@ -213,6 +213,25 @@ def kd_serving_stats(ctx: Context) -> dict:
     return {"completed": n.value, "p50_us": p50.value, "p99_us": p99.value}
 
 
+def kd_presort_noalloc(ctx: Context, coords, arrays_out=None, m_out=None):
+    """kd_presort_noalloc: presort + duplicate removal of one small cloud
+    (device tensor, n <= KD_NOALLOC_MAX_N) into caller-owned device buffers;
+    the library allocates nothing.  ``arrays_out`` (k x n int32) and
+    ``m_out`` (1 int32) are made here when not given.  Asynchronous on the
+    context's stream: read ``m_out`` (m, or KD_ENAN) after the stream.
+    Returns (arrays_out, m_out)."""
+    c, keep = _cloud(coords)
+    dev = torch.device("cuda", ctx.device)
+    if arrays_out is None:
+        arrays_out = torch.empty((c.k, max(c.n, 1)), dtype=torch.int32, device=dev)
+    if m_out is None:
+        m_out = torch.empty(1, dtype=torch.int32, device=dev)
+    ctx.check(_lib.load().kd_presort_noalloc(ctx.ptr, ctypes.byref(c), ctypes.c_void_p(arrays_out.data_ptr()),
+                                             ctypes.c_void_p(m_out.data_ptr())))
+    del keep
+    return arrays_out, m_out
+
+
 def kd_launch_count(ctx: Context) -> int:
     return int(_lib.load().kd_launch_count(ctx.ptr))
 

@@ -1053,6 +1053,14 @@ kd_status start_serving(kd_ctx* ctx) {
 
 }  // namespace
 
+// Context access for the entry point in kd_noalloc.cu.
+namespace kd {
+int ctx_device(const kd_ctx* ctx) { return ctx->device; }
+cudaStream_t ctx_stream(const kd_ctx* ctx) { return ctx->stream; }
+void ctx_set_error(kd_ctx* ctx, const std::string& msg) { ctx->last_error = msg; }
+void ctx_add_launches(kd_ctx* ctx, int n) { ctx->launches += n; }
+}  // namespace kd
+
 // =================================================================== C ABI
 extern "C" {
 

@@ -50,7 +50,10 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--n", type=int, default=N_POINTS, help="points per cloud (default 2^26)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample", type=int, default=1 << 21, help="oracle sample size (points)")
+    ap.add_argument("--cpu-sample", type=int, default=1 << 24,
+                    help="cpu_baseline: oracle sample size in points (2^24: about 15 s of one core)")
+    ap.add_argument("--ref-sample", type=int, default=1 << 21,
+                    help="--impl reference: oracle sample per step in points (about 2 s of one core)")
     ap.add_argument("--mode", default="plain", choices=["plain", "batched", "served"],
                     help="plain: the 2^26 build (default line); batched: 4096 uneven clouds in one call "
                          "vs per-cloud calls; served: a Poisson request stream through kd_submit")
@@ -64,6 +67,23 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def max_over_ranks(x: float, world: int, device="cpu") -> float:
+    """The maximum of x over all ranks (x itself at world size 1)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world: int, points_per_rank: int, seconds_per_step: float) -> float:
+    """Points/s of the whole job: every rank builds its own replica per step,
+    and the step takes as long as the slowest rank."""
+    return world * points_per_rank / seconds_per_step
 
 
 def measured_peaks():
@@ -168,7 +188,7 @@ def run_reference(args, rank, world):
         return
     import kdgen
     import oracle
-    sample = min(args.cpu_sample, args.n)
+    sample = min(args.ref_sample, args.n)
     coords = kdgen.large_gmm(n=sample)
     for _ in range(args.warmup):
         oracle.build_tree(coords)
@@ -348,13 +368,8 @@ def main():
     ms_total = e0.elapsed_time(e1)
     launches = api.kd_launch_count(ctx) - launches0
     stats = api.kd_kernel_stats(ctx)
-    ms_per_step = ms_total / args.steps
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([ms_per_step], device=f"cuda:{dev}")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_per_step = float(tt.item())
-    value = world * n / (ms_per_step / 1000.0)
+    ms_per_step = max_over_ranks(ms_total / args.steps, world, f"cuda:{dev}")
+    value = whole_job_value(world, n, ms_per_step / 1000.0)
 
     # end to end: pinned host coordinates in, whole tree back to pinned host
     out_node = torch.empty(n, dtype=torch.int32).pin_memory()
@@ -384,12 +399,7 @@ def main():
     for _ in range(e2e_steps):
         mh = e2e_step()
     torch.cuda.synchronize(dev)
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([e2e_s], device=f"cuda:{dev}")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world, f"cuda:{dev}")
     assert mh == m
     ctx_h.close()
 
@@ -429,7 +439,7 @@ def main():
                         "gbs": (v["bytes"] / (v["ms"] / 1000.0) / 1e9) if v["ms"] else None}
                     for f, v in stats.items() if v["launches"]},
         "clocks": clk,
-        "e2e": {"value": world * n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": n * K * 4,
+        "e2e": {"value": whole_job_value(world, n, e2e_s), "unit": UNIT, "h2d_bytes_per_step": n * K * 4,
                 "d2h_bytes_per_step": m * 13},
         "gpu_launches": launches,
     }

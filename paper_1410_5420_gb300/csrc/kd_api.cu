@@ -364,14 +364,14 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
     H->perm0 = (uint32_t*)p;
     const size_t rec_planes = k >= 2 ? (size_t)k * k : 0;
     if (rec_planes) {
-        kd_status st = dev_alloc(ctx, &H->rec_block, rec_planes * N * 4);
+        kd_status st = dev_alloc(ctx, &H->rec_block, (rec_planes * pad4(N) + 4) * 4);
         if (st != KD_OK) {
             dev_free(ctx, H->perm0);
             dev_free(ctx, H->d_m);
             return st;
         }
         for (int d = 0; d < k; ++d)
-            for (int q = 0; q < k; ++q) H->rec.p[d][q] = (uint32_t*)H->rec_block + ((size_t)d * k + q) * N;
+            for (int q = 0; q < k; ++q) H->rec.p[d][q] = (uint32_t*)H->rec_block + ((size_t)d * k + q) * pad4(N);
     }
     H->bytes = (size_t)N * 4 + rec_planes * N * 4;
     struct Guard {
@@ -873,10 +873,12 @@ kd_status build_batch(kd_ctx* ctx, kd_presorted* H, kd_tree* outs) {
         for (int p = 0; p < k; ++p) bufs.p[d][0][p] = H->rec.p[d][p];
     if (need_bufs) {
         uint32_t* blk = nullptr;
-        CKS(S.get(&blk, (size_t)2 * k * k * M * 4));
+        // plane strides padded to 16 bytes, and 16 bytes of slack at the end:
+        // the level passes stage tiles with 16-byte-aligned bulk copies
+        CKS(S.get(&blk, ((size_t)2 * k * k * pad4(M) + 4) * 4));
         for (int b = 1; b <= 2; ++b)
             for (int d = 0; d < k; ++d)
-                for (int p = 0; p < k; ++p) bufs.p[d][b][p] = blk + (((size_t)(b - 1) * k + d) * k + p) * M;
+                for (int p = 0; p < k; ++p) bufs.p[d][b][p] = blk + (((size_t)(b - 1) * k + d) * k + p) * pad4(M);
     }
 
     // upload tables -------------------------------------------------------
@@ -923,7 +925,7 @@ kd_status build_batch(kd_ctx* ctx, kd_presorted* H, kd_tree* outs) {
     for (size_t st = 0; st < step_jobs.size(); ++st) {
         const int F = step_jobs[st][0].lev_out - step_jobs[st][0].lev_in;
         LaunchTimer lt(ctx, F_LEVEL, step_elems[st], nullptr, 8.0 * k + 4.0 * F);
-        ctx->launches += 2;  // count pass and scan
+        ctx->launches += 3;  // tile records, count pass and scan
         CK(launch_level_pass(k, bufs, step_q[st], d_jobs + job_off[st], (int)step_jobs[st].size(),
                              (int)step_ntiles[st], d_cd, medr, H->perm0, d_status, d_err, s));
     }

@@ -28,6 +28,8 @@
 //                 element termination).
 //   k_top_nodes   children and split dimension of the nodes above the
 //                 finisher level (pure functions of m and the address).
+#include <algorithm>
+
 #include "kd_internal.cuh"
 
 namespace kd {
@@ -60,118 +62,311 @@ __device__ __forceinline__ int tile_segments(int32_t pos0, int32_t npos, int32_t
     return ns;
 }
 
-// Medians a tile needs: for each of its level-lev_in segments j, the
-// medians of levels lev_in .. lev_in+F-1 below it, heap-indexed (node 1 is
-// the segment itself, children of node h are 2h and 2h+1).
-template <int NBMAX>
-__device__ __forceinline__ void load_tile_medians(uint32_t (*s_med)[NBMAX], int ns, const int32_t* segidx, int F,
-                                                  int lev_in, const uint32_t* __restrict__ medr, int64_t medr_off) {
+// ------------------------------------------------------------ level step
+// A level step is four launches:
+//   k_level_tiles  one warp per tile: the tile's level-lev_in segments and
+//                  the medians of the F decision levels below each of them,
+//                  written as one tile record;
+//   k_level_count  per tile, the bucket counts of its last segment;
+//   k_level_scan   segmented scan of those counts over tiles;
+//   k_level_pass   the move: route, stable warp ranking, scatter.
+// The count and move passes are persistent: a producer warp takes tile ids
+// from a counter and streams each tile's record and plane slices into a
+// shared-memory stage with bulk async copies (full/empty mbarriers), while
+// eight consumer warps work on the previous stage.
+//
+// Tile record (u32 words): [0] ns, [1..4] segment lo, [5..8] hi, [9..12]
+// segment index, [13] pos0, [14] npos, [15] job; then at TR_HEAD +
+// x * NBMAX + h the median rank of heap node h (1 = the segment itself,
+// children 2h, 2h+1) of segment x.
+constexpr int TR_HEAD = 16;
+constexpr int LEVEL_STAGES = 2;
+constexpr int PLANE_SLACK = 8;  // staged slice = tile rounded out to 16-byte boundaries
+constexpr int LEVEL_BLOCK = LEVEL_THREADS + 32;  // eight consumer warps + one producer warp
+
+__host__ __device__ constexpr int level_ipt_of(int K) { return K <= 4 ? 8 : 4; }
+__host__ __device__ constexpr int level_tile_of(int K) { return LEVEL_THREADS * level_ipt_of(K); }
+__host__ __device__ constexpr int level_nbp(int K) { return (1 << (K - 1)) < 4 ? 4 : (1 << (K - 1)); }
+__host__ __device__ constexpr int trec_words(int K) { return TR_HEAD + LEVEL_NSMAX * (1 << (K - 1)); }
+
+struct StageMeta {
+    int32_t t;  // tile, or -1: no more tiles
+    int32_t cloud, lev_in, F, src_buf, dst_buf, write_med;
+    int32_t shift;  // offset of the tile's first element in the staged slices
+    int32_t pos0, npos, m, has_incl;
+    int64_t goff;
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// Barrier 1 over the consumer warps only (the producer warp never joins).
+__device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(LEVEL_THREADS) : "memory"); }
+__device__ __forceinline__ bool consumer_or(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n barrier.cta.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(LEVEL_THREADS)
+        : "memory");
+    return r != 0;
+}
+
+template <int K>
+__global__ void __launch_bounds__(256) k_level_tiles(const LevelJob* __restrict__ jobs, int njobs, int ntiles,
+                                                     const CloudDev* __restrict__ clouds,
+                                                     const uint32_t* __restrict__ medr, uint32_t* __restrict__ trec,
+                                                     uint32_t* __restrict__ ctrs, int* __restrict__ err) {
+    constexpr int NBMAX = 1 << (K - 1);
+    constexpr int TW = trec_words(K);
+    constexpr int TILE = level_tile_of(K);
+    if (blockIdx.x == 0 && threadIdx.x < 2) ctrs[threadIdx.x] = 0;  // tile counters of the two passes
+    const int lane = threadIdx.x & 31;
+    const int t = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (t >= ntiles) return;
+    int lo = 0, hi = njobs;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (jobs[mid].tile_begin <= t) lo = mid; else hi = mid;
+    }
+    const LevelJob J = jobs[lo];
+    const int32_t m = clouds[J.cloud].m;
+    const int64_t medr_off = clouds[J.cloud].medr_off;
+    const int32_t pos0 = (int32_t)((int64_t)(t - J.tile_begin) * TILE);
+    const int32_t npos = (m - pos0) < TILE ? (m - pos0) : TILE;
+    uint32_t* rec = trec + (int64_t)t * TW;
+    int32_t slo[LEVEL_NSMAX], shi[LEVEL_NSMAX], sidx[LEVEL_NSMAX];
+    int ns = 0;
+    if (lane == 0) {
+        ns = tile_segments(pos0, npos, m, J.lev_in, slo, shi, sidx, err);
+        rec[0] = (uint32_t)ns;
+        for (int x = 0; x < LEVEL_NSMAX; ++x) {
+            rec[1 + x] = (uint32_t)(x < ns ? slo[x] : 0);
+            rec[5 + x] = (uint32_t)(x < ns ? shi[x] : -1);
+            rec[9 + x] = (uint32_t)(x < ns ? sidx[x] : 0);
+        }
+        rec[13] = (uint32_t)pos0;
+        rec[14] = (uint32_t)npos;
+        rec[15] = (uint32_t)lo;
+    }
+    ns = __shfl_sync(0xffffffffu, ns, 0);
+    int32_t seg[LEVEL_NSMAX];
+#pragma unroll
+    for (int x = 0; x < LEVEL_NSMAX; ++x) seg[x] = __shfl_sync(0xffffffffu, lane == 0 && x < ns ? sidx[x] : 0, 0);
+    const int F = J.lev_out - J.lev_in;
     const int per = (1 << F) - 1;
-    for (int e = threadIdx.x; e < ns * per; e += blockDim.x) {
+    for (int e = lane; e < ns * per; e += 32) {
         const int j = e / per;
         const int h = e - j * per + 1;
         const int f = 31 - __clz(h);
-        const int64_t gseg = ((int64_t)segidx[j] << f) + (h - (1 << f));
-        s_med[j][h] = medr[medr_off + ((int64_t)1 << (lev_in + f)) - 1 + gseg];
+        int32_t sj = seg[0];
+#pragma unroll
+        for (int x = 1; x < LEVEL_NSMAX; ++x)
+            if (j == x) sj = seg[x];
+        const int64_t gseg = ((int64_t)sj << f) + (h - (1 << f));
+        rec[TR_HEAD + j * NBMAX + h] = medr[medr_off + ((int64_t)1 << (J.lev_in + f)) - 1 + gseg];
     }
 }
 
-// Route one element of segment slot sj through F levels: r[f] is its rank in
-// super key (lev_in + f) mod K.  Returns the digit (sj * 2^F + bucket) and
-// its final segment [flo, fhi], or INV if it is the median of one of these
-// levels (a node: not copied).
-template <int K, int NBMAX>
-__device__ __forceinline__ uint32_t route(const uint32_t (&r)[K], int F, int sj, int32_t a, int32_t z,
-                                          const uint32_t (*s_med)[NBMAX], int32_t& flo, int32_t& fhi) {
+// Producer of the persistent level kernels (lane 0 of the last warp): for
+// each tile it takes, waits until the stage is free, records the tile's
+// facts in the stage's meta entry and starts the bulk copies of the tile
+// record, `nplanes` plane slices and (move pass) the scanned counts of the
+// previous tile.  Ends by publishing t = -1.
+template <int K, bool MOVE>
+__device__ __forceinline__ void level_producer(const AllBufs& bufs, int q, const LevelJob* __restrict__ jobs,
+                                               int njobs, int ntiles, const CloudDev* __restrict__ clouds,
+                                               const uint32_t* __restrict__ trec, const uint32_t* __restrict__ incl,
+                                               uint32_t* ctr, uint32_t* smem, StageMeta* meta, uint64_t* full,
+                                               uint64_t* empty, int* err) {
+    constexpr int TW = trec_words(K);
+    constexpr int TILE = level_tile_of(K);
+    constexpr int PST = TILE + PLANE_SLACK;
+    constexpr int NP = MOVE ? K : K - 1;
+    constexpr int NBP = level_nbp(K);
+    constexpr int SW = TW + NBP + NP * PST;
+    for (int it = 0;; ++it) {
+        const int s = it % LEVEL_STAGES;
+        const uint32_t ph = (uint32_t)(it / LEVEL_STAGES) & 1u;
+        if (it >= LEVEL_STAGES && !mbar_wait(&empty[s], ph ^ 1u)) {
+            atomicOr(err, ERR_TIMEOUT);
+            meta[s].t = -1;
+            mbar_arrive(&full[s]);
+            return;
+        }
+        const int t = (int)atomicAdd(ctr, 1u);
+        StageMeta M;
+        M.t = t < ntiles ? t : -1;
+        if (M.t < 0) {
+            meta[s] = M;
+            mbar_arrive(&full[s]);
+            return;
+        }
+        const LevelTile T = job_tile(jobs, njobs, t, TILE, clouds);
+        M.cloud = T.cloud;
+        M.lev_in = T.lev_in;
+        M.F = T.lev_out - T.lev_in;
+        M.src_buf = T.src_buf;
+        M.dst_buf = T.dst_buf;
+        M.write_med = T.write_med;
+        M.pos0 = (int32_t)T.pos0;
+        M.npos = T.npos;
+        M.m = clouds[T.cloud].m;
+        M.goff = clouds[T.cloud].off;
+        M.has_incl = MOVE && T.pos0 > 0;
+        const int64_t g0 = M.goff + T.pos0;
+        const int64_t a0 = g0 & ~(int64_t)3;
+        const int64_t e1 = (g0 + T.npos + 3) & ~(int64_t)3;
+        M.shift = (int32_t)(g0 - a0);
+        const uint32_t pb = (uint32_t)((e1 - a0) * 4);
+        const int npl = MOVE ? K : M.F;
+        meta[s] = M;
+        uint32_t* st = smem + (size_t)s * SW;
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&full[s], TW * 4 + (M.has_incl ? NBP * 4 : 0) + (uint32_t)npl * pb);
+        bulk_g2s(st, trec + (int64_t)t * TW, TW * 4, &full[s]);
+        if (M.has_incl) bulk_g2s(st + TW, incl + (int64_t)(t - 1) * NBP, NBP * 4, &full[s]);
+        for (int f = 0; f < npl; ++f)
+            bulk_g2s(st + TW + NBP + f * PST, bufs.p[q][T.src_buf][(T.lev_in + f) % K] + a0, pb, &full[s]);
+    }
+}
+
+template <int K>
+constexpr size_t level_smem_bytes(bool move) {
+    return (size_t)LEVEL_STAGES *
+           (trec_words(K) + level_nbp(K) + (move ? K : K - 1) * (level_tile_of(K) + PLANE_SLACK)) * 4;
+}
+
+// Segment slot of cloud-local position pos among the tile's ns segments
+// [lo[x], hi[x]]; -1 for an address that is a node of a shallower level
+// (no element there).
+__device__ __forceinline__ int tile_slot(const int32_t (&lo)[LEVEL_NSMAX], const int32_t (&hi)[LEVEL_NSMAX], int ns,
+                                         int32_t pos) {
+    int sj = 0;
+    int32_t a = lo[0], z = hi[0];
+#pragma unroll
+    for (int x = 1; x < LEVEL_NSMAX; ++x)
+        if (x < ns && pos >= lo[x]) {
+            sj = x;
+            a = lo[x];
+            z = hi[x];
+        }
+    return (ns > 0 && pos >= a && pos <= z) ? sj : -1;
+}
+
+// Segment bounds of a tile record, in registers.
+__device__ __forceinline__ void tile_bounds(const uint32_t* rec, int32_t (&lo)[LEVEL_NSMAX],
+                                            int32_t (&hi)[LEVEL_NSMAX]) {
+#pragma unroll
+    for (int x = 0; x < LEVEL_NSMAX; ++x) {
+        lo[x] = (int32_t)rec[1 + x];
+        hi[x] = (int32_t)rec[5 + x];
+    }
+}
+
+// Bucket of an element of segment slot sj after F decision levels: r[f] is
+// its rank in super key (lev_in + f) mod K, compared with the medians of
+// the tile record; INV for an element equal to a median (the node itself).
+template <int K>
+__device__ __forceinline__ uint32_t route_rec(const uint32_t (&r)[K], int F, int sj, const uint32_t* rec) {
+    constexpr int NBMAX = 1 << (K - 1);
+    const uint32_t* med = rec + TR_HEAD + sj * NBMAX;
     uint32_t h = 1;
 #pragma unroll
     for (int f = 0; f < K - 1; ++f) {
         if (f < F) {
-            const int32_t mid = a + ((z - a) >> 1);
-            const uint32_t mv = s_med[sj][h];
-            if (r[f] < mv) {
-                z = mid - 1;
-                h = 2 * h;
-            } else if (r[f] > mv) {
-                a = mid + 1;
-                h = 2 * h + 1;
-            } else {
-                return INV;
-            }
+            const uint32_t mv = med[h];
+            if (r[f] == mv) return INV;
+            h = 2 * h + (r[f] > mv ? 1u : 0u);
         }
     }
-    flo = a;
-    fhi = z;
     return ((uint32_t)sj << F) + (h - (1u << F));
 }
 
-// Per-tile segment list written by the count pass for the move pass:
-// [0] ns, [1..4] lo, [5..8] hi, [9..12] segment index.
-constexpr int TILEINFO = 16;
-
-// Count pass of a level step: per tile, the bucket counts of its last
-// segment (cnt[t][b]) and whether that segment starts inside the tile
-// (head[t]).  Reads only the F decision planes.
-template <int K, int IPT>
-__global__ void __launch_bounds__(LEVEL_THREADS)
+// Count pass: per tile, the bucket counts of its last segment (cnt[t][b],
+// row stride level_nbp(K)) and whether that segment starts inside the tile
+// (head[t]).  Reads the F decision planes only.
+template <int K>
+__global__ void __launch_bounds__(LEVEL_BLOCK)
     k_level_count(const __grid_constant__ AllBufs bufs, int q, const LevelJob* __restrict__ jobs, int njobs,
-                  const CloudDev* __restrict__ clouds, const uint32_t* __restrict__ medr, uint32_t* __restrict__ cnt,
-                  uint32_t* __restrict__ head, int32_t* __restrict__ tinfo, int* __restrict__ err) {
+                  int ntiles, const CloudDev* __restrict__ clouds, const uint32_t* __restrict__ trec,
+                  uint32_t* __restrict__ cnt, uint32_t* __restrict__ head, uint32_t* __restrict__ ctr,
+                  int* __restrict__ err) {
+    constexpr int IPT = level_ipt_of(K);
+    constexpr int TILE = level_tile_of(K);
+    constexpr int PST = TILE + PLANE_SLACK;
     constexpr int NBMAX = 1 << (K - 1);
     constexpr int NDMAX = LEVEL_NSMAX * NBMAX;
-    __shared__ uint32_t s_cnt[NDMAX];
-    __shared__ uint32_t s_med[LEVEL_NSMAX][NBMAX];
-    __shared__ int32_t s_seglo[LEVEL_NSMAX], s_seghi[LEVEL_NSMAX], s_segidx[LEVEL_NSMAX];
-    __shared__ int s_ns;
-    const int tid = threadIdx.x;
-    const int t = blockIdx.x;
-    const LevelTile T = job_tile(jobs, njobs, t, LEVEL_THREADS * IPT, clouds);
-    const CloudDev& C = clouds[T.cloud];
-    const int F = T.lev_out - T.lev_in;
-    const int NB = 1 << F;
-    const int32_t pos0 = (int32_t)T.pos0;
-    for (int i = tid; i < NDMAX; i += LEVEL_THREADS) s_cnt[i] = 0;
+    constexpr int NBP = level_nbp(K);
+    constexpr int TW = trec_words(K);
+    constexpr int SW = TW + NBP + (K - 1) * PST;
+    extern __shared__ __align__(128) uint32_t lsm[];
+    __shared__ __align__(8) uint64_t full[LEVEL_STAGES], empty[LEVEL_STAGES];
+    __shared__ StageMeta meta[LEVEL_STAGES];
+    __shared__ uint32_t s_cnt[LEVEL_STAGES][NDMAX];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
-        const int ns = tile_segments(pos0, T.npos, C.m, T.lev_in, s_seglo, s_seghi, s_segidx, err);
-        s_ns = ns;
-        int32_t* ti = tinfo + (int64_t)t * TILEINFO;
-        ti[0] = ns;
-        for (int x = 0; x < LEVEL_NSMAX; ++x) {
-            ti[1 + x] = x < ns ? s_seglo[x] : 0;
-            ti[5 + x] = x < ns ? s_seghi[x] : -1;
-            ti[9 + x] = x < ns ? s_segidx[x] : 0;
+        for (int s = 0; s < LEVEL_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], LEVEL_WARPS);
         }
+        fence_mbar_init();
     }
+    for (int i = tid; i < LEVEL_STAGES * NDMAX; i += LEVEL_BLOCK) (&s_cnt[0][0])[i] = 0;
     __syncthreads();
-    const int ns = s_ns;
-    load_tile_medians<NBMAX>(s_med, ns, s_segidx, F, T.lev_in, medr, C.medr_off);
-    __syncthreads();
-    const int64_t goff = C.off;
-    const uint32_t* planes[K];
-#pragma unroll
-    for (int f = 0; f < K; ++f) planes[f] = bufs.p[q][T.src_buf][(T.lev_in + f) % K];
-    for (int o = tid; o < T.npos; o += LEVEL_THREADS) {
-        const int32_t pos = pos0 + o;
-        int sj = -1;
-#pragma unroll
-        for (int x = 0; x < LEVEL_NSMAX; ++x)
-            if (x < ns && pos >= s_seglo[x] && pos <= s_seghi[x]) sj = x;
-        if (sj < 0) continue;
-        uint32_t r[K];
-#pragma unroll
-        for (int f = 0; f < K; ++f) r[f] = (f < F) ? planes[f][goff + pos] : 0u;
-        int32_t flo, fhi;
-        const uint32_t d = route<K, NBMAX>(r, F, sj, s_seglo[sj], s_seghi[sj], s_med, flo, fhi);
-        if (d != INV) atomicAdd(&s_cnt[d], 1u);
+    if (warp == LEVEL_WARPS) {
+        if (lane == 0)
+            level_producer<K, false>(bufs, q, jobs, njobs, ntiles, clouds, trec, nullptr, ctr, lsm, meta, full, empty,
+                                     err);
+        return;
     }
-    __syncthreads();
-    if (tid < NBMAX) cnt[(int64_t)t * NBMAX + tid] = (ns > 0 && tid < NB) ? s_cnt[(ns - 1) * NB + tid] : 0u;
-    if (tid == 0) head[t] = (ns == 1 && s_seglo[0] < pos0) ? 0u : 1u;
+    const int wbase = warp * 32 * IPT;
+    for (int it = 0;; ++it) {
+        const int s = it % LEVEL_STAGES;
+        const bool ok = mbar_wait(&full[s], (uint32_t)(it / LEVEL_STAGES) & 1u);
+        if (consumer_or(!ok)) {
+            if (tid == 0) atomicOr(err, ERR_TIMEOUT);
+            break;
+        }
+        const StageMeta M = meta[s];
+        if (M.t < 0) break;
+        const uint32_t* st = lsm + (size_t)s * SW;
+        const uint32_t* rec = st;
+        const int ns = (int)rec[0];
+        int32_t tlo[LEVEL_NSMAX], thi[LEVEL_NSMAX];
+        tile_bounds(rec, tlo, thi);
+        const int32_t lo0 = tlo[0];
+        const int F = M.F;
+#pragma unroll
+        for (int j = 0; j < IPT; ++j) {
+            const int o = wbase + j * 32 + lane;
+            if (o < M.npos) {
+                const int32_t pos = M.pos0 + o;
+                const int sj = tile_slot(tlo, thi, ns, pos);
+                if (sj >= 0) {
+                    uint32_t r[K];
+#pragma unroll
+                    for (int f = 0; f < K; ++f) r[f] = (f < F) ? st[TW + NBP + f * PST + M.shift + o] : 0u;
+                    const uint32_t d = route_rec<K>(r, F, sj, rec);
+                    if (d != INV) atomicAdd(&s_cnt[s][d], 1u);
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+        consumer_sync();
+        const int NB = 1 << F;
+        if (tid < NBP) cnt[(int64_t)M.t * NBP + tid] = (ns > 0 && tid < NB) ? s_cnt[s][(ns - 1) * NB + tid] : 0u;
+        if (tid == 0) head[M.t] = (ns == 1 && lo0 < M.pos0) ? 0u : 1u;
+        // the next stage's counters were last read before this iteration's first barrier
+        for (int i = tid; i < NDMAX; i += LEVEL_THREADS) s_cnt[(s + 1) % LEVEL_STAGES][i] = 0;
+    }
 }
 
 // Segmented inclusive scan over the tiles of a level step, one block per
-// bucket: incl[t][b] = cnt[t][b] + (head[t] ? 0 : incl[t-1][b]).
-__global__ void __launch_bounds__(1024) k_level_scan(int ntiles, int nbmax, const uint32_t* __restrict__ cnt,
+// bucket: incl[t][b] = cnt[t][b] + (head[t] ? 0 : incl[t-1][b]) (row stride
+// `stride`).
+__global__ void __launch_bounds__(1024) k_level_scan(int ntiles, int stride, const uint32_t* __restrict__ cnt,
                                                      const uint32_t* __restrict__ head, uint32_t* __restrict__ incl) {
     __shared__ uint32_t s_f[32], s_v[32];
     const int b = blockIdx.x;
@@ -180,7 +375,7 @@ __global__ void __launch_bounds__(1024) k_level_scan(int ntiles, int nbmax, cons
     for (int t0 = 0; t0 < ntiles; t0 += 1024) {
         const int t = t0 + tid;
         uint32_t f = t < ntiles ? head[t] : 1u;
-        uint32_t v = t < ntiles ? cnt[(int64_t)t * nbmax + b] : 0u;
+        uint32_t v = t < ntiles ? cnt[(int64_t)t * stride + b] : 0u;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t f2 = __shfl_up_sync(0xffffffffu, f, o);
@@ -218,155 +413,197 @@ __global__ void __launch_bounds__(1024) k_level_scan(int ntiles, int nbmax, cons
         }
         if (!pf) pv += carry;
         if (!f) v += pv;
-        if (t < ntiles) incl[(int64_t)t * nbmax + b] = v;
+        if (t < ntiles) incl[(int64_t)t * stride + b] = v;
         const uint32_t lastf = s_f[31], lastv = s_v[31];
         carry = lastf ? lastv : carry + lastv;
         __syncthreads();
     }
 }
 
+// Value of the rotated plane holding super key p: v[f] is plane (lev_in + f) mod K.
 template <int K, int IPT>
-__global__ void __launch_bounds__(LEVEL_THREADS, 3)
+__device__ __forceinline__ uint32_t plane_value(const uint32_t (&v)[K][IPT], int j, int f_sel) {
+    uint32_t x = 0;
+#pragma unroll
+    for (int f = 0; f < K; ++f)
+        if (f == f_sel) x = v[f][j];
+    return x;
+}
+
+// Move pass: each element of array q goes to its bucket of the tile's
+// segments after F decision levels, keeping its order (stable warp
+// ranking), with all K planes.  The element landing on the middle of a
+// final segment of level lev_out (its primary level) is that segment's
+// median: its rank in super key q goes to medr and its tuple to the node.
+template <int K>
+__global__ void __launch_bounds__(LEVEL_BLOCK, K <= 3 ? 3 : 2)
     k_level_pass(const __grid_constant__ AllBufs bufs, int q, const LevelJob* __restrict__ jobs, int njobs,
-                 const CloudDev* __restrict__ clouds, uint32_t* __restrict__ medr,
-                 const uint32_t* __restrict__ perm0, const uint32_t* __restrict__ incl,
-                 const int32_t* __restrict__ tinfo, int* __restrict__ err) {
+                 int ntiles, const CloudDev* __restrict__ clouds, uint32_t* __restrict__ medr,
+                 const uint32_t* __restrict__ perm0, const uint32_t* __restrict__ trec,
+                 const uint32_t* __restrict__ incl, uint32_t* __restrict__ ctr, int* __restrict__ err) {
+    constexpr int IPT = level_ipt_of(K);
+    constexpr int TILE = level_tile_of(K);
+    constexpr int PST = TILE + PLANE_SLACK;
     constexpr int NBMAX = 1 << (K - 1);
     constexpr int NDMAX = LEVEL_NSMAX * NBMAX;
-    constexpr int DBITS = 2 + (K - 1) + 1;  // log2(NSMAX) + log2(NBMAX) + marker bit
+    constexpr int NBP = level_nbp(K);
+    constexpr int TW = trec_words(K);
+    constexpr int SW = TW + NBP + K * PST;
+    constexpr int DBITS = 2 + (K - 1) + 1;  // enough for digits 0 .. LEVEL_NSMAX * NBMAX (the marker)
+    extern __shared__ __align__(128) uint32_t lsm[];
+    __shared__ __align__(8) uint64_t full[LEVEL_STAGES], empty[LEVEL_STAGES];
+    __shared__ StageMeta meta[LEVEL_STAGES];
     __shared__ uint32_t s_wc[LEVEL_WARPS][NDMAX];
-    __shared__ int32_t s_dbase[NDMAX];
-    __shared__ uint32_t s_med[LEVEL_NSMAX][NBMAX];
-    __shared__ int32_t s_ti[TILEINFO];
-
+    __shared__ int32_t s_dbase[NDMAX], s_dlo[NDMAX], s_dhi[NDMAX], s_dmid[NDMAX];
+    __shared__ int32_t s_segidx[LEVEL_NSMAX];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int t = blockIdx.x;
-    const LevelTile T = job_tile(jobs, njobs, t, LEVEL_THREADS * IPT, clouds);
-    const CloudDev& C = clouds[T.cloud];
-    const int F = T.lev_out - T.lev_in;
-    const int NB = 1 << F;
-    const int32_t m = C.m;
-    const int32_t pos0 = (int32_t)T.pos0;
-    const int64_t goff = C.off;
-    if (tid < TILEINFO) s_ti[tid] = tinfo[(int64_t)t * TILEINFO + tid];
-    for (int i = tid; i < LEVEL_WARPS * NDMAX; i += LEVEL_THREADS) (&s_wc[0][0])[i] = 0;
+    if (tid == 0) {
+        for (int s = 0; s < LEVEL_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], LEVEL_WARPS);
+        }
+        fence_mbar_init();
+    }
+    for (int i = tid; i < LEVEL_WARPS * NDMAX; i += LEVEL_BLOCK) (&s_wc[0][0])[i] = 0;
     __syncthreads();
-    const int ns = s_ti[0];
-    load_tile_medians<NBMAX>(s_med, ns, s_ti + 9, F, T.lev_in, medr, C.medr_off);
-    __syncthreads();
-
-    const uint32_t* planes[K];
-#pragma unroll
-    for (int f = 0; f < K; ++f) planes[f] = bufs.p[q][T.src_buf][(T.lev_in + f) % K];
+    if (warp == LEVEL_WARPS) {
+        if (lane == 0)
+            level_producer<K, true>(bufs, q, jobs, njobs, ntiles, clouds, trec, incl, ctr, lsm, meta, full, empty, err);
+        return;
+    }
     const int wbase = warp * 32 * IPT;
-    uint32_t v[K][IPT];
-    uint32_t dig[IPT];
-    int32_t flo[IPT], fhi[IPT];  // final segment of each element
-#pragma unroll
-    for (int j = 0; j < IPT; ++j) {
-        const int o = wbase + j * 32 + lane;
-        dig[j] = INV;
-        flo[j] = 0;
-        fhi[j] = -1;
-#pragma unroll
-        for (int f = 0; f < K; ++f) v[f][j] = 0;
-        if (o < T.npos) {
-            const int32_t pos = pos0 + o;
-            // plane order rotated so that level lev_in + f reads v[f] (compile-time index)
-#pragma unroll
-            for (int f = 0; f < K; ++f) v[f][j] = planes[f][goff + pos];
-            int sj = -1;
-#pragma unroll
-            for (int x = 0; x < LEVEL_NSMAX; ++x)
-                if (x < ns && pos >= s_ti[1 + x] && pos <= s_ti[5 + x]) sj = x;
-            if (sj >= 0) {
-                uint32_t r[K];
-#pragma unroll
-                for (int f = 0; f < K; ++f) r[f] = v[f][j];
-                dig[j] = route<K, NBMAX>(r, F, sj, s_ti[1 + sj], s_ti[5 + sj], s_med, flo[j], fhi[j]);
-            }
+    for (int it = 0;; ++it) {
+        const int s = it % LEVEL_STAGES;
+        const bool ok = mbar_wait(&full[s], (uint32_t)(it / LEVEL_STAGES) & 1u);
+        if (consumer_or(!ok)) {
+            if (tid == 0) atomicOr(err, ERR_TIMEOUT);
+            break;
         }
-    }
-    // warp multisplit ranking on (segment, bucket): equal-digit lane masks
-    // from ballots over the digit bits (the invalid marker is NDMAX)
-    uint32_t rank[IPT];
+        const StageMeta M = meta[s];
+        if (M.t < 0) break;
+        const uint32_t* st = lsm + (size_t)s * SW;
+        const uint32_t* rec = st;
+        const int ns = (int)rec[0];
+        int32_t tlo[LEVEL_NSMAX], thi[LEVEL_NSMAX];
+        tile_bounds(rec, tlo, thi);
+        const int F = M.F;
+        const int NB = 1 << F;
+        const uint32_t marker = (uint32_t)(ns * NB);
+        const int nbits = 32 - __clz(marker);
+        uint32_t v[K][IPT];
+        uint32_t dig[IPT];
 #pragma unroll
-    for (int j = 0; j < IPT; ++j) {
-        const uint32_t d = dig[j] == INV ? (uint32_t)NDMAX : dig[j];
-        uint32_t peers = 0xffffffffu;
+        for (int j = 0; j < IPT; ++j) {
+            const int o = wbase + j * 32 + lane;
+            dig[j] = marker;
 #pragma unroll
-        for (int bit = 0; bit < DBITS; ++bit) {
-            const uint32_t bb = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
-            peers &= ((d >> bit) & 1u) ? bb : ~bb;
-        }
-        const int leader = __ffs(peers) - 1;
-        uint32_t old = 0;
-        if (lane == leader && d < (uint32_t)NDMAX) old = atomicAdd(&s_wc[warp][d], (uint32_t)__popc(peers));
-        old = __shfl_sync(0xffffffffu, old, leader);
-        rank[j] = old + __popc(peers & lanemask_lt());
-    }
-    __syncthreads();
-    // per digit: prefix over warps, and its base position: the final
-    // segment's start plus, for the first segment, the count of its elements
-    // in earlier tiles (scanned count pass)
-    const bool first_cont = ns > 0 && s_ti[1] < pos0;
-    for (int d = tid; d < LEVEL_NSMAX * NB; d += LEVEL_THREADS) {
-        uint32_t c = 0;
+            for (int f = 0; f < K; ++f) v[f][j] = 0;
+            if (o < M.npos) {
 #pragma unroll
-        for (int w = 0; w < LEVEL_WARPS; ++w) {
-            const uint32_t x = s_wc[w][d];
-            s_wc[w][d] = c;
-            c += x;
-        }
-        const int sj = d >> F;
-        const int b = d - (sj << F);
-        // start of bucket b below segment sj: walk the shape F levels
-        int32_t a = sj < ns ? s_ti[1 + sj] : 0, z = sj < ns ? s_ti[5 + sj] : -1;
-        for (int f = F - 1; f >= 0; --f) {
-            const int32_t mid = a + ((z - a) >> 1);
-            if ((b >> f) & 1) a = mid + 1; else z = mid - 1;
-        }
-        s_dbase[d] = a + ((sj == 0 && first_cont) ? (int32_t)incl[(int64_t)(t - 1) * NBMAX + b] : 0);
-    }
-    __syncthreads();
-    int32_t dest[IPT];
+                for (int f = 0; f < K; ++f) v[f][j] = st[TW + NBP + f * PST + M.shift + o];
+                const int sj = tile_slot(tlo, thi, ns, M.pos0 + o);
+                if (sj >= 0) {
+                    uint32_t r[K];
 #pragma unroll
-    for (int j = 0; j < IPT; ++j) {
-        dest[j] = -1;
-        if (dig[j] != INV) {
-            const uint32_t d = dig[j];
-            const int32_t dd = s_dbase[d] + (int32_t)(s_wc[warp][d] + rank[j]);
-            // the destination must lie in the element's final segment; any
-            // other value means inconsistent inputs and is never written
-            if (dd >= flo[j] && dd <= fhi[j]) {
-                dest[j] = dd;
-                if (T.write_med && dd == flo[j] + ((fhi[j] - flo[j]) >> 1)) {
-                    // the new median of level lev_out: its rank in super key
-                    // q and tuple (plane 0), and its segment index
-                    const int sj = (int)(d >> F);
-                    const int32_t si = (s_ti[9 + sj] << F) + (int32_t)(d - ((uint32_t)sj << F));
-                    const int64_t gsrc = goff + pos0 + wbase + j * 32 + lane;
-                    const uint32_t rq = bufs.p[q][T.src_buf][q][gsrc];
-                    const uint32_t r0 = bufs.p[q][T.src_buf][0][gsrc];
-                    medr[C.medr_off + ((int64_t)1 << T.lev_out) - 1 + si] = rq;
-                    if (r0 >= goff && r0 < goff + m)
-                        C.node[dd] = (int32_t)((int64_t)perm0[r0] - C.in_off);
-                    else
-                        atomicOr(err, ERR_INTERNAL);
+                    for (int f = 0; f < K; ++f) r[f] = v[f][j];
+                    const uint32_t d = route_rec<K>(r, F, sj, rec);
+                    if (d != INV) dig[j] = d;
                 }
-            } else {
-                atomicOr(err, ERR_INTERNAL);
             }
         }
-    }
-    // each run of equal digits goes to consecutive addresses: stores from
-    // registers, coalesced per run
+        // stable warp ranking: lanes with equal digits from ballots over the
+        // digit bits (nbits of them suffice for this tile)
+        uint32_t rank[IPT];
 #pragma unroll
-    for (int f = 0; f < K; ++f) {
-        uint32_t* dp = bufs.p[q][T.dst_buf][(T.lev_in + f) % K] + goff;
+        for (int j = 0; j < IPT; ++j) {
+            const uint32_t d = dig[j];
+            uint32_t peers = 0xffffffffu;
 #pragma unroll
-        for (int j = 0; j < IPT; ++j)
-            if (dest[j] >= 0) dp[dest[j]] = v[f][j];
+            for (int bit = 0; bit < DBITS; ++bit) {
+                if (bit < nbits) {
+                    const uint32_t bb = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
+                    peers &= ((d >> bit) & 1u) ? bb : ~bb;
+                }
+            }
+            const int leader = __ffs(peers) - 1;
+            uint32_t old = 0;
+            if (lane == leader && d < marker) old = atomicAdd(&s_wc[warp][d], (uint32_t)__popc(peers));
+            old = __shfl_sync(0xffffffffu, old, leader);
+            rank[j] = old + __popc(peers & lanemask_lt());
+        }
+        consumer_sync();
+        // per digit: prefix over warps; base, bounds and middle of its final
+        // segment; the first segment continues the scanned counts of earlier tiles
+        const bool first_cont = ns > 0 && tlo[0] < M.pos0;
+        for (int d = tid; d < ns * NB; d += LEVEL_THREADS) {
+            uint32_t c = 0;
+#pragma unroll
+            for (int w = 0; w < LEVEL_WARPS; ++w) {
+                const uint32_t x = s_wc[w][d];
+                s_wc[w][d] = c;
+                c += x;
+            }
+            const int sj = d >> F;
+            const int b = d - (sj << F);
+            int32_t a = (int32_t)rec[1 + sj], z = (int32_t)rec[5 + sj];
+            for (int f = F - 1; f >= 0; --f) {
+                const int32_t mid = a + ((z - a) >> 1);
+                if ((b >> f) & 1) a = mid + 1; else z = mid - 1;
+            }
+            s_dlo[d] = a;
+            s_dhi[d] = z;
+            s_dmid[d] = M.write_med ? a + ((z - a) >> 1) : -1;
+            s_dbase[d] = a + ((sj == 0 && first_cont && M.has_incl) ? (int32_t)st[TW + b] : 0);
+        }
+        if (tid < LEVEL_NSMAX) s_segidx[tid] = (int32_t)rec[9 + tid];
+        consumer_sync();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);  // this warp is done with the stage
+        const CloudDev& C = clouds[M.cloud];
+        int32_t dest[IPT];
+#pragma unroll
+        for (int j = 0; j < IPT; ++j) {
+            dest[j] = -1;
+            const uint32_t d = dig[j];
+            if (d < marker) {
+                const int32_t dd = s_dbase[d] + (int32_t)(s_wc[warp][d] + rank[j]);
+                // the destination must lie in the element's final segment; any
+                // other value means inconsistent inputs and is never written
+                if (dd >= s_dlo[d] && dd <= s_dhi[d]) {
+                    dest[j] = dd;
+                    if (dd == s_dmid[d]) {
+                        const int sj = (int)(d >> F);
+                        const int32_t si = (s_segidx[sj] << F) + (int32_t)(d - ((uint32_t)sj << F));
+                        const int fq = (q - M.lev_in % K + K) % K;
+                        const int f0 = (K - M.lev_in % K) % K;
+                        const uint32_t rq = plane_value<K, IPT>(v, j, fq);
+                        const uint32_t r0 = plane_value<K, IPT>(v, j, f0);
+                        const int64_t lev_out = M.lev_in + F;
+                        medr[C.medr_off + ((int64_t)1 << lev_out) - 1 + si] = rq;
+                        if (r0 >= M.goff && r0 < M.goff + M.m)
+                            C.node[dd] = (int32_t)((int64_t)perm0[r0] - C.in_off);
+                        else
+                            atomicOr(err, ERR_INTERNAL);
+                    }
+                } else {
+                    atomicOr(err, ERR_INTERNAL);
+                }
+            }
+        }
+        // each run of equal digits goes to consecutive addresses: stores from
+        // registers, coalesced per run
+#pragma unroll
+        for (int f = 0; f < K; ++f) {
+            uint32_t* dp = bufs.p[q][M.dst_buf][(M.lev_in + f) % K] + M.goff;
+#pragma unroll
+            for (int j = 0; j < IPT; ++j)
+                if (dest[j] >= 0) dp[dest[j]] = v[f][j];
+        }
+        // this warp's counters start the next tile at zero (only this warp
+        // reads its row after the digit loop above)
+        __syncwarp();
+        for (int d = lane; d < NDMAX; d += 32) s_wc[warp][d] = 0;
+        __syncwarp();
     }
 }
 
@@ -816,26 +1053,54 @@ __global__ void k_top_nodes(const CloudDev* __restrict__ clouds, const int64_t* 
 }
 
 // ------------------------------------------------------------ launchers
-int level_ipt(int k) { return 8; }
-int level_tile(int k) { return LEVEL_THREADS * level_ipt(k); }
-int level_status_stride(int k) { return 1 << (k - 1); }  // status rows (buckets) per tile
+int level_tile(int k) { return level_tile_of(k); }
+
+// Resident blocks per SM of the persistent level kernels ([0] count,
+// [1] move; by K) and the SM count, set by init_build_kernels.
+static int g_level_occ[2][MAXK + 1];
+static int g_num_sms = 0;
+
+// Status area of one level step (u32 words, every region 16-byte aligned):
+// counts [t][nbp], scanned counts [t][nbp], head flags [t], tile records
+// [t][trec_words], two tile counters.
+struct LevelStatus {
+    uint32_t *cnt, *incl, *head, *trec, *ctrs;
+};
+static LevelStatus level_status_layout(int k, int ntiles, uint32_t* status) {
+    const size_t t4 = ((size_t)ntiles + 3) & ~(size_t)3;
+    const size_t nbp = (size_t)level_nbp(k);
+    LevelStatus L;
+    L.cnt = status;
+    L.incl = L.cnt + t4 * nbp;
+    L.head = L.incl + t4 * nbp;
+    L.trec = L.head + t4;
+    L.ctrs = L.trec + t4 * (size_t)trec_words(k);
+    return L;
+}
+
+size_t level_status_words(int k, int ntiles) {
+    const size_t t4 = ((size_t)ntiles + 3) & ~(size_t)3;
+    return t4 * (2 * (size_t)level_nbp(k) + 1 + (size_t)trec_words(k)) + 4;
+}
 
 cudaError_t launch_level_pass(int k, const AllBufs& bufs, int q, const LevelJob* jobs, int njobs, int ntiles,
                               const CloudDev* clouds, uint32_t* medr, const uint32_t* perm0, uint32_t* status,
                               int* err, cudaStream_t s) {
     if (ntiles == 0) return cudaSuccess;
+    if (k < 2 || k > MAXK || g_num_sms == 0) return cudaErrorInvalidValue;
+    const LevelStatus L = level_status_layout(k, ntiles, status);
     const int nbmax = 1 << (k - 1);
-    uint32_t* cnt = status;                                  // [ntiles][nbmax]
-    uint32_t* incl = cnt + (size_t)ntiles * nbmax;           // [ntiles][nbmax]
-    uint32_t* head = incl + (size_t)ntiles * nbmax;          // [ntiles]
-    int32_t* tinfo = reinterpret_cast<int32_t*>(head + ntiles);  // [ntiles][TILEINFO]
-#define KD_LEVEL_CASE(KK)                                                                                    \
-    case KK:                                                                                               \
-        k_level_count<KK, 8><<<ntiles, LEVEL_THREADS, 0, s>>>(bufs, q, jobs, njobs, clouds, medr, cnt, head,   \
-                                                              tinfo, err);                                 \
-        k_level_scan<<<nbmax, 1024, 0, s>>>(ntiles, nbmax, cnt, head, incl);                                \
-        k_level_pass<KK, 8><<<ntiles, LEVEL_THREADS, 0, s>>>(bufs, q, jobs, njobs, clouds, medr, perm0, incl,  \
-                                                             tinfo, err);                                  \
+    const int gc = std::min(ntiles, g_num_sms * g_level_occ[0][k]);
+    const int gm = std::min(ntiles, g_num_sms * g_level_occ[1][k]);
+#define KD_LEVEL_CASE(KK)                                                                                      \
+    case KK:                                                                                                 \
+        k_level_tiles<KK><<<(ntiles + 7) / 8, 256, 0, s>>>(jobs, njobs, ntiles, clouds, medr, L.trec, L.ctrs,   \
+                                                           err);                                             \
+        k_level_count<KK><<<gc, LEVEL_BLOCK, level_smem_bytes<KK>(false), s>>>(                              \
+            bufs, q, jobs, njobs, ntiles, clouds, L.trec, L.cnt, L.head, L.ctrs, err);                       \
+        k_level_scan<<<nbmax, 1024, 0, s>>>(ntiles, level_nbp(KK), L.cnt, L.head, L.incl);                   \
+        k_level_pass<KK><<<gm, LEVEL_BLOCK, level_smem_bytes<KK>(true), s>>>(                                \
+            bufs, q, jobs, njobs, ntiles, clouds, medr, perm0, L.trec, L.incl, L.ctrs + 1, err);             \
         break;
     switch (k) {
         KD_LEVEL_CASE(2)
@@ -852,9 +1117,19 @@ cudaError_t launch_level_pass(int k, const AllBufs& bufs, int q, const LevelJob*
     return cudaGetLastError();
 }
 
-// status words one level step needs: counts, inclusive scan, head flags, tile segment lists
-size_t level_status_words(int k, int ntiles) {
-    return (size_t)ntiles * (2u << (k - 1)) + (size_t)ntiles + (size_t)ntiles * TILEINFO;
+template <int K>
+static cudaError_t init_level_kernels() {
+    const size_t sc = level_smem_bytes<K>(false), sm = level_smem_bytes<K>(true);
+    cudaError_t e = cudaFuncSetAttribute((const void*)k_level_count<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sc);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute((const void*)k_level_pass<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    int oc = 0, om = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oc, k_level_count<K>, LEVEL_BLOCK, sc);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&om, k_level_pass<K>, LEVEL_BLOCK, sm);
+    g_level_occ[0][K] = oc > 0 ? oc : 1;
+    g_level_occ[1][K] = om > 0 ? om : 1;
+    return e;
 }
 
 int finish_kmax(int smax) { return fin_kmax(smax); }
@@ -864,6 +1139,16 @@ size_t finish_smem(int k, int smax) {
 
 cudaError_t init_build_kernels() {
     cudaError_t e = cudaSuccess;
+    int dev = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = init_level_kernels<2>();
+    if (e == cudaSuccess) e = init_level_kernels<3>();
+    if (e == cudaSuccess) e = init_level_kernels<4>();
+    if (e == cudaSuccess) e = init_level_kernels<5>();
+    if (e == cudaSuccess) e = init_level_kernels<6>();
+    if (e == cudaSuccess) e = init_level_kernels<7>();
+    if (e == cudaSuccess) e = init_level_kernels<8>();
     auto set = [&](const void* f, size_t bytes) {
         if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     };

@@ -28,13 +28,10 @@ namespace kd {
 cudaError_t launch_transform(int dtype, const void* coords, int64_t n, int k, void* keys, int64_t stride,
                              const int64_t* cloud_start, int ncloud, uint32_t* cloud_plane, int cloud_digits,
                              uint32_t* hist, int* err, cudaStream_t s);
-int sort_tile(int key64);
 size_t sort_status_words(int64_t max_count);
-size_t sort_flag_words(int64_t max_count);
-cudaError_t launch_sort_pass(int key64, int mode, const int64_t* count_ptr, int64_t max_count,
-                             const void* key_src, const uint32_t* gidx, void* key_dst, const PayloadArgs& pay,
-                             const uint32_t* digit_base, int shift, uint32_t* status, uint32_t* tile_ctr, int* err,
-                             cudaStream_t s);
+cudaError_t launch_sort_pass(int key64, const int64_t* count_ptr, int64_t max_count, const void* key_src,
+                             void* key_dst, const PayloadArgs& pay, const uint32_t* digit_base, int shift,
+                             uint32_t* status, int* err, cudaStream_t s);
 cudaError_t launch_digit_bases(const uint32_t* hist, int nrows, uint32_t* bases, cudaStream_t s);
 cudaError_t launch_gather(int key64, const int64_t* count_ptr, int64_t max_count, const void* plane,
                           const uint32_t* ids, void* out, int* err, cudaStream_t s);
@@ -360,7 +357,7 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
         *out = H.release();
         return KD_OK;
     }
-    CKS(dev_alloc(ctx, &p, (size_t)N * 4));
+    CKS(dev_alloc(ctx, &p, (size_t)pad4(N) * 4 + 16));
     H->perm0 = (uint32_t*)p;
     const size_t rec_planes = k >= 2 ? (size_t)k * k : 0;
     if (rec_planes) {
@@ -407,9 +404,12 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
     int64_t *cstart = nullptr, *d_n = nullptr;
     int32_t* mcloud = nullptr;
     int* d_err = nullptr;
-    CKS(S.get(&keys, (size_t)k * N * w));
+    // every plane and sort buffer: stride padded to 16 bytes plus 16 bytes of
+    // slack, for the 16-byte-aligned bulk copies of the sort passes
+    const int64_t NS = pad4(N);
+    CKS(S.get(&keys, (size_t)k * NS * w + 16));
     if (count > 1) {
-        CKS(S.get(&cloud_plane, (size_t)N * 4));
+        CKS(S.get(&cloud_plane, (size_t)NS * 4 + 16));
         CKS(S.get(&cstart, (size_t)(count + 1) * 8));
     }
     CKS(S.get(&hist, (size_t)nrows * RADIX * 4));
@@ -429,7 +429,7 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
         CK(cudaMemcpyAsync(cstart, H->in_off.data(), (size_t)(count + 1) * 8, cudaMemcpyHostToDevice, s));
     {
         LaunchTimer lt(ctx, F_TRANSFORM, (double)N, nullptr, (double)k * (tsz + w) + (count > 1 ? 4 : 0));
-        CK(launch_transform(dtype, coords, N, k, keys, N, cstart, count, cloud_plane, cloud_digits, hist, d_err, s));
+        CK(launch_transform(dtype, coords, N, k, keys, NS, cstart, count, cloud_plane, cloud_digits, hist, d_err, s));
     }
     {
         LaunchTimer lt(ctx, F_OTHER, 0.0);
@@ -467,33 +467,25 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
     if (count > 1) plane_passes(cloud_sort, -1, cloud_digits, false);
 
     // buffers
-    size_t npasses = s0.size() + cloud_sort.size();
-    for (auto& v : chain) npasses += v.size();
-    const int nperm = k >= 2 ? k - 1 : 0;  // grouping passes of the rank-plane permutations
-    npasses += nperm;
-    uint32_t *status = nullptr, *ctrs = nullptr;
-    const size_t status_words_per = (sort_status_words(N) + 3) & ~(size_t)3;  // flags | records, per pass
+    // one status area serves every sort pass in turn (each pass clears what
+    // it needs), followed by the dedup scratch
+    uint32_t* status = nullptr;
+    const size_t status_words = sort_status_words(N);
     const size_t dedup_words = dedup_scratch_words(N);
-    CKS(S.get(&status, (npasses * status_words_per + dedup_words) * 4));
-    CKS(S.get(&ctrs, (npasses + 1) * 4));
-    // only the flag words need zeroing (records are written before their flags)
-    for (size_t pi = 0; pi < npasses; ++pi)
-        CK(cudaMemsetAsync(status + pi * status_words_per, 0, sort_flag_words(N) * 4, s));
-    CK(cudaMemsetAsync(ctrs, 0, (npasses + 1) * 4, s));
+    CKS(S.get(&status, (status_words + dedup_words) * 4));
     unsigned char* kbuf[2];
     uint32_t* ibuf[2];
     const int maxpay = k + 1;
     uint32_t* pbuf[2][MAXPAY];
-    CKS(S.get(&kbuf[0], (size_t)N * w));
-    CKS(S.get(&kbuf[1], (size_t)N * w));
-    CKS(S.get(&ibuf[0], (size_t)N * 4));
-    CKS(S.get(&ibuf[1], (size_t)N * 4));
+    CKS(S.get(&kbuf[0], (size_t)NS * w + 16));
+    CKS(S.get(&kbuf[1], (size_t)NS * w + 16));
+    CKS(S.get(&ibuf[0], (size_t)NS * 4 + 16));
+    CKS(S.get(&ibuf[1], (size_t)NS * 4 + 16));
     if (k >= 2)
         for (int b = 0; b < 2; ++b)
-            for (int j = 0; j < maxpay; ++j) CKS(S.get(&pbuf[b][j], (size_t)N * 4));
-    size_t pass_no = 0;
+            for (int j = 0; j < maxpay; ++j) CKS(S.get(&pbuf[b][j], (size_t)NS * 4 + 16));
     auto plane_ptr = [&](int plane) -> const void* {
-        return plane >= 0 ? (const void*)(keys + (size_t)plane * N * w) : (const void*)cloud_plane;
+        return plane >= 0 ? (const void*)(keys + (size_t)plane * NS * w) : (const void*)cloud_plane;
     };
     auto plane64 = [&](int plane) { return plane >= 0 ? key64 : 0; };
 
@@ -509,18 +501,15 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
         pay.dst[0] = ibuf[ic ^ 1];
         const void* ksrc = P.mode == KEY_BUF ? (const void*)kbuf[kc] : plane_ptr(P.plane);
         void* kdst = next_gathers ? nullptr : (void*)kbuf[kc ^ 1];
-        int mode = P.mode;
-        if (mode == KEY_GATHER) {  // gather the new plane's keys into order first
+        if (P.mode == KEY_GATHER) {  // gather the new plane's keys into order first
             LaunchTimer lg(ctx, F_SORT, (double)N, nullptr, 4.0 + 2.0 * P.w);
             CK(launch_gather(plane64(P.plane), d_n, N, plane_ptr(P.plane), ibuf[ic], kbuf[kc], d_err, s));
             ksrc = kbuf[kc];
-            mode = KEY_BUF;
         }
         LaunchTimer lt(ctx, F_SORT, (double)N, nullptr, pass_bytes(P, kdst != nullptr, pay.n));
-        CK(launch_sort_pass(plane64(P.plane), mode, d_n, N, ksrc, ibuf[ic], kdst, pay,
-                            bases_all + (size_t)row_of(P.plane, P.digit) * RADIX, 8 * P.digit,
-                            status + pass_no * status_words_per, ctrs + pass_no, d_err, s));
-        ++pass_no;
+        ctx->launches += 2;  // count and scan kernels of the pass
+        CK(launch_sort_pass(plane64(P.plane), d_n, N, ksrc, kdst, pay,
+                            bases_all + (size_t)row_of(P.plane, P.digit) * RADIX, 8 * P.digit, status, d_err, s));
         kc ^= 1;
         ic ^= 1;
     }
@@ -529,8 +518,8 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
     {
         LaunchTimer lt(ctx, F_DEDUP, (double)N, nullptr, 2.0 * w + 8);
         ctx->launches += 2;  // flags, tile scan, compaction
-        CK(launch_dedup(key64, N, kbuf[kc], ibuf[ic], keys, N, k, cloud_plane, cloud_digits, dedup_out,
-                        status + npasses * status_words_per, H->d_m, hist, mcloud, d_err, s));
+        CK(launch_dedup(key64, N, kbuf[kc], ibuf[ic], keys, NS, k, cloud_plane, cloud_digits, dedup_out,
+                        status + status_words, H->d_m, hist, mcloud, d_err, s));
     }
     ic ^= 1;
     {
@@ -546,18 +535,15 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
         pay.src[0] = ibuf[ic];
         pay.dst[0] = last ? H->perm0 : ibuf[ic ^ 1];
         const void* ksrc = P.mode == KEY_BUF ? (const void*)kbuf[kc] : plane_ptr(-1);
-        int mode = P.mode;
-        if (mode == KEY_GATHER) {
+        if (P.mode == KEY_GATHER) {
             LaunchTimer lg(ctx, F_SORT, 0.0, H->d_m, 12.0);
             CK(launch_gather(0, H->d_m, N, plane_ptr(-1), ibuf[ic], kbuf[kc], d_err, s));
             ksrc = kbuf[kc];
-            mode = KEY_BUF;
         }
         LaunchTimer lt(ctx, F_SORT, 0.0, H->d_m, pass_bytes(P, !last, 1));
-        CK(launch_sort_pass(0, mode, H->d_m, N, ksrc, ibuf[ic], last ? nullptr : (void*)kbuf[kc ^ 1], pay,
-                            bases_kept + (size_t)row_of(-1, P.digit) * RADIX, 8 * P.digit,
-                            status + pass_no * status_words_per, ctrs + pass_no, d_err, s));
-        ++pass_no;
+        ctx->launches += 2;  // count and scan kernels of the pass
+        CK(launch_sort_pass(0, H->d_m, N, ksrc, last ? nullptr : (void*)kbuf[kc ^ 1], pay,
+                            bases_kept + (size_t)row_of(-1, P.digit) * RADIX, 8 * P.digit, status, d_err, s));
         kc ^= 1;
         ic ^= 1;
     }
@@ -604,18 +590,16 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
                 pay.n = np;
                 const void* ksrc = P.mode == KEY_BUF ? (const void*)kbuf[kc] : plane_ptr(P.plane);
                 void* kdst = (last || next_gathers) ? nullptr : (void*)kbuf[kc ^ 1];
-                int mode = P.mode;
-                if (mode == KEY_GATHER) {
+                if (P.mode == KEY_GATHER) {
                     LaunchTimer lg(ctx, F_SORT, 0.0, H->d_m, 4.0 + 2.0 * P.w);
                     CK(launch_gather(plane64(P.plane), H->d_m, N, plane_ptr(P.plane), cur_id, kbuf[kc], d_err, s));
                     ksrc = kbuf[kc];
-                    mode = KEY_BUF;
                 }
                 LaunchTimer lt(ctx, F_SORT, 0.0, H->d_m, pass_bytes(P, kdst != nullptr, pay.n));
-                CK(launch_sort_pass(plane64(P.plane), mode, H->d_m, N, ksrc, cur_id, kdst, pay,
-                                    bases_kept + (size_t)row_of(P.plane, P.digit) * RADIX, 8 * P.digit,
-                                    status + pass_no * status_words_per, ctrs + pass_no, d_err, s));
-                ++pass_no;
+                ctx->launches += 2;  // count and scan kernels of the pass
+                CK(launch_sort_pass(plane64(P.plane), H->d_m, N, ksrc, kdst, pay,
+                                    bases_kept + (size_t)row_of(P.plane, P.digit) * RADIX, 8 * P.digit, status,
+                                    d_err, s));
                 kc ^= 1;
                 if (carry_id) cur_id = new_id;
                 for (size_t j = 0; j < ranks.size(); ++j) rsrc[j] = last ? H->rec.p[d][ranks[j]] : pbuf[pb][j];
@@ -662,10 +646,9 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
                 uint32_t* gdest = ibuf[0];
                 {
                     LaunchTimer lt(ctx, F_RECORDS, 0.0, H->d_m, 4.0 + 8.0 * nv + 4.0);
-                    CK(launch_sort_pass(0, KEY_DIRECT, H->d_m, N, H->rec.p[1][d], nullptr, gdest, pay, pbases, shift,
-                                        status + pass_no * status_words_per, ctrs + pass_no, d_err, s));
+                    ctx->launches += 2;  // count and scan kernels of the pass
+                    CK(launch_sort_pass(0, H->d_m, N, H->rec.p[1][d], gdest, pay, pbases, shift, status, d_err, s));
                 }
-                ++pass_no;
                 PayloadArgs sc{};
                 sc.n = nv;
                 for (int j = 0; j < nv; ++j) {

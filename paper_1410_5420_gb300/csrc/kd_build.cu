@@ -97,21 +97,6 @@ struct StageMeta {
     int64_t goff;
 };
 
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-// Barrier 1 over the consumer warps only (the producer warp never joins).
-__device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(LEVEL_THREADS) : "memory"); }
-__device__ __forceinline__ bool consumer_or(bool v) {
-    uint32_t r;
-    asm volatile(
-        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n barrier.cta.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}"
-        : "=r"(r)
-        : "r"((uint32_t)v), "n"(LEVEL_THREADS)
-        : "memory");
-    return r != 0;
-}
-
 template <int K>
 __global__ void __launch_bounds__(256) k_level_tiles(const LevelJob* __restrict__ jobs, int njobs, int ntiles,
                                                      const CloudDev* __restrict__ clouds,
@@ -324,7 +309,7 @@ __global__ void __launch_bounds__(LEVEL_BLOCK)
     for (int it = 0;; ++it) {
         const int s = it % LEVEL_STAGES;
         const bool ok = mbar_wait(&full[s], (uint32_t)(it / LEVEL_STAGES) & 1u);
-        if (consumer_or(!ok)) {
+        if (consumer_or<LEVEL_THREADS>(!ok)) {
             if (tid == 0) atomicOr(err, ERR_TIMEOUT);
             break;
         }
@@ -354,7 +339,7 @@ __global__ void __launch_bounds__(LEVEL_BLOCK)
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
-        consumer_sync();
+        consumer_sync<LEVEL_THREADS>();
         const int NB = 1 << F;
         if (tid < NBP) cnt[(int64_t)M.t * NBP + tid] = (ns > 0 && tid < NB) ? s_cnt[s][(ns - 1) * NB + tid] : 0u;
         if (tid == 0) head[M.t] = (ns == 1 && lo0 < M.pos0) ? 0u : 1u;
@@ -475,7 +460,7 @@ __global__ void __launch_bounds__(LEVEL_BLOCK, K <= 3 ? 3 : 2)
     for (int it = 0;; ++it) {
         const int s = it % LEVEL_STAGES;
         const bool ok = mbar_wait(&full[s], (uint32_t)(it / LEVEL_STAGES) & 1u);
-        if (consumer_or(!ok)) {
+        if (consumer_or<LEVEL_THREADS>(!ok)) {
             if (tid == 0) atomicOr(err, ERR_TIMEOUT);
             break;
         }
@@ -531,7 +516,7 @@ __global__ void __launch_bounds__(LEVEL_BLOCK, K <= 3 ? 3 : 2)
             old = __shfl_sync(0xffffffffu, old, leader);
             rank[j] = old + __popc(peers & lanemask_lt());
         }
-        consumer_sync();
+        consumer_sync<LEVEL_THREADS>();
         // per digit: prefix over warps; base, bounds and middle of its final
         // segment; the first segment continues the scanned counts of earlier tiles
         const bool first_cont = ns > 0 && tlo[0] < M.pos0;
@@ -556,7 +541,7 @@ __global__ void __launch_bounds__(LEVEL_BLOCK, K <= 3 ? 3 : 2)
             s_dbase[d] = a + ((sj == 0 && first_cont && M.has_incl) ? (int32_t)st[TW + b] : 0);
         }
         if (tid < LEVEL_NSMAX) s_segidx[tid] = (int32_t)rec[9 + tid];
-        consumer_sync();
+        consumer_sync<LEVEL_THREADS>();
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);  // this warp is done with the stage
         const CloudDev& C = clouds[M.cloud];

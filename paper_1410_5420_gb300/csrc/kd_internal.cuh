@@ -10,10 +10,6 @@ namespace kd {
 // ------------------------------------------------------------------ limits
 constexpr int MAXK = 8;
 constexpr int RADIX = 256;
-constexpr int SORT_THREADS = 512;
-constexpr int SORT_WARPS = SORT_THREADS / 32;
-constexpr int SORT_IPT = 16;
-constexpr int SORT_TILE = SORT_THREADS * SORT_IPT;
 constexpr int MAXPAY = 10;          // payload planes carried by one sort pass
 constexpr int LEVEL_THREADS = 256;
 constexpr int LEVEL_WARPS = LEVEL_THREADS / 32;
@@ -86,6 +82,25 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
         : "r"(smem_u32(bar)), "r"(parity)
         : "memory");
     return ok != 0;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// Named barrier 1 over the first NT threads of the block (the consumer
+// warps of a kernel whose last warp is a producer that never joins it).
+template <int NT>
+__device__ __forceinline__ void consumer_sync() {
+    asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+}
+template <int NT>
+__device__ __forceinline__ bool consumer_or(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n barrier.cta.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(NT)
+        : "memory");
+    return r != 0;
 }
 // Wait for phase `parity` of an mbarrier to complete; false after
 // SPIN_LIMIT polls (each poll may itself block for a bounded time).

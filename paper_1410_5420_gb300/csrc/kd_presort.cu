@@ -5,19 +5,25 @@
 // computed here as:
 //   k_transform   coordinates -> order-preserving unsigned key planes (SoA)
 //                 plus 256-bin histograms of every key byte;
-//   k_sort_pass   one stable 8-bit LSD pass (onesweep: warp match/popc
-//                 ranking, decoupled look-back over tiles, smem-staged
-//                 coalesced scatter).  Sorting least-significant part first
-//                 over x_{k-1}, ..., x_0 leaves the index array in x:y:...
-//                 order; each further array d is a stable sort of array d+1
-//                 by x_d alone (ties keep the order of super key d+1, which
-//                 equals super key d's order on them);
+//   k_rs_count / k_rs_scan / k_rs_move
+//                 one stable 8-bit LSD pass as reduce (per-tile digit
+//                 histograms), scan (per-digit tile offsets) and a persistent
+//                 move kernel fed by bulk async copies (stable warp ranking,
+//                 tile ordered by digit in shared memory, coalesced runs).
+//                 Sorting least-significant part first over x_{k-1}, ...,
+//                 x_0 leaves the index array in x:y:... order; each further
+//                 array d is a stable sort of array d+1 by x_d alone (ties
+//                 keep the order of super key d+1, which equals super key
+//                 d's order on them);
+//   k_gather      the keys of the next coordinate in the current order;
 //   k_dedup       adjacent-compare of the sorted array 0 and stream
 //                 compaction (Section 2.1, duplicates paragraph);
 //   k_records     rank vectors: rec[d][p][i] = position, in super-key-p
 //                 order, of the tuple at position i of array d.  After
 //                 deduplication super keys are unique, so comparing super
 //                 keys equals comparing these ranks.
+#include <algorithm>
+
 #include "kd_internal.cuh"
 
 namespace kd {
@@ -74,168 +80,296 @@ __global__ void __launch_bounds__(256) k_transform(const T* __restrict__ coords,
     if (nan) atomicOr(err, ERR_NAN);
 }
 
-// ------------------------------------------------------------ sort pass
-// One stable LSD pass over `*count_ptr` elements on digit (key >> shift) & 255.
-//   MODE KEY_BUF:    key = key_src[pos]           (keys of the previous pass)
-//   MODE KEY_DIRECT: key = key_src[pos]           (a key plane, identity order)
-//   MODE KEY_GATHER: key = key_src[gidx[pos]]     (a key plane, by tuple id)
-// Payload planes move with the key; a null source emits the source position.
-// digit_base holds, per digit, the number of elements of this sort with a
-// smaller digit (exclusive prefix of the digit histogram).
-// Tile pipeline (8192 keys, 512 threads): load; warp multisplit ranking
-// (equal-digit lane masks from 9 ballots, per-warp digit counters advanced
-// by one shared-memory atomic per group); publish the tile's digit counts;
-// tile-local prefix and staging of keys in digit order; look-back over
-// tile-major count records; then every digit's run is written with
-// consecutive addresses, keys first, then each payload plane.
-struct SortStatus {
-    uint32_t* flags;     // [tiles]
-    uint16_t* aggrec;    // [tiles][256]
-    uint32_t* increc;    // [tiles][256]
+// ---------------------------------------------------------- sort passes
+// One stable LSD digit pass is three launches (reduce, scan, move):
+//   k_rs_count  per tile, the 256-bin histogram of the pass digit;
+//   k_rs_scan   per digit, the exclusive prefix over tiles plus the digit's
+//               global base: chunks of RS_CHUNK tiles, chained by a
+//               decoupled look-back over chunk totals;
+//   k_rs_move   persistent: a producer warp streams each tile's offsets row,
+//               keys and up to SP payload planes into a shared-memory stage
+//               with bulk async copies (full/empty mbarriers); eight consumer
+//               warps rank the keys stably (ballots over the digit bits, per-
+//               warp counters), order the tile by digit in shared memory and
+//               write every plane with runs of equal digits to consecutive
+//               addresses.
+// Stability: within a tile, elements are ranked in position order (warp by
+// warp, lane by lane); across tiles, the scan orders tiles by index.
+constexpr int RS_THREADS = 256;
+constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RS_BLOCK = RS_THREADS + 32;  // + producer warp
+constexpr int RS_CHUNK = 64;               // tiles per scan chunk
+constexpr int RS_TILE_MIN = 1024;          // smallest tile of any variant (sizes the status area)
+
+struct SortMeta {
+    int32_t t;  // tile, or -1: no more tiles
+    int32_t n;  // elements in the tile
+    int64_t base;
 };
 
-template <typename KW, int MODE>
-__global__ void __launch_bounds__(SORT_THREADS, 2)
-    k_sort_pass(const int64_t* __restrict__ count_ptr, const KW* __restrict__ key_src,
-                const uint32_t* __restrict__ gidx, KW* __restrict__ key_dst, const __grid_constant__ PayloadArgs pay,
-                const uint32_t* __restrict__ digit_base, int shift, SortStatus st,
-                uint32_t* __restrict__ tile_ctr, int* __restrict__ err, int64_t gather_limit) {
-    constexpr int IPT = sizeof(KW) == 8 ? SORT_IPT / 2 : SORT_IPT;  // 64-bit keys: half tiles
-    constexpr int TILE = SORT_THREADS * IPT;
-    __shared__ uint32_t s_wc[SORT_WARPS][RADIX];
-    __shared__ uint32_t s_goff[RADIX];
-    __shared__ uint32_t s_tstart[RADIX];
-    __shared__ uint32_t s_warp[SORT_WARPS];
-    __shared__ uint32_t s_tile, s_ctl;
-    // s_dyn: [TILE * 8 bytes] keys, later dest | values;  then s_slot [TILE] u16
-    extern __shared__ __align__(16) unsigned char s_dyn[];
-    uint16_t* s_slot = reinterpret_cast<uint16_t*>(s_dyn + (size_t)TILE * 8);
+template <typename KW>
+__device__ __forceinline__ uint32_t digit_of(KW key, int shift) {
+    return (uint32_t)(key >> shift) & 255u;
+}
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
-    for (int i = tid; i < SORT_WARPS * RADIX; i += SORT_THREADS) (&s_wc[0][0])[i] = 0;
+template <typename KW, int TILE>
+__global__ void __launch_bounds__(256) k_rs_count(const int64_t* __restrict__ count_ptr, const KW* __restrict__ key_src,
+                                                  int shift, uint32_t* __restrict__ cnt,
+                                                  uint32_t* __restrict__ scan_flags, int nflags,
+                                                  uint32_t* __restrict__ scan_ctr) {
+    constexpr int V = 16 / sizeof(KW);            // keys per 16-byte load
+    constexpr int NV = TILE / V / 256;            // loads per thread
+    __shared__ uint32_t s_h[8][RADIX];
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (blockIdx.x == 0) {  // the scan of this pass starts from cleared flags
+        for (int i = tid; i < nflags; i += 256) scan_flags[i] = 0;
+        if (tid == 0) *scan_ctr = 0;
+    }
+    for (int i = tid; i < 8 * RADIX; i += 256) (&s_h[0][0])[i] = 0;
     __syncthreads();
     const int64_t count = *count_ptr;
-    const int64_t tile = s_tile;
-    const int64_t base = tile * TILE;
+    const int64_t base = (int64_t)blockIdx.x * TILE;
     if (base >= count) return;
-    const int tile_n = (int)(count - base < TILE ? count - base : (int64_t)TILE);
-    const int wbase = warp * 32 * IPT;
+    const int n = (int)(count - base < TILE ? count - base : (int64_t)TILE);
+    const KW* src = key_src + base;
+    uint4 x[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const int o = (v * 256 + tid) * V;
+        x[v] = o + V <= n ? *reinterpret_cast<const uint4*>(src + o) : make_uint4(0, 0, 0, 0);
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const int o = (v * 256 + tid) * V;
+        if (o + V <= n) {
+            const KW* kv = reinterpret_cast<const KW*>(&x[v]);
+#pragma unroll
+            for (int e = 0; e < V; ++e) atomicAdd(&s_h[warp][digit_of(kv[e], shift)], 1u);
+        } else {
+            for (int e = 0; e < V; ++e)
+                if (o + e < n) atomicAdd(&s_h[warp][digit_of(src[o + e], shift)], 1u);
+        }
+    }
+    __syncthreads();
+    uint32_t c = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) c += s_h[w][tid];
+    cnt[(int64_t)blockIdx.x * RADIX + tid] = c;
+}
 
-    KW key[IPT];
-    uint32_t rank[IPT];
-#pragma unroll
-    for (int j = 0; j < IPT; ++j) {
-        const int o = wbase + j * 32 + lane;
-        key[j] = 0;
-        if (o < tile_n) {
-            const int64_t pos = base + o;
-            if (MODE == KEY_GATHER) {
-                const uint32_t id = gidx[pos];
-                if ((int64_t)id < gather_limit) key[j] = key_src[id]; else atomicOr(err, ERR_INTERNAL);
-            } else {
-                key[j] = key_src[pos];
-            }
-        }
-    }
-    // warp multisplit: lanes with equal digits (9 bits: 8 digit bits and the
-    // out-of-range marker) found by ballots; ranks follow item order
-#pragma unroll
-    for (int j = 0; j < IPT; ++j) {
-        const int o = wbase + j * 32 + lane;
-        const uint32_t d = (o < tile_n) ? (uint32_t)((key[j] >> shift) & 255u) : (uint32_t)RADIX;
-        uint32_t peers = 0xffffffffu;
-#pragma unroll
-        for (int bit = 0; bit < 9; ++bit) {
-            const uint32_t bb = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
-            peers &= ((d >> bit) & 1u) ? bb : ~bb;
-        }
-        const int leader = __ffs(peers) - 1;
-        uint32_t old = 0;
-        if (lane == leader && d < RADIX) old = atomicAdd(&s_wc[warp][d], (uint32_t)__popc(peers));
-        old = __shfl_sync(0xffffffffu, old, leader);
-        rank[j] = old + __popc(peers & lanemask_lt());
-    }
+// offs[t][d] = digit_base[d] + (elements of digit d in tiles before t).
+__global__ void __launch_bounds__(256) k_rs_scan(const int64_t* __restrict__ count_ptr, int tile,
+                                                 const uint32_t* __restrict__ cnt,
+                                                 const uint32_t* __restrict__ digit_base, uint32_t* __restrict__ offs,
+                                                 uint32_t* __restrict__ flags, uint32_t* __restrict__ agg,
+                                                 uint32_t* __restrict__ inc, uint32_t* __restrict__ scan_ctr,
+                                                 uint32_t* __restrict__ move_ctr, int* __restrict__ err) {
+    __shared__ uint32_t s_chunk, s_ctl;
+    const int tid = threadIdx.x;
+    if (tid == 0) s_chunk = atomicAdd(scan_ctr, 1u);
+    if (blockIdx.x == 0 && tid == 0) *move_ctr = 0;  // the move pass starts after this kernel
     __syncthreads();
-    // threads < 256 own digit tid: tile count, published at once
-    uint32_t cnt = 0;
-    if (tid < RADIX) {
-#pragma unroll
-        for (int w = 0; w < SORT_WARPS; ++w) {
-            const uint32_t c = s_wc[w][tid];
-            s_wc[w][tid] = cnt;
-            cnt += c;
-        }
-        if (tile == 0) st.increc[tid] = cnt;
-        else st.aggrec[tile * RADIX + tid] = (uint16_t)cnt;
-    }
+    const int64_t count = *count_ptr;
+    const int64_t ntiles = (count + tile - 1) / tile;
+    const int64_t nchunks = (ntiles + RS_CHUNK - 1) / RS_CHUNK;
+    const int64_t c = s_chunk;
+    if (c >= nchunks) return;
+    const int64_t t0 = c * RS_CHUNK;
+    const int64_t t1 = t0 + RS_CHUNK < ntiles ? t0 + RS_CHUNK : ntiles;
+    uint32_t sum = 0;
+#pragma unroll 8
+    for (int64_t t = t0; t < t1; ++t) sum += cnt[t * RADIX + tid];
+    if (c == 0) inc[tid] = sum;
+    else agg[c * RADIX + tid] = sum;
     __syncthreads();
-    if (tid == 0) publish_flag(st.flags, tile, tile == 0 ? FLAG_INC : FLAG_AGG);
-    const uint32_t tstart = block_excl_scan<SORT_THREADS>(cnt, s_warp, nullptr);
-    if (tid < RADIX) s_tstart[tid] = tstart;
-    __syncthreads();
-    // stage keys in tile order (sorted by digit); remember each item's slot
-    KW* s_key = reinterpret_cast<KW*>(s_dyn);
-#pragma unroll
-    for (int j = 0; j < IPT; ++j) {
-        const int o = wbase + j * 32 + lane;
-        if (o < tile_n) {
-            const uint32_t d = (uint32_t)((key[j] >> shift) & 255u);
-            const uint32_t slot = s_tstart[d] + s_wc[warp][d] + rank[j];
-            s_key[slot] = key[j];
-            s_slot[o] = (uint16_t)slot;
-        }
-    }
+    if (tid == 0) publish_flag(flags, c, c == 0 ? FLAG_INC : FLAG_AGG);
     uint32_t excl = 0;
-    if (tile > 0) {
-        excl = block_lookback<uint16_t>(st.flags, st.aggrec, st.increc, RADIX, tile, &s_ctl, err);
-        if (tid < RADIX) st.increc[tile * RADIX + tid] = excl + cnt;
+    if (c > 0) {
+        excl = block_lookback<uint32_t>(flags, agg, inc, RADIX, c, &s_ctl, err);
+        inc[c * RADIX + tid] = excl + sum;
         __syncthreads();
-        if (tid == 0) publish_flag(st.flags, tile, FLAG_INC);
+        if (tid == 0) publish_flag(flags, c, FLAG_INC);
     }
-    if (tid < RADIX) s_goff[tid] = digit_base[tid] + excl - tstart;  // dest = s_goff[digit] + slot (mod 2^32)
+    uint32_t run = digit_base[tid] + excl;
+    for (int64_t t = t0; t < t1; ++t) {
+        const uint32_t v = cnt[t * RADIX + tid];
+        offs[t * RADIX + tid] = run;
+        run += v;
+    }
+}
+
+template <typename KW, int TILE, int SP>
+constexpr size_t rs_move_smem() {
+    return ((size_t)2 * (RADIX + TILE * (sizeof(KW) / 4) + SP * TILE) + (size_t)TILE * (sizeof(KW) / 4)) * 4;
+}
+
+template <typename KW, int TILE, int SP>
+__global__ void __launch_bounds__(RS_BLOCK, 2)
+    k_rs_move(const int64_t* __restrict__ count_ptr, const KW* __restrict__ key_src, KW* __restrict__ key_dst,
+              const __grid_constant__ PayloadArgs pay, const uint32_t* __restrict__ offs, int shift,
+              uint32_t* __restrict__ ctr, int* __restrict__ err) {
+    constexpr int IPT = TILE / RS_THREADS;
+    constexpr int KWW = sizeof(KW) / 4;
+    constexpr int SW = RADIX + TILE * KWW + SP * TILE;  // stage words: offsets row | keys | payloads
+    extern __shared__ __align__(128) uint32_t rsm[];     // [2][SW] stages, then the sorted tile [TILE] keys
+    __shared__ __align__(8) uint64_t full[2], empty[2];
+    __shared__ SortMeta meta[2];
+    __shared__ uint32_t s_wc[RS_WARPS][RADIX];
+    __shared__ uint32_t s_goff[RADIX], s_tstart[RADIX];
+    __shared__ uint32_t s_wsum[RS_WARPS];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], RS_WARPS);
+        }
+        fence_mbar_init();
+    }
+    for (int i = tid; i < RS_WARPS * RADIX; i += RS_BLOCK) (&s_wc[0][0])[i] = 0;
     __syncthreads();
-    // A destination outside [0, count) can only come from an inconsistent
-    // histogram; it is reported and never written.
-    uint32_t dest[IPT];
-#pragma unroll
-    for (int i = 0; i < IPT; ++i) {
-        const int s = i * SORT_THREADS + tid;
-        dest[i] = 0xffffffffu;
-        if (s < tile_n) {
-            const KW kk = s_key[s];
-            const uint32_t dd = s_goff[(uint32_t)((kk >> shift) & 255u)] + (uint32_t)s;
-            if ((int64_t)dd < count) {
-                dest[i] = dd;
-                if (key_dst) key_dst[dd] = kk;
-            } else {
-                atomicOr(err, ERR_INTERNAL);
+    const int64_t count = *count_ptr;
+    const int64_t ntiles = (count + TILE - 1) / TILE;
+    if (warp == RS_WARPS) {  // producer
+        if (lane != 0) return;
+        for (int it = 0;; ++it) {
+            const int s = it & 1;
+            const uint32_t ph = (uint32_t)(it >> 1) & 1u;
+            if (it >= 2 && !mbar_wait(&empty[s], ph ^ 1u)) {
+                atomicOr(err, ERR_TIMEOUT);
+                meta[s].t = -1;
+                mbar_arrive(&full[s]);
+                return;
             }
+            const int64_t t = atomicAdd(ctr, 1u);
+            SortMeta M;
+            M.t = t < ntiles ? (int32_t)t : -1;
+            if (M.t < 0) {
+                meta[s] = M;
+                mbar_arrive(&full[s]);
+                return;
+            }
+            M.base = t * TILE;
+            M.n = (int32_t)(count - M.base < TILE ? count - M.base : (int64_t)TILE);
+            const uint32_t kb = ((uint32_t)M.n * sizeof(KW) + 15u) & ~15u;
+            const uint32_t pb = ((uint32_t)M.n * 4u + 15u) & ~15u;
+            int nst = 0;
+            for (int p = 0; p < pay.n && p < SP; ++p) nst += pay.src[p] != nullptr;
+            meta[s] = M;
+            uint32_t* st = rsm + (size_t)s * SW;
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&full[s], RADIX * 4 + kb + (uint32_t)nst * pb);
+            bulk_g2s(st, offs + t * RADIX, RADIX * 4, &full[s]);
+            bulk_g2s(st + RADIX, key_src + M.base, kb, &full[s]);
+            for (int p = 0; p < pay.n && p < SP; ++p)
+                if (pay.src[p]) bulk_g2s(st + RADIX + TILE * KWW + p * TILE, pay.src[p] + M.base, pb, &full[s]);
         }
     }
-    if (pay.n == 0) return;
-    __syncthreads();
-    uint32_t* s_dest = reinterpret_cast<uint32_t*>(s_dyn);
-    uint32_t* s_val = reinterpret_cast<uint32_t*>(s_dyn + (size_t)TILE * 4);
-#pragma unroll
-    for (int i = 0; i < IPT; ++i) s_dest[i * SORT_THREADS + tid] = dest[i];
-    for (int p = 0; p < pay.n; ++p) {
-        const uint32_t* src = pay.src[p];
+    KW* sbuf = reinterpret_cast<KW*>(rsm + (size_t)2 * SW);
+    uint32_t* sb32 = rsm + (size_t)2 * SW;
+    const int wbase = warp * 32 * IPT;
+    for (int it = 0;; ++it) {
+        const int s = it & 1;
+        const bool ok = mbar_wait(&full[s], (uint32_t)(it >> 1) & 1u);
+        if (consumer_or<RS_THREADS>(!ok)) {
+            if (tid == 0) atomicOr(err, ERR_TIMEOUT);
+            break;
+        }
+        const SortMeta M = meta[s];
+        if (M.t < 0) break;
+        const uint32_t* st = rsm + (size_t)s * SW;
+        const KW* skeys = reinterpret_cast<const KW*>(st + RADIX);
+        const int nbits = M.n == TILE ? 8 : 9;  // digit 256 marks a slot past the tile's end
+        uint32_t dig[IPT], slot[IPT];
 #pragma unroll
         for (int j = 0; j < IPT; ++j) {
             const int o = wbase + j * 32 + lane;
-            if (o < tile_n) {
-                const int64_t pos = base + o;
-                s_val[s_slot[o]] = src ? src[pos] : (uint32_t)pos;
+            const uint32_t d = o < M.n ? digit_of(skeys[o], shift) : (uint32_t)RADIX;
+            uint32_t peers = 0xffffffffu;
+#pragma unroll
+            for (int bit = 0; bit < 9; ++bit) {
+                if (bit < nbits) {
+                    const uint32_t bb = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
+                    peers &= ((d >> bit) & 1u) ? bb : ~bb;
+                }
+            }
+            const int leader = __ffs(peers) - 1;
+            uint32_t old = 0;
+            if (lane == leader && d < RADIX) old = atomicAdd(&s_wc[warp][d], (uint32_t)__popc(peers));
+            old = __shfl_sync(0xffffffffu, old, leader);
+            slot[j] = old + __popc(peers & lanemask_lt());
+            dig[j] = d;
+        }
+        consumer_sync<RS_THREADS>();
+        // digit tid: prefix over warps in place, tile count, tile start
+        uint32_t c = 0;
+#pragma unroll
+        for (int w = 0; w < RS_WARPS; ++w) {
+            const uint32_t x = s_wc[w][tid];
+            s_wc[w][tid] = c;
+            c += x;
+        }
+        uint32_t x = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_wsum[warp] = x;
+        consumer_sync<RS_THREADS>();
+        uint32_t wpre = 0;
+#pragma unroll
+        for (int w = 0; w < RS_WARPS; ++w) wpre += w < warp ? s_wsum[w] : 0u;
+        const uint32_t tstart = wpre + x - c;
+        s_tstart[tid] = tstart;
+        s_goff[tid] = st[tid] - tstart;  // destination of sorted slot i with digit d: s_goff[d] + i
+        consumer_sync<RS_THREADS>();
+#pragma unroll
+        for (int j = 0; j < IPT; ++j)
+            if (dig[j] < RADIX) slot[j] += s_tstart[dig[j]] + s_wc[warp][dig[j]];
+        __syncwarp();
+        for (int d = lane; d < RADIX; d += 32) s_wc[warp][d] = 0;  // own row, read above only by this warp
+#pragma unroll
+        for (int j = 0; j < IPT; ++j)
+            if (dig[j] < RADIX) sbuf[slot[j]] = skeys[wbase + j * 32 + lane];
+        consumer_sync<RS_THREADS>();
+        // A destination outside [0, count) can only come from inconsistent
+        // counts; it is reported and never written.
+        uint32_t dest[IPT];
+#pragma unroll
+        for (int r = 0; r < IPT; ++r) {
+            const int i = r * RS_THREADS + tid;
+            dest[r] = 0xffffffffu;
+            if (i < M.n) {
+                const KW kk = sbuf[i];
+                const uint32_t dd = s_goff[digit_of(kk, shift)] + (uint32_t)i;
+                if ((int64_t)dd < count) {
+                    dest[r] = dd;
+                    if (key_dst) key_dst[dd] = kk;
+                } else {
+                    atomicOr(err, ERR_INTERNAL);
+                }
             }
         }
-        __syncthreads();
-        uint32_t* dst = pay.dst[p];
-        for (int s = tid; s < tile_n; s += SORT_THREADS) {
-            const uint32_t dd = s_dest[s];
-            if (dd != 0xffffffffu) dst[dd] = s_val[s];
+        for (int p = 0; p < pay.n; ++p) {
+            consumer_sync<RS_THREADS>();  // earlier readers of the sorted tile are done
+            const uint32_t* src = pay.src[p];
+            const uint32_t* sp = st + RADIX + TILE * KWW + p * TILE;
+            const bool staged = p < SP && src != nullptr;
+#pragma unroll
+            for (int j = 0; j < IPT; ++j) {
+                const int o = wbase + j * 32 + lane;
+                if (dig[j] < RADIX)
+                    sb32[slot[j]] = staged ? sp[o] : (src ? src[M.base + o] : (uint32_t)(M.base + o));
+            }
+            consumer_sync<RS_THREADS>();
+            uint32_t* dst = pay.dst[p];
+#pragma unroll
+            for (int r = 0; r < IPT; ++r)
+                if (dest[r] != 0xffffffffu) dst[dest[r]] = sb32[r * RS_THREADS + tid];
         }
-        __syncthreads();
+        // every read of this stage is behind the barriers above
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
     }
 }
 
@@ -476,54 +610,88 @@ cudaError_t launch_transform(int dtype, const void* coords, int64_t n, int k, vo
     return cudaGetLastError();
 }
 
-int sort_tile(int key64) { return key64 ? SORT_TILE / 2 : SORT_TILE; }
-// Status words of one pass: flags [tiles] | aggregate records [tiles][256]
-// u16 | inclusive records [tiles][256] u32.  Only the flags need zeroing.
-// Sized for the smaller (64-bit key) tiles, which covers both key widths.
-static int64_t sort_tiles_max(int64_t max_count) { return (max_count + SORT_TILE / 2 - 1) / (SORT_TILE / 2); }
-size_t sort_status_words(int64_t max_count) {
-    const int64_t tiles = sort_tiles_max(max_count);
-    return (size_t)pad4(tiles) + (size_t)tiles * RADIX / 2 + (size_t)tiles * RADIX;
+// Status area of the sort passes, reused by every pass (u32 words, regions
+// 16-byte aligned): tile counts [tiles][256] | tile offsets [tiles][256] |
+// chunk flags [chunks] | chunk aggregates [chunks][256] | chunk inclusive
+// prefixes [chunks][256] | scan and move tile counters.  Sized for the
+// smallest tile.
+struct SortStatusArea {
+    uint32_t *cnt, *offs, *flags, *agg, *inc, *ctrs;
+    int64_t nchunks;
+};
+static SortStatusArea sort_status_layout(int64_t max_count, uint32_t* status) {
+    const int64_t tiles = pad4((max_count + RS_TILE_MIN - 1) / RS_TILE_MIN);
+    const int64_t chunks = pad4((tiles + RS_CHUNK - 1) / RS_CHUNK);
+    SortStatusArea A;
+    A.cnt = status;
+    A.offs = A.cnt + tiles * RADIX;
+    A.flags = A.offs + tiles * RADIX;
+    A.agg = A.flags + chunks;
+    A.inc = A.agg + chunks * RADIX;
+    A.ctrs = A.inc + chunks * RADIX;
+    A.nchunks = chunks;
+    return A;
 }
-size_t sort_flag_words(int64_t max_count) { return (size_t)pad4(sort_tiles_max(max_count)); }
+size_t sort_status_words(int64_t max_count) {
+    const int64_t tiles = pad4((max_count + RS_TILE_MIN - 1) / RS_TILE_MIN);
+    const int64_t chunks = pad4((tiles + RS_CHUNK - 1) / RS_CHUNK);
+    return (size_t)(2 * tiles * RADIX + chunks + 2 * chunks * RADIX + 4);
+}
 
-cudaError_t launch_sort_pass(int key64, int mode, const int64_t* count_ptr, int64_t max_count,
-                             const void* key_src, const uint32_t* gidx, void* key_dst,
-                             const PayloadArgs& pay, const uint32_t* digit_base, int shift,
-                             uint32_t* status, uint32_t* tile_ctr, int* err, cudaStream_t s) {
-    const int64_t gather_limit = max_count;  // tuple ids index planes of max_count entries
-    const int tile = sort_tile(key64);
-    const int64_t tiles = (max_count + tile - 1) / tile;
-    if (tiles == 0) return cudaSuccess;
-    const int64_t tmax = sort_tiles_max(max_count);
-    SortStatus st;
-    st.flags = status;
-    st.aggrec = reinterpret_cast<uint16_t*>(status + pad4(tmax));
-    st.increc = status + pad4(tmax) + tmax * RADIX / 2;
-    const size_t smem = (size_t)tile * 8 + (size_t)tile * 2;
-#define KD_SORT_LAUNCH(KW, MODE)                                                                          \
-    do {                                                                                                  \
-        auto kf = k_sort_pass<KW, MODE>;                                                                  \
-        kf<<<(unsigned)tiles, SORT_THREADS, smem, s>>>(count_ptr, (const KW*)key_src, gidx, (KW*)key_dst, \
-                                                       pay, digit_base, shift, st, tile_ctr, err,         \
-                                                       gather_limit);                                     \
-    } while (0)
-    if (key64) {
-        if (mode == KEY_DIRECT) KD_SORT_LAUNCH(uint64_t, KEY_DIRECT);
-        else if (mode == KEY_GATHER) KD_SORT_LAUNCH(uint64_t, KEY_GATHER);
-        else KD_SORT_LAUNCH(uint64_t, KEY_BUF);
-    } else {
-        if (mode == KEY_DIRECT) KD_SORT_LAUNCH(uint32_t, KEY_DIRECT);
-        else if (mode == KEY_GATHER) KD_SORT_LAUNCH(uint32_t, KEY_GATHER);
-        else KD_SORT_LAUNCH(uint32_t, KEY_BUF);
-    }
-#undef KD_SORT_LAUNCH
+// Resident blocks per SM of the move kernels (by variant) and the SM count.
+static int g_rs_occ[4];
+static int g_rs_sms = 0;
+
+template <typename KW, int TILE, int SP>
+static cudaError_t rs_pass(const int64_t* count_ptr, int64_t max_count, const void* key_src, void* key_dst,
+                           const PayloadArgs& pay, const uint32_t* digit_base, int shift, const SortStatusArea& A,
+                           int occ, int* err, cudaStream_t s) {
+    const int64_t tiles = (max_count + TILE - 1) / TILE;
+    const int64_t chunks = (tiles + RS_CHUNK - 1) / RS_CHUNK;
+    k_rs_count<KW, TILE><<<(unsigned)tiles, 256, 0, s>>>(count_ptr, (const KW*)key_src, shift, A.cnt, A.flags,
+                                                          (int)A.nchunks, A.ctrs);
+    k_rs_scan<<<(unsigned)chunks, 256, 0, s>>>(count_ptr, TILE, A.cnt, digit_base, A.offs, A.flags, A.agg, A.inc,
+                                               A.ctrs, A.ctrs + 1, err);
+    const int64_t grid = std::min<int64_t>(tiles, (int64_t)g_rs_sms * occ);
+    k_rs_move<KW, TILE, SP><<<(unsigned)grid, RS_BLOCK, rs_move_smem<KW, TILE, SP>(), s>>>(
+        count_ptr, (const KW*)key_src, (KW*)key_dst, pay, A.offs, shift, A.ctrs + 1, err);
     return cudaGetLastError();
 }
 
-// Dynamic shared memory limits, set once per process at their maxima (a
-// per-launch setting would race between threads launching on the same
-// kernels with different sizes).
+// One stable LSD pass over *count_ptr (<= max_count) elements on digit
+// (key >> shift) & 255: keys from key_src (written to key_dst when not
+// NULL), payload planes moved along (a NULL source means the position).
+// Key, payload and plane buffers must be 16-byte aligned and readable up to
+// the count rounded up to a multiple of 4 elements.
+cudaError_t launch_sort_pass(int key64, const int64_t* count_ptr, int64_t max_count, const void* key_src,
+                             void* key_dst, const PayloadArgs& pay, const uint32_t* digit_base, int shift,
+                             uint32_t* status, int* err, cudaStream_t s) {
+    if (max_count == 0) return cudaSuccess;
+    if (g_rs_sms == 0) return cudaErrorInvalidValue;
+    const SortStatusArea A = sort_status_layout(max_count, status);
+    const bool many = pay.n > 1;
+    if (key64)
+        return many ? rs_pass<uint64_t, 1024, 4>(count_ptr, max_count, key_src, key_dst, pay, digit_base, shift, A,
+                                                 g_rs_occ[3], err, s)
+                    : rs_pass<uint64_t, 2048, 1>(count_ptr, max_count, key_src, key_dst, pay, digit_base, shift, A,
+                                                 g_rs_occ[2], err, s);
+    return many ? rs_pass<uint32_t, 2048, 4>(count_ptr, max_count, key_src, key_dst, pay, digit_base, shift, A,
+                                             g_rs_occ[1], err, s)
+                : rs_pass<uint32_t, 4096, 1>(count_ptr, max_count, key_src, key_dst, pay, digit_base, shift, A,
+                                             g_rs_occ[0], err, s);
+}
+
+template <typename KW, int TILE, int SP>
+static cudaError_t init_rs_move(int* occ) {
+    const size_t smem = rs_move_smem<KW, TILE, SP>();
+    cudaError_t e = cudaFuncSetAttribute((const void*)k_rs_move<KW, TILE, SP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int o = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_rs_move<KW, TILE, SP>, RS_BLOCK, smem);
+    *occ = o > 0 ? o : 1;
+    return e;
+}
+
 cudaError_t init_presort_kernels() {
     cudaError_t e = cudaSuccess;
     auto set = [&](const void* f, size_t bytes) {
@@ -532,13 +700,13 @@ cudaError_t init_presort_kernels() {
     set((const void*)k_transform<int32_t, uint32_t>, TRANSFORM_SMEM_MAX);
     set((const void*)k_transform<int64_t, uint64_t>, TRANSFORM_SMEM_MAX);
     set((const void*)k_transform<float, uint32_t>, TRANSFORM_SMEM_MAX);
-    const size_t s32 = (size_t)SORT_TILE * 10, s64 = (size_t)(SORT_TILE / 2) * 10;
-    set((const void*)k_sort_pass<uint32_t, KEY_DIRECT>, s32);
-    set((const void*)k_sort_pass<uint32_t, KEY_GATHER>, s32);
-    set((const void*)k_sort_pass<uint32_t, KEY_BUF>, s32);
-    set((const void*)k_sort_pass<uint64_t, KEY_DIRECT>, s64);
-    set((const void*)k_sort_pass<uint64_t, KEY_GATHER>, s64);
-    set((const void*)k_sort_pass<uint64_t, KEY_BUF>, s64);
+    int dev = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g_rs_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = init_rs_move<uint32_t, 4096, 1>(&g_rs_occ[0]);
+    if (e == cudaSuccess) e = init_rs_move<uint32_t, 2048, 4>(&g_rs_occ[1]);
+    if (e == cudaSuccess) e = init_rs_move<uint64_t, 2048, 1>(&g_rs_occ[2]);
+    if (e == cudaSuccess) e = init_rs_move<uint64_t, 1024, 4>(&g_rs_occ[3]);
     return e;
 }
 

@@ -322,18 +322,39 @@ __global__ void __launch_bounds__(LEVEL_BLOCK)
         tile_bounds(rec, tlo, thi);
         const int32_t lo0 = tlo[0];
         const int F = M.F;
+        if (ns == 1 && F == K - 1) {  // one segment, every decision level
+            const uint32_t* med = rec + TR_HEAD;
 #pragma unroll
-        for (int j = 0; j < IPT; ++j) {
-            const int o = wbase + j * 32 + lane;
-            if (o < M.npos) {
+            for (int j = 0; j < IPT; ++j) {
+                const int o = wbase + j * 32 + lane;
                 const int32_t pos = M.pos0 + o;
-                const int sj = tile_slot(tlo, thi, ns, pos);
-                if (sj >= 0) {
-                    uint32_t r[K];
+                if (o < M.npos && pos >= tlo[0] && pos <= thi[0]) {
+                    uint32_t h = 1;
+                    bool eq = false;
 #pragma unroll
-                    for (int f = 0; f < K; ++f) r[f] = (f < F) ? st[TW + NBP + f * PST + M.shift + o] : 0u;
-                    const uint32_t d = route_rec<K>(r, F, sj, rec);
-                    if (d != INV) atomicAdd(&s_cnt[s][d], 1u);
+                    for (int f = 0; f < K - 1; ++f) {
+                        const uint32_t r = st[TW + NBP + f * PST + M.shift + o];
+                        const uint32_t mv = med[h];
+                        eq |= r == mv;
+                        h = 2 * h + (r > mv ? 1u : 0u);
+                    }
+                    if (!eq) atomicAdd(&s_cnt[s][h - (uint32_t)NBMAX], 1u);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < IPT; ++j) {
+                const int o = wbase + j * 32 + lane;
+                if (o < M.npos) {
+                    const int32_t pos = M.pos0 + o;
+                    const int sj = tile_slot(tlo, thi, ns, pos);
+                    if (sj >= 0) {
+                        uint32_t r[K];
+#pragma unroll
+                        for (int f = 0; f < K; ++f) r[f] = (f < F) ? st[TW + NBP + f * PST + M.shift + o] : 0u;
+                        const uint32_t d = route_rec<K>(r, F, sj, rec);
+                        if (d != INV) atomicAdd(&s_cnt[s][d], 1u);
+                    }
                 }
             }
         }
@@ -402,6 +423,32 @@ __global__ void __launch_bounds__(1024) k_level_scan(int ntiles, int stride, con
         const uint32_t lastf = s_f[31], lastv = s_v[31];
         carry = lastf ? lastv : carry + lastv;
         __syncthreads();
+    }
+}
+
+// Stable warp ranking of digits below `marker` (the marker: no element):
+// lanes with equal digits from ballots over the low `nbits` <= MAXBITS digit
+// bits; the lowest such lane advances the warp's counter of the digit.
+template <int IPT, int MAXBITS>
+__device__ __forceinline__ void warp_rank(const uint32_t (&dig)[IPT], uint32_t marker, int nbits,
+                                          uint32_t* __restrict__ wc, uint32_t (&rank)[IPT]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+        const uint32_t d = dig[j];
+        uint32_t peers = 0xffffffffu;
+#pragma unroll
+        for (int bit = 0; bit < MAXBITS; ++bit) {
+            if (bit < nbits) {
+                const uint32_t bb = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
+                peers &= ((d >> bit) & 1u) ? bb : ~bb;
+            }
+        }
+        const int leader = __ffs(peers) - 1;
+        uint32_t old = 0;
+        if (lane == leader && d < marker) old = atomicAdd(&wc[d], (uint32_t)__popc(peers));
+        old = __shfl_sync(0xffffffffu, old, leader);
+        rank[j] = old + __popc(peers & lanemask_lt());
     }
 }
 
@@ -477,44 +524,56 @@ __global__ void __launch_bounds__(LEVEL_BLOCK, K <= 3 ? 3 : 2)
         const int nbits = 32 - __clz(marker);
         uint32_t v[K][IPT];
         uint32_t dig[IPT];
-#pragma unroll
-        for (int j = 0; j < IPT; ++j) {
-            const int o = wbase + j * 32 + lane;
-            dig[j] = marker;
-#pragma unroll
-            for (int f = 0; f < K; ++f) v[f][j] = 0;
-            if (o < M.npos) {
-#pragma unroll
-                for (int f = 0; f < K; ++f) v[f][j] = st[TW + NBP + f * PST + M.shift + o];
-                const int sj = tile_slot(tlo, thi, ns, M.pos0 + o);
-                if (sj >= 0) {
-                    uint32_t r[K];
-#pragma unroll
-                    for (int f = 0; f < K; ++f) r[f] = v[f][j];
-                    const uint32_t d = route_rec<K>(r, F, sj, rec);
-                    if (d != INV) dig[j] = d;
-                }
-            }
-        }
-        // stable warp ranking: lanes with equal digits from ballots over the
-        // digit bits (nbits of them suffice for this tile)
         uint32_t rank[IPT];
+        if (ns == 1 && F == K - 1) {
+            // one segment and every decision level: compile-time routing and
+            // K ballot bits (buckets 0 .. NB-1, marker NB)
+            const uint32_t* med = rec + TR_HEAD;
 #pragma unroll
-        for (int j = 0; j < IPT; ++j) {
-            const uint32_t d = dig[j];
-            uint32_t peers = 0xffffffffu;
+            for (int j = 0; j < IPT; ++j) {
+                const int o = wbase + j * 32 + lane;
+                const int32_t pos = M.pos0 + o;
+                dig[j] = marker;
 #pragma unroll
-            for (int bit = 0; bit < DBITS; ++bit) {
-                if (bit < nbits) {
-                    const uint32_t bb = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
-                    peers &= ((d >> bit) & 1u) ? bb : ~bb;
+                for (int f = 0; f < K; ++f) v[f][j] = 0;
+                if (o < M.npos) {
+#pragma unroll
+                    for (int f = 0; f < K; ++f) v[f][j] = st[TW + NBP + f * PST + M.shift + o];
+                    if (pos >= tlo[0] && pos <= thi[0]) {
+                        uint32_t h = 1;
+                        bool eq = false;
+#pragma unroll
+                        for (int f = 0; f < K - 1; ++f) {
+                            const uint32_t mv = med[h];
+                            eq |= v[f][j] == mv;
+                            h = 2 * h + (v[f][j] > mv ? 1u : 0u);
+                        }
+                        if (!eq) dig[j] = h - (uint32_t)NBMAX;
+                    }
                 }
             }
-            const int leader = __ffs(peers) - 1;
-            uint32_t old = 0;
-            if (lane == leader && d < marker) old = atomicAdd(&s_wc[warp][d], (uint32_t)__popc(peers));
-            old = __shfl_sync(0xffffffffu, old, leader);
-            rank[j] = old + __popc(peers & lanemask_lt());
+            warp_rank<IPT, K>(dig, marker, K, s_wc[warp], rank);
+        } else {
+#pragma unroll
+            for (int j = 0; j < IPT; ++j) {
+                const int o = wbase + j * 32 + lane;
+                dig[j] = marker;
+#pragma unroll
+                for (int f = 0; f < K; ++f) v[f][j] = 0;
+                if (o < M.npos) {
+#pragma unroll
+                    for (int f = 0; f < K; ++f) v[f][j] = st[TW + NBP + f * PST + M.shift + o];
+                    const int sj = tile_slot(tlo, thi, ns, M.pos0 + o);
+                    if (sj >= 0) {
+                        uint32_t r[K];
+#pragma unroll
+                        for (int f = 0; f < K; ++f) r[f] = v[f][j];
+                        const uint32_t d = route_rec<K>(r, F, sj, rec);
+                        if (d != INV) dig[j] = d;
+                    }
+                }
+            }
+            warp_rank<IPT, DBITS>(dig, marker, nbits, s_wc[warp], rank);
         }
         consumer_sync<LEVEL_THREADS>();
         // per digit: prefix over warps; base, bounds and middle of its final

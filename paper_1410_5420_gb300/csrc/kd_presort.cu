@@ -204,7 +204,7 @@ constexpr size_t rs_move_smem() {
 }
 
 template <typename KW, int TILE, int SP>
-__global__ void __launch_bounds__(RS_BLOCK, 2)
+__global__ void __launch_bounds__(RS_BLOCK, TILE * (SP + 1) * sizeof(KW) <= 2048 * 8 ? 3 : 2)
     k_rs_move(const int64_t* __restrict__ count_ptr, const KW* __restrict__ key_src, KW* __restrict__ key_dst,
               const __grid_constant__ PayloadArgs pay, const uint32_t* __restrict__ offs, int shift,
               uint32_t* __restrict__ ctr, int* __restrict__ err) {
@@ -215,6 +215,7 @@ __global__ void __launch_bounds__(RS_BLOCK, 2)
     __shared__ __align__(8) uint64_t full[2], empty[2];
     __shared__ SortMeta meta[2];
     __shared__ uint32_t s_wc[RS_WARPS][RADIX];
+    __shared__ uint32_t s_match[RS_WARPS][RADIX];  // lane masks of the ranking; all zero between uses
     __shared__ uint32_t s_goff[RADIX], s_tstart[RADIX];
     __shared__ uint32_t s_wsum[RS_WARPS];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -225,7 +226,10 @@ __global__ void __launch_bounds__(RS_BLOCK, 2)
         }
         fence_mbar_init();
     }
-    for (int i = tid; i < RS_WARPS * RADIX; i += RS_BLOCK) (&s_wc[0][0])[i] = 0;
+    for (int i = tid; i < RS_WARPS * RADIX; i += RS_BLOCK) {
+        (&s_wc[0][0])[i] = 0;
+        (&s_match[0][0])[i] = 0;
+    }
     __syncthreads();
     const int64_t count = *count_ptr;
     const int64_t ntiles = (count + TILE - 1) / TILE;
@@ -278,23 +282,26 @@ __global__ void __launch_bounds__(RS_BLOCK, 2)
         if (M.t < 0) break;
         const uint32_t* st = rsm + (size_t)s * SW;
         const KW* skeys = reinterpret_cast<const KW*>(st + RADIX);
-        const int nbits = M.n == TILE ? 8 : 9;  // digit 256 marks a slot past the tile's end
+        // stable warp ranking: each lane ORs its bit into its digit's mask
+        // word, reads back the lanes sharing its digit, and the highest of
+        // them advances the warp's counter for the digit and clears the word
         uint32_t dig[IPT], slot[IPT];
 #pragma unroll
         for (int j = 0; j < IPT; ++j) {
             const int o = wbase + j * 32 + lane;
             const uint32_t d = o < M.n ? digit_of(skeys[o], shift) : (uint32_t)RADIX;
-            uint32_t peers = 0xffffffffu;
-#pragma unroll
-            for (int bit = 0; bit < 9; ++bit) {
-                if (bit < nbits) {
-                    const uint32_t bb = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
-                    peers &= ((d >> bit) & 1u) ? bb : ~bb;
-                }
-            }
-            const int leader = __ffs(peers) - 1;
+            if (d < RADIX) atomicOr(&s_match[warp][d], 1u << lane);
+            __syncwarp();
+            const uint32_t peers = d < RADIX ? s_match[warp][d] : (1u << lane);
+            __syncwarp();
+            const int leader = 31 - __clz(peers);
             uint32_t old = 0;
-            if (lane == leader && d < RADIX) old = atomicAdd(&s_wc[warp][d], (uint32_t)__popc(peers));
+            if (lane == leader && d < RADIX) {
+                old = s_wc[warp][d];
+                s_wc[warp][d] = old + (uint32_t)__popc(peers);
+                s_match[warp][d] = 0;
+            }
+            __syncwarp();
             old = __shfl_sync(0xffffffffu, old, leader);
             slot[j] = old + __popc(peers & lanemask_lt());
             dig[j] = d;
@@ -677,7 +684,7 @@ cudaError_t launch_sort_pass(int key64, const int64_t* count_ptr, int64_t max_co
                                                  g_rs_occ[2], err, s);
     return many ? rs_pass<uint32_t, 2048, 4>(count_ptr, max_count, key_src, key_dst, pay, digit_base, shift, A,
                                              g_rs_occ[1], err, s)
-                : rs_pass<uint32_t, 4096, 1>(count_ptr, max_count, key_src, key_dst, pay, digit_base, shift, A,
+                : rs_pass<uint32_t, 2048, 1>(count_ptr, max_count, key_src, key_dst, pay, digit_base, shift, A,
                                              g_rs_occ[0], err, s);
 }
 
@@ -703,7 +710,7 @@ cudaError_t init_presort_kernels() {
     int dev = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g_rs_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = init_rs_move<uint32_t, 4096, 1>(&g_rs_occ[0]);
+    if (e == cudaSuccess) e = init_rs_move<uint32_t, 2048, 1>(&g_rs_occ[0]);
     if (e == cudaSuccess) e = init_rs_move<uint32_t, 2048, 4>(&g_rs_occ[1]);
     if (e == cudaSuccess) e = init_rs_move<uint64_t, 2048, 1>(&g_rs_occ[2]);
     if (e == cudaSuccess) e = init_rs_move<uint64_t, 1024, 4>(&g_rs_occ[3]);

@@ -221,8 +221,9 @@ kd_status kd_kernel_stats_reset(kd_ctx *ctx);
  * on-chip finisher's phases, summed over its thread blocks in nanoseconds
  * (block time, not wall time): [0] loading a subtree's rank table and
  * index arrays, [1] levels with segments above 32 tuples, [2] levels
- * finished one warp per segment, [3] resolving node tuples.  Copies
- * min(n, 8) values into out.
+ * finished one warp per segment, [3] resolving node tuples, [4] ordering
+ * every array within the segments the warps finish.  Copies min(n, 8)
+ * values into out.
  */
 kd_status kd_trace_counters(kd_ctx *ctx, double *out, int n);
 

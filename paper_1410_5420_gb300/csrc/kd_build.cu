@@ -652,119 +652,72 @@ __global__ void __launch_bounds__(LEVEL_BLOCK, K <= 3 ? 3 : 2)
 }
 
 // ------------------------------------------------------------- finisher
-constexpr uint32_t HOLE = 0xffffffffu;
 
 __device__ __forceinline__ uint32_t seg_pack(int32_t a, int32_t b) { return (uint32_t)a | ((uint32_t)b << 16); }
 
-// Stable partition of one array (lids, src) around the medians of the
-// current level into dst; side[lid] says where tuple lid goes (0 less, 1
-// greater, 2 the median itself).  Each warp owns a chunk of consecutive positions
-// and walks it 32 at a time: ballots of "less" / "greater" / "segment start"
-// give every lane its count of earlier less/greater elements in its segment;
-// a segment crossing chunk boundaries gets the preceding warps' counts.
-template <int GMAX>
-__device__ __forceinline__ void fin_partition(const uint16_t* __restrict__ src, uint16_t* __restrict__ dst,
-                                              const uint8_t* __restrict__ side, const uint32_t* __restrict__ seg,
-                                              int S, uint32_t* s_agg, int* bad) {
+constexpr int FIN_WARPS = FIN_THREADS / 32;
+constexpr uint8_t LAB_DONE = 0xff;  // the tuple is a node already
+
+// Labels of the last block level: segments at relative level l number 2^l.
+__host__ __device__ constexpr int fin_labels(int smax) { return smax / 32; }
+
+// Unit-relative address range [a, b] of segment X at relative level l.
+__device__ __forceinline__ void label_range(int S, int l, int X, int32_t& a, int32_t& b) {
+    a = 0;
+    b = S - 1;
+    for (int f = l - 1; f >= 0; --f) {
+        const int32_t c = a + ((b - a) >> 1);
+        if ((X >> f) & 1) a = c + 1; else b = c - 1;
+    }
+}
+
+// One pass over array A (lids in key order): each live tuple's rank among
+// the tuples of its segment label, in A's order (stable warp ranking, then
+// the counts of earlier warps).  On return s_wc[w][X] holds the count of
+// label X in warps before w, s_lab[X] = (a, b) of segment X, and a label
+// whose count differs from its segment's size is reported.
+template <int SMAX>
+__device__ __forceinline__ void fin_label_rank(const uint16_t* __restrict__ A, int S, int l,
+                                               const uint8_t* __restrict__ lab, uint32_t (*s_wc)[fin_labels(SMAX)],
+                                               int2* s_lab, uint32_t (&lid)[SMAX / FIN_THREADS],
+                                               uint32_t (&dig)[SMAX / FIN_THREADS],
+                                               uint32_t (&rank)[SMAX / FIN_THREADS], int* bad) {
+    constexpr int IPT = SMAX / FIN_THREADS;
+    constexpr int MAXB = 32 - __builtin_clz((unsigned)fin_labels(SMAX));  // bits of the marker
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int groups = (S + FIN_THREADS - 1) / FIN_THREADS;  // per warp, <= GMAX
-    const int chunk = groups * 32;
-    const uint32_t lt = lanemask_lt();
-    uint32_t info[GMAX];  // lid | isL << 16 | isR << 17 | needs-carry << 18
-    uint32_t ex[GMAX];    // in-warp exclusive counts: less | greater << 16
-    uint32_t pos2[GMAX];  // a | c << 16
-    uint32_t cl = 0, cr = 0;
-    bool seen = false;
+    const uint32_t marker = 1u << l;
 #pragma unroll
-    for (int g = 0; g < GMAX; ++g) {
-        info[g] = 0;
-        ex[g] = 0;
-        pos2[g] = 0;
-        if (g < groups) {
-            const int i = warp * chunk + g * 32 + lane;
-            const uint32_t sg = i < S ? seg[i] : HOLE;
-            bool isL = false, isR = false, start = false;
-            uint32_t lid = 0;
-            int32_t a = 0, c = 0;
-            if (sg != HOLE) {
-                a = sg & 0xffff;
-                const int32_t bb = sg >> 16;
-                c = a + ((bb - a) >> 1);
-                lid = src[i];
-                const uint32_t sd = side[lid];
-                isL = sd == 0;
-                isR = sd == 1;
-                start = i == a;
-            }
-            const uint32_t Lm = __ballot_sync(0xffffffffu, isL);
-            const uint32_t Rm = __ballot_sync(0xffffffffu, isR);
-            const uint32_t Sm = __ballot_sync(0xffffffffu, start);
-            const uint32_t sle = Sm & (lt | (1u << lane));
-            uint32_t inseg, bl, br;
-            bool need = false;
-            if (sle) {
-                const int s0 = 31 - __clz(sle);
-                inseg = lt & ~((1u << s0) - 1u);
-                bl = 0;
-                br = 0;
-            } else {
-                inseg = lt;
-                bl = cl;
-                br = cr;
-                need = !seen;
-            }
-            const uint32_t el = bl + __popc(Lm & inseg), er = br + __popc(Rm & inseg);
-            info[g] = lid | (isL ? 1u << 16 : 0u) | (isR ? 1u << 17 : 0u) | (need ? 1u << 18 : 0u);
-            ex[g] = el | (er << 16);
-            pos2[g] = (uint32_t)a | ((uint32_t)c << 16);
-            if (Sm) {
-                const int sl = 31 - __clz(Sm);
-                const uint32_t tail = ~((1u << sl) - 1u);
-                cl = __popc(Lm & tail);
-                cr = __popc(Rm & tail);
-                seen = true;
-            } else {
-                cl += __popc(Lm);
-                cr += __popc(Rm);
-            }
-        }
+    for (int j = 0; j < IPT; ++j) {
+        const int i = warp * 32 * IPT + j * 32 + lane;
+        lid[j] = i < S ? A[i] : 0u;
+        const uint32_t x = i < S ? lab[lid[j]] : LAB_DONE;
+        dig[j] = x == LAB_DONE ? marker : x;
     }
-    if (lane == 0) s_agg[warp] = (seen ? 1u << 31 : 0u) | (cl & 0x7fffu) | ((cr & 0x7fffu) << 15);
+    warp_rank<IPT, MAXB>(dig, marker, l + 1, s_wc[warp], rank);
     __syncthreads();
-    // carry into this warp's chunk: segmented sum of the preceding warps
-    uint32_t wl = 0, wr = 0;
-    for (int w = 0; w < warp; ++w) {
-        const uint32_t x = s_agg[w];
-        if (x >> 31) {
-            wl = x & 0x7fffu;
-            wr = (x >> 15) & 0x7fffu;
-        } else {
-            wl += x & 0x7fffu;
-            wr += (x >> 15) & 0x7fffu;
-        }
-    }
+    for (int X = tid; X < (int)marker; X += FIN_THREADS) {
+        uint32_t c = 0;
 #pragma unroll
-    for (int g = 0; g < GMAX; ++g) {
-        if (g < groups) {
-            const uint32_t f = info[g];
-            uint32_t el = ex[g] & 0xffffu, er = ex[g] >> 16;
-            if ((f >> 18) & 1u) {
-                el += wl;
-                er += wr;
-            }
-            const int32_t a = pos2[g] & 0xffff, c = pos2[g] >> 16;
-            const uint16_t lid = (uint16_t)(f & 0xffffu);
-            if ((f >> 16) & 1u) {
-                const int32_t o = a + (int32_t)el;
-                if (o < c) dst[o] = lid; else *bad = 1;
-            } else if ((f >> 17) & 1u) {
-                const int32_t o = c + 1 + (int32_t)er;
-                const int32_t i = warp * chunk + g * 32 + lane;
-                const int32_t bb = (int32_t)(seg[i] >> 16);
-                if (o <= bb) dst[o] = lid; else *bad = 1;
-            }
+        for (int w = 0; w < FIN_WARPS; ++w) {
+            const uint32_t x = s_wc[w][X];
+            s_wc[w][X] = c;
+            c += x;
         }
+        int32_t a, b;
+        label_range(S, l, X, a, b);
+        s_lab[X] = make_int2(a, b);
+        if ((int32_t)c != (b >= a ? b - a + 1 : 0)) *bad = 1;
     }
+    __syncthreads();
+}
+
+// The warp's own counter row back to zero for the next pass.
+template <int SMAX>
+__device__ __forceinline__ void fin_clear_row(uint32_t (*s_wc)[fin_labels(SMAX)]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncwarp();
+    for (int X = lane; X < fin_labels(SMAX); X += 32) s_wc[warp][X] = 0;
+    __syncwarp();
 }
 
 // The node at unit position c (median of unit-relative [a, b]) is tuple
@@ -868,14 +821,15 @@ __global__ void __launch_bounds__(FIN_THREADS, SMAX >= 4096 ? 2 : 3)
     constexpr int GMAX = SMAX / FIN_THREADS;
     constexpr int smax = SMAX;
     extern __shared__ __align__(16) uint32_t sm[];
-    __shared__ uint32_t s_agg[FIN_THREADS / 32];
+    __shared__ uint32_t s_wc[FIN_WARPS][fin_labels(SMAX)];
+    __shared__ int2 s_lab[fin_labels(SMAX)];
     __shared__ int s_cur[MAXK + 1];
     __shared__ int s_nseg;
     uint32_t* rk = sm;                                          // rk[p * smax + lid]
     uint32_t* seg = rk + (size_t)k * smax;                      // packed segment per position
     uint16_t* arr = reinterpret_cast<uint16_t*>(seg + smax);   // (k+1) storages of lids
     uint16_t* nodelid = arr + (size_t)(k + 1) * smax;           // tuple chosen at each position
-    uint8_t* side = reinterpret_cast<uint8_t*>(nodelid + smax);  // per lid: side of this level's split
+    uint8_t* lab = reinterpret_cast<uint8_t*>(nodelid + smax);   // per lid: segment label at the current level
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     FinUnit U;
     U.cloud = last_le(unit_prefix, ncloud + 1, blockIdx.x);
@@ -908,56 +862,66 @@ __global__ void __launch_bounds__(FIN_THREADS, SMAX >= 4096 ? 2 : 3)
         case 8: fin_load_dispatch<8, SMAX>(bufs, C, g, S, rk, arr, &bad); break;
         default: bad = 1;
     }
-    __syncthreads();
     for (int i = tid; i < S; i += FIN_THREADS) {
-        arr[i] = (uint16_t)i;
-        seg[i] = seg_pack(0, S - 1);
+        arr[i] = (uint16_t)i;  // array 0 is the rank table's own order
+        lab[i] = 0;
     }
+    for (int i = tid; i < FIN_WARPS * fin_labels(SMAX); i += FIN_THREADS) (&s_wc[0][0])[i] = 0;
     __syncthreads();
     FIN_STAMP(0);  // rank table and lids of the unit
-    // block levels: while a segment may hold more than 32 tuples.  cur
-    // packs which storage holds array d (4 bits each; storage k is spare);
-    // every thread keeps the same copy, so rotating needs no barrier.
-    uint64_t cur = 0;
-    for (int d = 0; d <= k; ++d) cur |= (uint64_t)d << (4 * d);
-    auto slot = [&](int d) { return (int)((cur >> (4 * d)) & 0xfu); };
+    // Block levels, while a segment may hold more than 32 tuples.  The k
+    // arrays keep their unit-level order (array d sorted by super key d) and
+    // every tuple carries its segment label at the current level (lab[lid],
+    // LAB_DONE once it is a node).  At level l a pass over the primary array
+    // p ranks each tuple among its label's tuples in key-p order: the one at
+    // the segment's median offset becomes the node, the others take the
+    // label of their half.
     int dl = 0;
     for (; (S >> dl) > 32; ++dl) {
-        const int L = C.lam + dl;
-        const int p = L % k;
-        const uint16_t* prim = arr + slot(p) * smax;
-        // the primary array decides every tuple's side; its medians are nodes
-        for (int i = tid; i < S; i += FIN_THREADS) {
-            const uint32_t sg = seg[i];
-            if (sg == HOLE) continue;
-            const int32_t a = sg & 0xffff, b = sg >> 16, c = a + ((b - a) >> 1);
-            const uint16_t lid = prim[i];
-            side[lid] = i < c ? 0 : (i > c ? 1 : 2);
-            if (i == c) fin_emit(C, nodelid, lo, a, b, c, lid, p);
+        const int p = (C.lam + dl) % k;
+        uint32_t lid[GMAX], dig[GMAX], rank[GMAX];
+        fin_label_rank<SMAX>(arr + p * smax, S, dl, lab, s_wc, s_lab, lid, dig, rank, &bad);
+        const uint32_t marker = 1u << dl;
+#pragma unroll
+        for (int j = 0; j < GMAX; ++j) {
+            if (dig[j] < marker) {
+                const int X = (int)dig[j];
+                const int2 ab = s_lab[X];
+                const int32_t off = (ab.y - ab.x) >> 1;
+                const int32_t r = (int32_t)(s_wc[warp][X] + rank[j]);
+                if (r == off) {
+                    fin_emit(C, nodelid, lo, ab.x, ab.y, ab.x + off, (uint16_t)lid[j], p);
+                    lab[lid[j]] = LAB_DONE;
+                } else {
+                    lab[lid[j]] = (uint8_t)(2 * X + (r > off ? 1 : 0));
+                }
+            }
         }
+        fin_clear_row<SMAX>(s_wc);
         __syncthreads();
-        FIN_STAMP(4);  // block levels: sides and nodes
-        for (int j = 1; j < k; ++j) {
-            const int d = (p + j) % k;
-            fin_partition<GMAX>(arr + slot(d) * smax, arr + slot(k) * smax, side, seg, S, s_agg, &bad);
-            const int x = slot(d), y = slot(k);
-            cur = (cur & ~((uint64_t)0xf << (4 * d)) & ~((uint64_t)0xf << (4 * k))) | ((uint64_t)y << (4 * d)) |
-                  ((uint64_t)x << (4 * k));
-            __syncthreads();
-        }
-        FIN_STAMP(5);  // block levels: partitions
-        for (int i = tid; i < S; i += FIN_THREADS) {
-            const uint32_t sg = seg[i];
-            if (sg == HOLE) continue;
-            const int32_t a = sg & 0xffff, b = sg >> 16, c = a + ((b - a) >> 1);
-            seg[i] = (i == c) ? HOLE : (i < c ? seg_pack(a, c - 1) : seg_pack(c + 1, b));
-        }
-        __syncthreads();
-        FIN_STAMP(6);  // block levels: segment update
     }
-    if (tid <= k) s_cur[tid] = slot(tid);
+    FIN_STAMP(1);  // block levels
+    // every array in key order within each remaining segment: a stable
+    // multisplit by label, in place (all reads precede the first barrier)
+    for (int q = 0; q < k; ++q) {
+        uint16_t* A = arr + q * smax;
+        uint32_t lid[GMAX], dig[GMAX], rank[GMAX];
+        fin_label_rank<SMAX>(A, S, dl, lab, s_wc, s_lab, lid, dig, rank, &bad);
+        const uint32_t marker = 1u << dl;
+#pragma unroll
+        for (int j = 0; j < GMAX; ++j) {
+            if (dig[j] < marker) {
+                const int2 ab = s_lab[dig[j]];
+                const int32_t o = ab.x + (int32_t)(s_wc[warp][dig[j]] + rank[j]);
+                if (o <= ab.y) A[o] = (uint16_t)lid[j]; else bad = 1;
+            }
+        }
+        fin_clear_row<SMAX>(s_wc);
+        __syncthreads();
+    }
+    if (tid <= k) s_cur[tid] = tid;
     __syncthreads();
-    FIN_STAMP(1);  // levels with segments of more than 32 tuples
+    FIN_STAMP(4);  // final splits by segment
     // warp levels: every remaining segment has at most 32 tuples; one warp
     // finishes a segment with one tuple per lane, in the order of the
     // current primary array.  For every dimension q the lane holds LESS_q,
@@ -966,11 +930,12 @@ __global__ void __launch_bounds__(FIN_THREADS, SMAX >= 4096 ? 2 : 3)
     // then popc(LESS_p & SUB): equal to the median offset -> node, below ->
     // left child, above -> right child.
     uint32_t* list = reinterpret_cast<uint32_t*>(arr + s_cur[k] * smax);  // spare storage, first smax bytes
-    for (int i = tid; i < S; i += FIN_THREADS) {
-        const uint32_t sg = seg[i];
-        if (sg != HOLE && (int32_t)(sg & 0xffff) == i) {
+    for (int X = tid; X < (1 << dl); X += FIN_THREADS) {
+        int32_t a, b;
+        label_range(S, dl, X, a, b);
+        if (b >= a) {
             const int e = atomicAdd(&s_nseg, 1);
-            if (e < smax / 4) list[e] = sg; else bad = 1;  // below lane_of (byte smax)
+            if (e < smax / 4) list[e] = seg_pack(a, b); else bad = 1;  // below lane_of (byte smax)
         }
     }
     __syncthreads();

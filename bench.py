@@ -54,9 +54,10 @@ def parse():
                     help="cpu_baseline: oracle sample size in points (2^24: about 15 s of one core)")
     ap.add_argument("--ref-sample", type=int, default=1 << 21,
                     help="--impl reference: oracle sample per step in points (about 2 s of one core)")
-    ap.add_argument("--mode", default="plain", choices=["plain", "batched", "served"],
+    ap.add_argument("--mode", default="plain", choices=["plain", "batched", "served", "sweep"],
                     help="plain: the 2^26 build (default line); batched: 4096 uneven clouds in one call "
-                         "vs per-cloud calls; served: a Poisson request stream through kd_submit")
+                         "vs per-cloud calls; served: a Poisson request stream through kd_submit; "
+                         "sweep: n=2^22 at k=2..6")
     ap.add_argument("--clouds", type=int, default=4096)
     ap.add_argument("--requests", type=int, default=2000)
     return ap.parse_args()
@@ -253,15 +254,54 @@ def run_batched(args):
     ctx.close()
 
 
+def run_sweep(args):
+    """Dimension sweep: n = 2^22 tuples at k = 2..6, int64 uniform in
+    [0, 2^40) (seed 3 + k): points/s of presort + build and the bytes each
+    level step moves per element as k grows."""
+    import torch
+    import kdgen
+    from paper_1410_5420_gb300 import api
+    n = min(args.n, 1 << 22)
+    stream = torch.cuda.current_stream()
+    rows = []
+    for k in range(2, 7):
+        x = torch.from_numpy(kdgen.sweep_int64(k, n=n)).cuda()
+        ctx = api.kd_create(0, stream=stream, debug=2)
+        for _ in range(max(1, args.warmup)):
+            api.build_tree(ctx, x, on_device=True)
+        api.kd_kernel_stats_reset(ctx)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            t = api.build_tree(ctx, x, on_device=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        st = api.kd_kernel_stats(ctx)
+        lv = st["level_pass"]
+        rows.append({"k": k, "m": t["m"], "ms": ms, "points_per_s": n / (ms / 1000.0),
+                     "level_steps": lv["launches"] / args.steps,
+                     "level_bytes_per_element": lv["bytes"] / lv["units"] if lv["units"] else None,
+                     "families_ms": {f: v["ms"] / args.steps for f, v in st.items() if v["launches"]}})
+        ctx.close()
+    line = {"metric": METRIC, "mode": "sweep", "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": f"dimension sweep: n={n} tuples, k=2..6, int64 uniform in [0, 2^40) (seed 3+k)"},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+
+
 def run_served(args):
     """Poisson stream of build requests through kd_submit / kd_wait: sizes
-    log-uniform in [2^8, 2^16] (scaled from 2^20), k in {2,3,4}, int32 or
-    float32 mixture; arrival rate 0.8x the measured serial plain throughput."""
+    log-uniform in [2^8, 2^20], k in {2,3,4}, int32 or float32 mixture
+    (the first --requests of the stream); arrival rate 0.8x the measured
+    serial plain throughput, then a saturation run."""
     import threading
     import torch
     import kdgen
     from paper_1410_5420_gb300 import api
-    reqs = kdgen.serving_requests(count=args.requests, seed=5, lo_log2=8.0, hi_log2=16.0)
+    reqs = kdgen.serving_requests(count=args.requests, seed=5, lo_log2=8.0, hi_log2=20.0)
     clouds = [kdgen.serving_cloud(*r) for r in reqs]
     pts = sum(c.shape[0] for c in clouds)
     ctx = api.kd_create(0, mem_budget_bytes=64 << 30)
@@ -294,7 +334,7 @@ def run_served(args):
     sat_s = time.perf_counter() - t1
     line = {"metric": METRIC, "mode": "served", "value": pts / sat_s, "unit": UNIT, "n_gpus": 1,
             "higher_is_better": True, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": f"served: {len(clouds)} Poisson requests, sizes log-U[2^8,2^16], k in {{2,3,4}}, "
+            "config": {"workload": f"served: {len(clouds)} Poisson requests, sizes log-U[2^8,2^20], k in {{2,3,4}}, "
                                    f"int32 U[0,2^24) or float32 mixture (seed 5)", "points": pts,
                        "rate_per_s": rate},
             "poisson": {"points_per_s": pts / served_s, "p50_us": st["p50_us"], "p99_us": st["p99_us"],
@@ -310,7 +350,7 @@ def main():
     rank, world, local = dist_env()
     if args.mode != "plain" and args.impl == "gb300":
         if rank == 0:
-            (run_batched if args.mode == "batched" else run_served)(args)
+            {"batched": run_batched, "served": run_served, "sweep": run_sweep}[args.mode](args)
         return
     if world > 1:
         import torch.distributed as dist

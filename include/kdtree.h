@@ -204,7 +204,7 @@ int64_t kd_launch_count(kd_ctx *ctx);
  * Kernel timing (instrumentation; active when cfg->debug & 2): CUDA events
  * recorded on the context's stream around every launch, summed per kernel
  * family (0 transform, 1 sort pass, 2 dedup, 3 records, 4 level pass,
- * 5 finisher, 6 top nodes, 7 other).  *ms: device time, *launches: launch
+ * 5 finisher, 6 top nodes, 7 other, 8 key gathers between sorts).  *ms: device time, *launches: launch
  * count, *units: elements the launches processed, *bytes: the algorithmic
  * bytes those launches must move (reads + writes per element of each kernel,
  * summed over launches).  Any output pointer may be NULL.  Synchronises the

@@ -67,7 +67,7 @@ using namespace kd;
 
 namespace {
 
-enum Family { F_TRANSFORM = 0, F_SORT, F_DEDUP, F_RECORDS, F_LEVEL, F_FINISH, F_TOP, F_OTHER, F_COUNT };
+enum Family { F_TRANSFORM = 0, F_SORT, F_DEDUP, F_RECORDS, F_LEVEL, F_FINISH, F_TOP, F_OTHER, F_GATHER, F_COUNT };
 
 struct TimedLaunch {
     int family;
@@ -502,7 +502,7 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
         const void* ksrc = P.mode == KEY_BUF ? (const void*)kbuf[kc] : plane_ptr(P.plane);
         void* kdst = next_gathers ? nullptr : (void*)kbuf[kc ^ 1];
         if (P.mode == KEY_GATHER) {  // gather the new plane's keys into order first
-            LaunchTimer lg(ctx, F_SORT, (double)N, nullptr, 4.0 + 2.0 * P.w);
+            LaunchTimer lg(ctx, F_GATHER, (double)N, nullptr, 4.0 + 2.0 * P.w);
             CK(launch_gather(plane64(P.plane), d_n, N, plane_ptr(P.plane), ibuf[ic], kbuf[kc], d_err, s));
             ksrc = kbuf[kc];
         }
@@ -536,7 +536,7 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
         pay.dst[0] = last ? H->perm0 : ibuf[ic ^ 1];
         const void* ksrc = P.mode == KEY_BUF ? (const void*)kbuf[kc] : plane_ptr(-1);
         if (P.mode == KEY_GATHER) {
-            LaunchTimer lg(ctx, F_SORT, 0.0, H->d_m, 12.0);
+            LaunchTimer lg(ctx, F_GATHER, 0.0, H->d_m, 12.0);
             CK(launch_gather(0, H->d_m, N, plane_ptr(-1), ibuf[ic], kbuf[kc], d_err, s));
             ksrc = kbuf[kc];
         }
@@ -591,7 +591,7 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
                 const void* ksrc = P.mode == KEY_BUF ? (const void*)kbuf[kc] : plane_ptr(P.plane);
                 void* kdst = (last || next_gathers) ? nullptr : (void*)kbuf[kc ^ 1];
                 if (P.mode == KEY_GATHER) {
-                    LaunchTimer lg(ctx, F_SORT, 0.0, H->d_m, 4.0 + 2.0 * P.w);
+                    LaunchTimer lg(ctx, F_GATHER, 0.0, H->d_m, 4.0 + 2.0 * P.w);
                     CK(launch_gather(plane64(P.plane), H->d_m, N, plane_ptr(P.plane), cur_id, kbuf[kc], d_err, s));
                     ksrc = kbuf[kc];
                 }

@@ -865,6 +865,7 @@ __global__ void __launch_bounds__(FIN_THREADS, SMAX >= 4096 ? 2 : 3)
     for (int i = tid; i < S; i += FIN_THREADS) {
         arr[i] = (uint16_t)i;  // array 0 is the rank table's own order
         lab[i] = 0;
+        nodelid[i] = 0xffffu;  // every address gets its node below; checked at the end
     }
     for (int i = tid; i < FIN_WARPS * fin_labels(SMAX); i += FIN_THREADS) (&s_wc[0][0])[i] = 0;
     __syncthreads();
@@ -1019,7 +1020,12 @@ __global__ void __launch_bounds__(FIN_THREADS, SMAX >= 4096 ? 2 : 3)
     FIN_STAMP(2);  // warp levels
 #pragma unroll 4
     for (int i = tid; i < S; i += FIN_THREADS) {
-        const uint32_t r0 = rk[nodelid[i]];
+        const uint32_t nl = nodelid[i];
+        if (nl >= (uint32_t)S) {
+            bad = 1;
+            continue;
+        }
+        const uint32_t r0 = rk[nl];
         if (r0 >= C.off && r0 < C.off + C.m)
             C.node[lo + i] = (int32_t)((int64_t)perm0[r0] - C.in_off);
         else

@@ -559,14 +559,31 @@ __global__ void k_perm_bases(const int64_t* __restrict__ m_ptr, int shift, uint3
     bases[threadIdx.x] = block_excl_scan256((uint32_t)c, s_warp, nullptr);
 }
 
+// Scatter of nval planes by destination: dst[j][dest[i]] = src[j][i].  Each
+// thread moves PS_ITEMS elements with all their loads in flight at once.
+constexpr int PS_ITEMS = 8;
 __global__ void __launch_bounds__(256) k_perm_scatter(const int64_t* __restrict__ m_ptr,
                                                       const uint32_t* __restrict__ dest, int nval,
                                                       const __grid_constant__ PayloadArgs pa) {
     const int64_t m = *m_ptr;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t d = dest[i];
-        if ((int64_t)d >= m) continue;  // inconsistent input: never written out of range
-        for (int j = 0; j < nval; ++j) pa.dst[j][d] = pa.src[j][i];
+    const int64_t base = (int64_t)blockIdx.x * 256 * PS_ITEMS + threadIdx.x;
+    if (base >= m) return;
+    uint32_t d[PS_ITEMS];
+#pragma unroll
+    for (int e = 0; e < PS_ITEMS; ++e) {
+        const int64_t i = base + (int64_t)e * 256;
+        d[e] = i < m ? dest[i] : 0xffffffffu;
+    }
+    for (int j = 0; j < nval; ++j) {
+        uint32_t v[PS_ITEMS];
+#pragma unroll
+        for (int e = 0; e < PS_ITEMS; ++e) {
+            const int64_t i = base + (int64_t)e * 256;
+            v[e] = i < m ? pa.src[j][i] : 0u;
+        }
+#pragma unroll
+        for (int e = 0; e < PS_ITEMS; ++e)
+            if ((int64_t)d[e] < m) pa.dst[j][d[e]] = v[e];  // an inconsistent destination is never written
     }
 }
 
@@ -779,7 +796,8 @@ cudaError_t launch_perm_bases(const int64_t* m_ptr, int shift, uint32_t* bases, 
 cudaError_t launch_perm_scatter(const int64_t* m_ptr, int64_t max_m, const uint32_t* dest, const PayloadArgs& pa,
                                 cudaStream_t s) {
     if (max_m == 0) return cudaSuccess;
-    k_perm_scatter<<<grid_for(max_m, 256, 152 * 8), 256, 0, s>>>(m_ptr, dest, pa.n, pa);
+    const int64_t blocks = (max_m + 256 * PS_ITEMS - 1) / (256 * PS_ITEMS);
+    k_perm_scatter<<<(unsigned)blocks, 256, 0, s>>>(m_ptr, dest, pa.n, pa);
     return cudaGetLastError();
 }
 

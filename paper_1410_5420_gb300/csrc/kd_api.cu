@@ -662,7 +662,7 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
             present |= bits << (d * MAXK);
         }
         if (present != 0) {
-            LaunchTimer lt(ctx, F_RECORDS, 0.0, H->d_m, 4.0 * k);
+            LaunchTimer lt(ctx, F_RECORDS, 0.0, H->d_m, 4.0);
             CK(launch_own_ranks(H->d_m, N, k, H->rec, s));
         }
     }
@@ -907,7 +907,8 @@ kd_status build_batch(kd_ctx* ctx, kd_presorted* H, kd_tree* outs) {
     }
     for (size_t st = 0; st < step_jobs.size(); ++st) {
         const int F = step_jobs[st][0].lev_out - step_jobs[st][0].lev_in;
-        LaunchTimer lt(ctx, F_LEVEL, step_elems[st], nullptr, 8.0 * k + 4.0 * F);
+        // array q moves k planes (array 0) or k - 1 (its own rank is not carried)
+        LaunchTimer lt(ctx, F_LEVEL, step_elems[st], nullptr, 8.0 * (k - (step_q[st] != 0)) + 4.0 * F);
         ctx->launches += 3;  // tile records, count pass and scan
         CK(launch_level_pass(k, bufs, step_q[st], d_jobs + job_off[st], (int)step_jobs[st].size(),
                              (int)step_ntiles[st], d_cd, medr, H->perm0, d_status, d_err, s));

@@ -204,15 +204,20 @@ __device__ __forceinline__ void level_producer(const AllBufs& bufs, int q, const
         const int64_t e1 = (g0 + T.npos + 3) & ~(int64_t)3;
         M.shift = (int32_t)(g0 - a0);
         const uint32_t pb = (uint32_t)((e1 - a0) * 4);
+        // the move stages every plane but the array's own (its rank in
+        // super key q, which only array 0 carries); the count the F
+        // decision planes
         const int npl = MOVE ? K : M.F;
+        const int skip = (MOVE && q != 0) ? (q - T.lev_in % K + K) % K : -1;
         meta[s] = M;
         uint32_t* st = smem + (size_t)s * SW;
         fence_proxy_async_smem();
-        mbar_arrive_expect_tx(&full[s], TW * 4 + (M.has_incl ? NBP * 4 : 0) + (uint32_t)npl * pb);
+        mbar_arrive_expect_tx(&full[s], TW * 4 + (M.has_incl ? NBP * 4 : 0) + (uint32_t)(npl - (skip >= 0)) * pb);
         bulk_g2s(st, trec + (int64_t)t * TW, TW * 4, &full[s]);
         if (M.has_incl) bulk_g2s(st + TW, incl + (int64_t)(t - 1) * NBP, NBP * 4, &full[s]);
         for (int f = 0; f < npl; ++f)
-            bulk_g2s(st + TW + NBP + f * PST, bufs.p[q][T.src_buf][(T.lev_in + f) % K] + a0, pb, &full[s]);
+            if (f != skip)
+                bulk_g2s(st + TW + NBP + f * PST, bufs.p[q][T.src_buf][(T.lev_in + f) % K] + a0, pb, &full[s]);
     }
 }
 
@@ -522,6 +527,7 @@ __global__ void __launch_bounds__(LEVEL_BLOCK, K <= 3 ? 3 : 2)
         const int NB = 1 << F;
         const uint32_t marker = (uint32_t)(ns * NB);
         const int nbits = 32 - __clz(marker);
+        const int own = q != 0 ? (q - M.lev_in % K + K) % K : -1;  // slot of the array's own plane: not carried
         uint32_t v[K][IPT];
         uint32_t dig[IPT];
         uint32_t rank[IPT];
@@ -538,7 +544,7 @@ __global__ void __launch_bounds__(LEVEL_BLOCK, K <= 3 ? 3 : 2)
                 for (int f = 0; f < K; ++f) v[f][j] = 0;
                 if (o < M.npos) {
 #pragma unroll
-                    for (int f = 0; f < K; ++f) v[f][j] = st[TW + NBP + f * PST + M.shift + o];
+                    for (int f = 0; f < K; ++f) v[f][j] = f != own ? st[TW + NBP + f * PST + M.shift + o] : 0u;
                     if (pos >= tlo[0] && pos <= thi[0]) {
                         uint32_t h = 1;
                         bool eq = false;
@@ -562,7 +568,7 @@ __global__ void __launch_bounds__(LEVEL_BLOCK, K <= 3 ? 3 : 2)
                 for (int f = 0; f < K; ++f) v[f][j] = 0;
                 if (o < M.npos) {
 #pragma unroll
-                    for (int f = 0; f < K; ++f) v[f][j] = st[TW + NBP + f * PST + M.shift + o];
+                    for (int f = 0; f < K; ++f) v[f][j] = f != own ? st[TW + NBP + f * PST + M.shift + o] : 0u;
                     const int sj = tile_slot(tlo, thi, ns, M.pos0 + o);
                     if (sj >= 0) {
                         uint32_t r[K];
@@ -618,16 +624,19 @@ __global__ void __launch_bounds__(LEVEL_BLOCK, K <= 3 ? 3 : 2)
                     if (dd == s_dmid[d]) {
                         const int sj = (int)(d >> F);
                         const int32_t si = (s_segidx[sj] << F) + (int32_t)(d - ((uint32_t)sj << F));
-                        const int fq = (q - M.lev_in % K + K) % K;
+                        // rank 0 of the median (its position in array 0) gives
+                        // its tuple and, through array 0's initial record,
+                        // its rank in super key q
                         const int f0 = (K - M.lev_in % K) % K;
-                        const uint32_t rq = plane_value<K, IPT>(v, j, fq);
                         const uint32_t r0 = plane_value<K, IPT>(v, j, f0);
                         const int64_t lev_out = M.lev_in + F;
-                        medr[C.medr_off + ((int64_t)1 << lev_out) - 1 + si] = rq;
-                        if (r0 >= M.goff && r0 < M.goff + M.m)
+                        if (r0 >= M.goff && r0 < M.goff + M.m) {
+                            const uint32_t rq = q == 0 ? r0 : bufs.p[0][0][q][r0];
+                            medr[C.medr_off + ((int64_t)1 << lev_out) - 1 + si] = rq;
                             C.node[dd] = (int32_t)((int64_t)perm0[r0] - C.in_off);
-                        else
+                        } else {
                             atomicOr(err, ERR_INTERNAL);
+                        }
                     }
                 } else {
                     atomicOr(err, ERR_INTERNAL);
@@ -638,6 +647,7 @@ __global__ void __launch_bounds__(LEVEL_BLOCK, K <= 3 ? 3 : 2)
         // registers, coalesced per run
 #pragma unroll
         for (int f = 0; f < K; ++f) {
+            if (f == own) continue;
             uint32_t* dp = bufs.p[q][M.dst_buf][(M.lev_in + f) % K] + M.goff;
 #pragma unroll
             for (int j = 0; j < IPT; ++j)

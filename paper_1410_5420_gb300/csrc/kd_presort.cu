@@ -540,10 +540,13 @@ __global__ void __launch_bounds__(256) k_dedup_compact(int64_t n, const uint32_t
 // array d.  After deduplication super keys are unique, so comparing super
 // keys equals comparing these ranks.  The chain sorts write most planes,
 // the permutation below the rest; an array's own plane is its position.
+// Array 0's own rank plane: rec[0][0][i] = i.  (The other arrays' own
+// planes are never read: a level pass moves array d >= 1 without its rank
+// in super key d.)
 __global__ void __launch_bounds__(256) k_own_ranks(const int64_t* __restrict__ m_ptr, int k, AllPlanes rec) {
     const int64_t m = *m_ptr;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
-        for (int d = 0; d < k; ++d) rec.p[d][d][i] = (uint32_t)i;
+        rec.p[0][0][i] = (uint32_t)i;
 }
 
 // Permutation by destination index, in two streaming steps: a sort pass on

@@ -431,32 +431,6 @@ __global__ void __launch_bounds__(1024) k_level_scan(int ntiles, int stride, con
     }
 }
 
-// Stable warp ranking of digits below `marker` (the marker: no element):
-// lanes with equal digits from ballots over the low `nbits` <= MAXBITS digit
-// bits; the lowest such lane advances the warp's counter of the digit.
-template <int IPT, int MAXBITS>
-__device__ __forceinline__ void warp_rank(const uint32_t (&dig)[IPT], uint32_t marker, int nbits,
-                                          uint32_t* __restrict__ wc, uint32_t (&rank)[IPT]) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int j = 0; j < IPT; ++j) {
-        const uint32_t d = dig[j];
-        uint32_t peers = 0xffffffffu;
-#pragma unroll
-        for (int bit = 0; bit < MAXBITS; ++bit) {
-            if (bit < nbits) {
-                const uint32_t bb = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
-                peers &= ((d >> bit) & 1u) ? bb : ~bb;
-            }
-        }
-        const int leader = __ffs(peers) - 1;
-        uint32_t old = 0;
-        if (lane == leader && d < marker) old = atomicAdd(&wc[d], (uint32_t)__popc(peers));
-        old = __shfl_sync(0xffffffffu, old, leader);
-        rank[j] = old + __popc(peers & lanemask_lt());
-    }
-}
-
 // Value of the rotated plane holding super key p: v[f] is plane (lev_in + f) mod K.
 template <int K, int IPT>
 __device__ __forceinline__ uint32_t plane_value(const uint32_t (&v)[K][IPT], int j, int f_sel) {
@@ -544,7 +518,7 @@ __global__ void __launch_bounds__(LEVEL_BLOCK, K <= 3 ? 3 : 2)
                 for (int f = 0; f < K; ++f) v[f][j] = 0;
                 if (o < M.npos) {
 #pragma unroll
-                    for (int f = 0; f < K; ++f) v[f][j] = f != own ? st[TW + NBP + f * PST + M.shift + o] : 0u;
+                    for (int f = 0; f < K; ++f) v[f][j] = st[TW + NBP + f * PST + M.shift + o];  // slot `own` is unused
                     if (pos >= tlo[0] && pos <= thi[0]) {
                         uint32_t h = 1;
                         bool eq = false;
@@ -568,7 +542,7 @@ __global__ void __launch_bounds__(LEVEL_BLOCK, K <= 3 ? 3 : 2)
                 for (int f = 0; f < K; ++f) v[f][j] = 0;
                 if (o < M.npos) {
 #pragma unroll
-                    for (int f = 0; f < K; ++f) v[f][j] = f != own ? st[TW + NBP + f * PST + M.shift + o] : 0u;
+                    for (int f = 0; f < K; ++f) v[f][j] = st[TW + NBP + f * PST + M.shift + o];  // slot `own` is unused
                     const int sj = tile_slot(tlo, thi, ns, M.pos0 + o);
                     if (sj >= 0) {
                         uint32_t r[K];

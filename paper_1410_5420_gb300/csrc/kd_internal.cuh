@@ -524,6 +524,32 @@ __device__ __forceinline__ LevelTile job_tile(const LevelJob* __restrict__ jobs,
     return T;
 }
 
+// Stable warp ranking of digits below `marker` (the marker: no element):
+// lanes with equal digits from ballots over the low `nbits` <= MAXBITS digit
+// bits; the lowest such lane advances the warp's counter of the digit.
+template <int IPT, int MAXBITS>
+__device__ __forceinline__ void warp_rank(const uint32_t (&dig)[IPT], uint32_t marker, int nbits,
+                                          uint32_t* __restrict__ wc, uint32_t (&rank)[IPT]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+        const uint32_t d = dig[j];
+        uint32_t peers = 0xffffffffu;
+#pragma unroll
+        for (int bit = 0; bit < MAXBITS; ++bit) {
+            if (bit < nbits) {
+                const uint32_t bb = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
+                peers &= ((d >> bit) & 1u) ? bb : ~bb;
+            }
+        }
+        const int leader = __ffs(peers) - 1;
+        uint32_t old = 0;
+        if (lane == leader && d < marker) old = atomicAdd(&wc[d], (uint32_t)__popc(peers));
+        old = __shfl_sync(0xffffffffu, old, leader);
+        rank[j] = old + __popc(peers & lanemask_lt());
+    }
+}
+
 // rec[d][p]: plane p (ranks in super-key-p order) of index array d.
 struct AllPlanes {
     uint32_t* p[MAXK][MAXK];

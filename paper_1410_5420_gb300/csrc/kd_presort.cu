@@ -200,7 +200,10 @@ __global__ void __launch_bounds__(256) k_rs_scan(const int64_t* __restrict__ cou
 
 template <typename KW, int TILE, int SP>
 constexpr size_t rs_move_smem() {
-    return ((size_t)2 * (RADIX + TILE * (sizeof(KW) / 4) + SP * TILE) + (size_t)TILE * (sizeof(KW) / 4)) * 4;
+    // two stages, then the sorted tile: keys, or key + payload pairs for
+    // 32-bit keys with one payload plane
+    const size_t sorted = (sizeof(KW) == 4 && SP == 1) ? (size_t)TILE * 2 : (size_t)TILE * (sizeof(KW) / 4);
+    return ((size_t)2 * (RADIX + TILE * (sizeof(KW) / 4) + SP * TILE) + sorted) * 4;
 }
 
 template <typename KW, int TILE, int SP>
@@ -211,6 +214,7 @@ __global__ void __launch_bounds__(RS_BLOCK, TILE * (SP + 1) * sizeof(KW) <= 2048
     constexpr int IPT = TILE / RS_THREADS;
     constexpr int KWW = sizeof(KW) / 4;
     constexpr int SW = RADIX + TILE * KWW + SP * TILE;  // stage words: offsets row | keys | payloads
+    constexpr bool PAIR = sizeof(KW) == 4 && SP == 1;   // key and payload sorted together
     extern __shared__ __align__(128) uint32_t rsm[];     // [2][SW] stages, then the sorted tile [TILE] keys
     __shared__ __align__(8) uint64_t full[2], empty[2];
     __shared__ SortMeta meta[2];
@@ -335,6 +339,40 @@ __global__ void __launch_bounds__(RS_BLOCK, TILE * (SP + 1) * sizeof(KW) <= 2048
             if (dig[j] < RADIX) slot[j] += s_tstart[dig[j]] + s_wc[warp][dig[j]];
         __syncwarp();
         for (int d = lane; d < RADIX; d += 32) s_wc[warp][d] = 0;  // own row, read above only by this warp
+        if constexpr (PAIR) {
+            if (pay.n == 1) {
+                // 32-bit keys with one payload: both go through the sorted
+                // tile as one 8-byte word
+                const uint32_t* src = pay.src[0];
+                const uint32_t* sp = st + RADIX + TILE * KWW;
+                uint2* sb2 = reinterpret_cast<uint2*>(sb32);
+#pragma unroll
+                for (int j = 0; j < IPT; ++j) {
+                    const int o = wbase + j * 32 + lane;
+                    if (dig[j] < RADIX)
+                        sb2[slot[j]] = make_uint2((uint32_t)skeys[o], src ? sp[o] : (uint32_t)(M.base + o));
+                }
+                consumer_sync<RS_THREADS>();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[s]);  // every read of the stage is behind the barrier
+                uint32_t* dst = pay.dst[0];
+#pragma unroll
+                for (int r = 0; r < IPT; ++r) {
+                    const int i = r * RS_THREADS + tid;
+                    if (i < M.n) {
+                        const uint2 kv = sb2[i];
+                        const uint32_t dd = s_goff[digit_of((KW)kv.x, shift)] + (uint32_t)i;
+                        if ((int64_t)dd < count) {
+                            if (key_dst) key_dst[dd] = (KW)kv.x;
+                            dst[dd] = kv.y;
+                        } else {
+                            atomicOr(err, ERR_INTERNAL);
+                        }
+                    }
+                }
+                continue;
+            }
+        }
 #pragma unroll
         for (int j = 0; j < IPT; ++j)
             if (dig[j] < RADIX) sbuf[slot[j]] = skeys[wbase + j * 32 + lane];

@@ -663,11 +663,11 @@ __device__ __forceinline__ void label_range(int S, int l, int X, int32_t& a, int
 template <int SMAX>
 __device__ __forceinline__ void fin_label_rank(const uint16_t* __restrict__ A, int S, int l,
                                                const uint8_t* __restrict__ lab, uint32_t (*s_wc)[fin_labels(SMAX)],
-                                               int2* s_lab, uint32_t (&lid)[SMAX / FIN_THREADS],
+                                               int2* s_lab,
+                                               uint32_t (&lid)[SMAX / FIN_THREADS],
                                                uint32_t (&dig)[SMAX / FIN_THREADS],
                                                uint32_t (&rank)[SMAX / FIN_THREADS], int* bad) {
     constexpr int IPT = SMAX / FIN_THREADS;
-    constexpr int MAXB = 32 - __builtin_clz((unsigned)fin_labels(SMAX));  // bits of the marker
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t marker = 1u << l;
 #pragma unroll
@@ -677,6 +677,7 @@ __device__ __forceinline__ void fin_label_rank(const uint16_t* __restrict__ A, i
         const uint32_t x = i < S ? lab[lid[j]] : LAB_DONE;
         dig[j] = x == LAB_DONE ? marker : x;
     }
+    constexpr int MAXB = 32 - __builtin_clz((unsigned)fin_labels(SMAX));  // bits of the marker
     warp_rank<IPT, MAXB>(dig, marker, l + 1, s_wc[warp], rank);
     __syncthreads();
     for (int X = tid; X < (int)marker; X += FIN_THREADS) {

@@ -550,6 +550,35 @@ __device__ __forceinline__ void warp_rank(const uint32_t (&dig)[IPT], uint32_t m
     }
 }
 
+// Stable warp ranking through shared-memory match words (digits below
+// `marker`; the marker: no element).  Each lane ORs its bit into its
+// digit's word, reads back the lanes sharing its digit, and the highest of
+// them advances the warp's counter of the digit (wc) and clears the word,
+// so `match` is all zero between calls.
+template <int IPT>
+__device__ __forceinline__ void warp_rank_words(const uint32_t (&dig)[IPT], uint32_t marker, uint32_t* __restrict__ wc,
+                                                uint32_t* __restrict__ match, uint32_t (&rank)[IPT]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+        const uint32_t d = dig[j];
+        if (d < marker) atomicOr(&match[d], 1u << lane);
+        __syncwarp();
+        const uint32_t peers = d < marker ? match[d] : (1u << lane);
+        __syncwarp();
+        const int leader = 31 - __clz(peers);
+        uint32_t old = 0;
+        if (lane == leader && d < marker) {
+            old = wc[d];
+            wc[d] = old + (uint32_t)__popc(peers);
+            match[d] = 0;
+        }
+        __syncwarp();
+        old = __shfl_sync(0xffffffffu, old, leader);
+        rank[j] = old + __popc(peers & lanemask_lt());
+    }
+}
+
 // rec[d][p]: plane p (ranks in super-key-p order) of index array d.
 struct AllPlanes {
     uint32_t* p[MAXK][MAXK];

@@ -286,30 +286,14 @@ __global__ void __launch_bounds__(RS_BLOCK, TILE * (SP + 1) * sizeof(KW) <= 2048
         if (M.t < 0) break;
         const uint32_t* st = rsm + (size_t)s * SW;
         const KW* skeys = reinterpret_cast<const KW*>(st + RADIX);
-        // stable warp ranking: each lane ORs its bit into its digit's mask
-        // word, reads back the lanes sharing its digit, and the highest of
-        // them advances the warp's counter for the digit and clears the word
+        // stable warp ranking through match words
         uint32_t dig[IPT], slot[IPT];
 #pragma unroll
         for (int j = 0; j < IPT; ++j) {
             const int o = wbase + j * 32 + lane;
-            const uint32_t d = o < M.n ? digit_of(skeys[o], shift) : (uint32_t)RADIX;
-            if (d < RADIX) atomicOr(&s_match[warp][d], 1u << lane);
-            __syncwarp();
-            const uint32_t peers = d < RADIX ? s_match[warp][d] : (1u << lane);
-            __syncwarp();
-            const int leader = 31 - __clz(peers);
-            uint32_t old = 0;
-            if (lane == leader && d < RADIX) {
-                old = s_wc[warp][d];
-                s_wc[warp][d] = old + (uint32_t)__popc(peers);
-                s_match[warp][d] = 0;
-            }
-            __syncwarp();
-            old = __shfl_sync(0xffffffffu, old, leader);
-            slot[j] = old + __popc(peers & lanemask_lt());
-            dig[j] = d;
+            dig[j] = o < M.n ? digit_of(skeys[o], shift) : (uint32_t)RADIX;
         }
+        warp_rank_words<IPT>(dig, RADIX, s_wc[warp], s_match[warp], slot);
         consumer_sync<RS_THREADS>();
         // digit tid: prefix over warps in place, tile count, tile start
         uint32_t c = 0;

@@ -25,7 +25,7 @@
 #include "kdtree.h"
 
 namespace kd {
-cudaError_t launch_transform(int dtype, const void* coords, int64_t n, int k, void* keys, int64_t stride,
+cudaError_t launch_transform(int dtype, const void* coords, int64_t n, int k, void* keys, int64_t stride, void* tail,
                              const int64_t* cloud_start, int ncloud, uint32_t* cloud_plane, int cloud_digits,
                              uint32_t* hist, int* err, cudaStream_t s);
 size_t sort_status_words(int64_t max_count);
@@ -36,10 +36,10 @@ cudaError_t launch_digit_bases(const uint32_t* hist, int nrows, uint32_t* bases,
 cudaError_t launch_gather(int key64, const int64_t* count_ptr, int64_t max_count, const void* plane,
                           const uint32_t* ids, void* out, int* err, cudaStream_t s);
 size_t dedup_scratch_words(int64_t n);
-cudaError_t launch_dedup(int key64, int64_t n, const void* key0, const uint32_t* ids, const void* keys,
-                         int64_t stride, int k, const uint32_t* cloud_plane, int cloud_digits, uint32_t* ids_out,
-                         uint32_t* scratch, int64_t* m_out, uint32_t* hist, int32_t* mcloud, int* err,
-                         cudaStream_t s);
+cudaError_t launch_dedup(int key64, int64_t n, const void* key0, const uint32_t* ids, const void* tail, int k,
+                         const uint32_t* cloud_plane, int cloud_digits, uint32_t* ids_out, void* y1, void* y2,
+                         void* y1_out, void* y2_out, uint32_t* scratch, int64_t* m_out, uint32_t* hist,
+                         int32_t* mcloud, int* err, cudaStream_t s);
 cudaError_t launch_own_ranks(const int64_t* m_ptr, int64_t max_m, int k, const AllPlanes& rec, cudaStream_t s);
 cudaError_t launch_perm_bases(const int64_t* m_ptr, int shift, uint32_t* bases, cudaStream_t s);
 cudaError_t launch_perm_scatter(const int64_t* m_ptr, int64_t max_m, const uint32_t* dest, const PayloadArgs& pa,
@@ -408,6 +408,10 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
     // slack, for the 16-byte-aligned bulk copies of the sort passes
     const int64_t NS = pad4(N);
     CKS(S.get(&keys, (size_t)k * NS * w + 16));
+    // tail records: keys x_1..x_{k-1} of each tuple side by side (duplicate
+    // removal reads one record per tuple)
+    unsigned char* tail = nullptr;
+    if (k >= 2) CKS(S.get(&tail, (size_t)N * (k - 1) * w + 16));
     if (count > 1) {
         CKS(S.get(&cloud_plane, (size_t)NS * 4 + 16));
         CKS(S.get(&cstart, (size_t)(count + 1) * 8));
@@ -429,7 +433,8 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
         CK(cudaMemcpyAsync(cstart, H->in_off.data(), (size_t)(count + 1) * 8, cudaMemcpyHostToDevice, s));
     {
         LaunchTimer lt(ctx, F_TRANSFORM, (double)N, nullptr, (double)k * (tsz + w) + (count > 1 ? 4 : 0));
-        CK(launch_transform(dtype, coords, N, k, keys, NS, cstart, count, cloud_plane, cloud_digits, hist, d_err, s));
+        CK(launch_transform(dtype, coords, N, k, keys, NS, tail, cstart, count, cloud_plane, cloud_digits, hist, d_err,
+                            s));
     }
     {
         LaunchTimer lt(ctx, F_OTHER, 0.0);
@@ -515,11 +520,24 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
     }
     // dedup ---------------------------------------------------------------
     uint32_t* dedup_out = count == 1 ? H->perm0 : ibuf[ic ^ 1];
+    // single cloud: duplicate removal also hands the chain x_{k-1} (into the
+    // key buffer the chain's first sort reads) and, for 32-bit keys and
+    // k >= 3, x_{k-2} (carried through that sort for the next one), both in
+    // array-0 order, so neither needs a gather
+    const bool y_first = count == 1 && k >= 2;
+    const bool y_second = y_first && k >= 3 && !key64;
+    unsigned char *y1tmp = nullptr, *y2tmp = nullptr, *y2c = nullptr;
+    if (y_first) CKS(S.get(&y1tmp, (size_t)NS * w + 16));
+    if (y_second) {
+        CKS(S.get(&y2tmp, (size_t)NS * w + 16));
+        CKS(S.get(&y2c, (size_t)NS * w + 16));
+    }
     {
-        LaunchTimer lt(ctx, F_DEDUP, (double)N, nullptr, 2.0 * w + 8);
+        LaunchTimer lt(ctx, F_DEDUP, (double)N, nullptr, 2.0 * w + 8 + (k - 1) * w);
         ctx->launches += 2;  // flags, tile scan, compaction
-        CK(launch_dedup(key64, N, kbuf[kc], ibuf[ic], keys, NS, k, cloud_plane, cloud_digits, dedup_out,
-                        status + status_words, H->d_m, hist, mcloud, d_err, s));
+        CK(launch_dedup(key64, N, kbuf[kc], ibuf[ic], tail, k, cloud_plane, cloud_digits, dedup_out, y1tmp, y2tmp,
+                        y_first ? (void*)kbuf[kc] : nullptr, y2c, status + status_words, H->d_m, hist, mcloud,
+                        d_err, s));
     }
     ic ^= 1;
     {
@@ -551,10 +569,16 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
     // payload plane list: [id (while a later gather needs it)], R_0, R_{k-1}, ..., R_{d+1}
     if (k >= 2) {
         const uint32_t* id_src = H->perm0;  // array 0 order
+        // the first sort's keys come from duplicate removal; the second's are
+        // carried through the first sort (see above)
+        auto gathers = [&](size_t ci, const Pass& P) {
+            return P.mode == KEY_GATHER && !(ci == 0 && y_first) && !(ci == 1 && y_second);
+        };
         int gathers_left = 0;
-        for (auto& v : chain)
-            for (auto& P : v) gathers_left += P.mode == KEY_GATHER;
+        for (size_t ci = 0; ci < chain.size(); ++ci)
+            for (auto& P : chain[ci]) gathers_left += gathers(ci, P);
         std::vector<int> ranks_prev;  // rank planes carried by the previous array (R index list)
+        const void* ysrc = y2c;       // x_{k-2} in the current order while it is carried
         for (size_t ci = 0; ci < chain.size(); ++ci) {
             const int d = k - 1 - (int)ci;
             const auto& v = chain[ci];
@@ -570,7 +594,8 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
             for (size_t i = 0; i < v.size(); ++i) {
                 const Pass& P = v[i];
                 const bool last = i + 1 == v.size();
-                if (P.mode == KEY_GATHER) --gathers_left;
+                const bool gather = gathers(ci, P);
+                if (gather) --gathers_left;
                 const bool carry_id = gathers_left > 0;
                 const bool next_gathers = !last && v[i + 1].mode != KEY_BUF;
                 PayloadArgs pay{};
@@ -587,10 +612,17 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
                     pay.dst[np] = last ? H->rec.p[d][ranks[j]] : pbuf[pb][j];
                     ++np;
                 }
+                // x_{k-2} for the next sort, ending in the key buffer it reads
+                const bool carry_y = ci == 0 && y_second;
+                if (carry_y) {
+                    pay.src[np] = (const uint32_t*)ysrc;
+                    pay.dst[np] = last ? (uint32_t*)kbuf[kc ^ 1] : pbuf[pb][maxpay - 1];
+                    ++np;
+                }
                 pay.n = np;
-                const void* ksrc = P.mode == KEY_BUF ? (const void*)kbuf[kc] : plane_ptr(P.plane);
+                const void* ksrc = P.mode == KEY_BUF || !gather ? (const void*)kbuf[kc] : plane_ptr(P.plane);
                 void* kdst = (last || next_gathers) ? nullptr : (void*)kbuf[kc ^ 1];
-                if (P.mode == KEY_GATHER) {
+                if (gather) {
                     LaunchTimer lg(ctx, F_GATHER, 0.0, H->d_m, 4.0 + 2.0 * P.w);
                     CK(launch_gather(plane64(P.plane), H->d_m, N, plane_ptr(P.plane), cur_id, kbuf[kc], d_err, s));
                     ksrc = kbuf[kc];
@@ -603,6 +635,7 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
                 kc ^= 1;
                 if (carry_id) cur_id = new_id;
                 for (size_t j = 0; j < ranks.size(); ++j) rsrc[j] = last ? H->rec.p[d][ranks[j]] : pbuf[pb][j];
+                if (carry_y) ysrc = pbuf[pb][maxpay - 1];
                 pb ^= 1;
             }
             id_src = cur_id;

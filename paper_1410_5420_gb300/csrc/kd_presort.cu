@@ -35,7 +35,7 @@ namespace kd {
 // histogram rows followed by a 256-point staging tile of coordinates.
 template <typename T, typename KW>
 __global__ void __launch_bounds__(256) k_transform(const T* __restrict__ coords, int64_t n, int k,
-                                                   KW* __restrict__ keys, int64_t stride,
+                                                   KW* __restrict__ keys, int64_t stride, KW* __restrict__ tail,
                                                    const int64_t* __restrict__ cloud_start, int ncloud,
                                                    uint32_t* __restrict__ cloud_plane,
                                                    int cloud_digits, uint32_t* __restrict__ hist,
@@ -58,6 +58,7 @@ __global__ void __launch_bounds__(256) k_transform(const T* __restrict__ coords,
             for (int d = 0; d < k; ++d) {
                 KW key = key_of(sc[tid * k + d], &nan);
                 keys[d * stride + p] = key;
+                if (tail && d > 0) tail[p * (k - 1) + d - 1] = key;
 #pragma unroll
                 for (int b = 0; b < D; ++b)
                     atomicAdd(&sh[(d * D + b) * RADIX + (uint32_t)((key >> (8 * b)) & 255u)], 1u);
@@ -449,57 +450,107 @@ __global__ void k_digit_bases(const uint32_t* __restrict__ hist, uint32_t* __res
 // into tile offsets (and m); k_dedup_compact writes the kept ids in order.
 constexpr int DEDUP_TILE = 4096;
 
+// Duplicate flags over array 0 (sorted by super key 0, equal tuples in index
+// order): a tuple equal to its predecessor goes.  The keys x_1..x_{k-1} of
+// each tuple come from its tail record (one random access per element; the
+// predecessor's record is the neighbour lane's).  The kept tuples' counts
+// leave the digit histograms, and y1 / y2 (if not NULL) receive x_{k-1} and
+// x_{k-2} in array-0 order for the first two sorts of the chain.
 template <typename KW>
 __global__ void __launch_bounds__(256) k_dedup_flags(int64_t n, const KW* __restrict__ key0,
-                                                     const uint32_t* __restrict__ ids, const KW* __restrict__ keys,
-                                                     int64_t stride, int k, const uint32_t* __restrict__ cloud_plane,
-                                                     int cloud_digits, uint32_t* __restrict__ keepbits,
-                                                     uint32_t* __restrict__ tile_cnt, uint32_t* __restrict__ hist,
-                                                     int32_t* __restrict__ mcloud, int* __restrict__ err) {
+                                                     const uint32_t* __restrict__ ids, const KW* __restrict__ tail,
+                                                     int k, const uint32_t* __restrict__ cloud_plane,
+                                                     int cloud_digits, KW* __restrict__ y1, KW* __restrict__ y2,
+                                                     uint32_t* __restrict__ keepbits, uint32_t* __restrict__ tile_cnt,
+                                                     uint32_t* __restrict__ hist, int32_t* __restrict__ mcloud,
+                                                     int* __restrict__ err) {
     constexpr int IPT = DEDUP_TILE / 256;
     constexpr int D = sizeof(KW);
+    constexpr int TM = MAXK - 1;
     __shared__ uint32_t s_wsum[8];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tk = k - 1;
     const int64_t base = (int64_t)blockIdx.x * DEDUP_TILE;
     const int wbase = warp * 32 * IPT;
-    uint32_t wcount = 0;
+    // the predecessor of this warp's first element
+    KW last[TM];
+    KW lastk0 = 0;
+    uint32_t lastid = 0;
 #pragma unroll
+    for (int d = 0; d < TM; ++d) last[d] = 0;
+    {
+        const int64_t p0 = base + wbase;
+        if (p0 > 0 && p0 - 1 < n) {
+            lastid = ids[p0 - 1];
+            if ((int64_t)lastid >= n) {
+                atomicOr(err, ERR_INTERNAL);
+                lastid = 0;
+            }
+            lastk0 = key0[p0 - 1];
+#pragma unroll
+            for (int d = 0; d < TM; ++d)
+                if (d < tk) last[d] = tail[(int64_t)lastid * tk + d];
+        }
+    }
+    uint32_t wcount = 0;
+#pragma unroll 1
     for (int j = 0; j < IPT; ++j) {
         const int64_t pos = base + wbase + j * 32 + lane;
-        bool keep = false;
-        if (pos < n) {
-            uint32_t id = ids[pos];
-            if ((int64_t)id >= n) {
-                atomicOr(err, ERR_INTERNAL);
-                id = 0;
+        const bool valid = pos < n;
+        uint32_t id = valid ? ids[pos] : 0u;
+        if ((int64_t)id >= n) {
+            atomicOr(err, ERR_INTERNAL);
+            id = 0;
+        }
+        const KW k0 = valid ? key0[pos] : (KW)0;
+        KW r[TM];
+#pragma unroll
+        for (int d = 0; d < TM; ++d) r[d] = (valid && d < tk) ? tail[(int64_t)id * tk + d] : (KW)0;
+        KW pk0 = __shfl_up_sync(0xffffffffu, k0, 1);
+        uint32_t pid = __shfl_up_sync(0xffffffffu, id, 1);
+        bool same = true;
+#pragma unroll
+        for (int d = 0; d < TM; ++d) {
+            KW q = __shfl_up_sync(0xffffffffu, r[d], 1);
+            if (lane == 0) q = last[d];
+            same = same && (d >= tk || q == r[d]);
+            last[d] = __shfl_sync(0xffffffffu, r[d], 31);
+        }
+        if (lane == 0) {
+            pk0 = lastk0;
+            pid = lastid;
+        }
+        lastk0 = __shfl_sync(0xffffffffu, k0, 31);
+        lastid = __shfl_sync(0xffffffffu, id, 31);
+        bool dup = valid && pos > 0 && pk0 == k0 && same;
+        if (dup && cloud_plane && cloud_plane[id] != cloud_plane[pid]) dup = false;
+        if (valid && y1) {
+            KW a = 0, b = 0;
+#pragma unroll
+            for (int d = 0; d < TM; ++d) {
+                if (d == tk - 1) a = r[d];
+                if (d == tk - 2) b = r[d];
             }
-            const KW k0 = key0[pos];
-            bool dup = false;
-            if (pos > 0 && key0[pos - 1] == k0 && (int64_t)ids[pos - 1] < n) {
-                const uint32_t pid = ids[pos - 1];
-                dup = true;
-                for (int d = 1; d < k && dup; ++d)
-                    if (keys[d * stride + id] != keys[d * stride + pid]) dup = false;
-                if (dup && cloud_plane && cloud_plane[id] != cloud_plane[pid]) dup = false;
-            }
-            keep = !dup;
-            if (dup) {
-                for (int d = 0; d < k; ++d) {
-                    const KW kd = keys[d * stride + id];
+            y1[pos] = a;
+            if (y2) y2[pos] = b;
+        }
+        if (dup) {
+            for (int b = 0; b < D; ++b) atomicSub(&hist[b * RADIX + (uint32_t)((k0 >> (8 * b)) & 255u)], 1u);
+#pragma unroll
+            for (int d = 0; d < TM; ++d)
+                if (d < tk)
                     for (int b = 0; b < D; ++b)
-                        atomicSub(&hist[(d * D + b) * RADIX + (uint32_t)((kd >> (8 * b)) & 255u)], 1u);
-                }
-                if (cloud_plane) {
-                    const uint32_t c = cloud_plane[id];
-                    for (int b = 0; b < cloud_digits; ++b)
-                        atomicSub(&hist[(k * D + b) * RADIX + ((c >> (8 * b)) & 255u)], 1u);
-                    atomicSub(&mcloud[c], 1);
-                } else if (mcloud) {
-                    atomicSub(&mcloud[0], 1);
-                }
+                        atomicSub(&hist[((d + 1) * D + b) * RADIX + (uint32_t)((r[d] >> (8 * b)) & 255u)], 1u);
+            if (cloud_plane) {
+                const uint32_t c = cloud_plane[id];
+                for (int b = 0; b < cloud_digits; ++b)
+                    atomicSub(&hist[(k * D + b) * RADIX + ((c >> (8 * b)) & 255u)], 1u);
+                atomicSub(&mcloud[c], 1);
+            } else if (mcloud) {
+                atomicSub(&mcloud[0], 1);
             }
         }
-        const uint32_t ball = __ballot_sync(0xffffffffu, keep);
+        const uint32_t ball = __ballot_sync(0xffffffffu, valid && !dup);
         if (lane == 0 && base + wbase + j * 32 < n) keepbits[(base + wbase + j * 32) >> 5] = ball;
         wcount += __popc(ball);
     }
@@ -528,10 +579,13 @@ __global__ void __launch_bounds__(1024) k_tile_scan(int64_t ntiles, const uint32
     if (threadIdx.x == 0) *total_out = carry;
 }
 
+template <typename KW>
 __global__ void __launch_bounds__(256) k_dedup_compact(int64_t n, const uint32_t* __restrict__ ids,
                                                        const uint32_t* __restrict__ keepbits,
                                                        const uint32_t* __restrict__ offs,
-                                                       uint32_t* __restrict__ ids_out) {
+                                                       uint32_t* __restrict__ ids_out, const KW* __restrict__ y1,
+                                                       const KW* __restrict__ y2, KW* __restrict__ y1_out,
+                                                       KW* __restrict__ y2_out) {
     constexpr int IPT = DEDUP_TILE / 256;
     __shared__ uint32_t s_wsum[8];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -552,7 +606,12 @@ __global__ void __launch_bounds__(256) k_dedup_compact(int64_t n, const uint32_t
 #pragma unroll
     for (int j = 0; j < IPT; ++j) {
         const int64_t pos = base + wbase + j * 32 + lane;
-        if ((ball[j] >> lane) & 1u) ids_out[out + __popc(ball[j] & lanemask_lt())] = ids[pos];
+        if ((ball[j] >> lane) & 1u) {
+            const uint32_t o = out + __popc(ball[j] & lanemask_lt());
+            ids_out[o] = ids[pos];
+            if (y1_out) y1_out[o] = y1[pos];
+            if (y2_out) y2_out[o] = y2[pos];
+        }
         out += __popc(ball[j]);
     }
 }
@@ -638,7 +697,7 @@ static int grid_for(int64_t work, int per_block, int cap) {
 // 64-bit keys plus 2 cloud-id digit rows, and the 256-point coordinate tile.
 constexpr size_t TRANSFORM_SMEM_MAX = (size_t)(MAXK * 8 + 4) * RADIX * 4 + 256 * MAXK * 8;
 
-cudaError_t launch_transform(int dtype, const void* coords, int64_t n, int k, void* keys, int64_t stride,
+cudaError_t launch_transform(int dtype, const void* coords, int64_t n, int k, void* keys, int64_t stride, void* tail,
                              const int64_t* cloud_start, int ncloud, uint32_t* cloud_plane,
                              int cloud_digits, uint32_t* hist, int* err, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
@@ -649,13 +708,13 @@ cudaError_t launch_transform(int dtype, const void* coords, int64_t n, int k, vo
     const int grid = grid_for(n, 256, 152 * 8);
     if (dtype == 0)
         k_transform<int32_t, uint32_t><<<grid, 256, smem, s>>>((const int32_t*)coords, n, k, (uint32_t*)keys, stride,
-                                                              cloud_start, ncloud, cloud_plane, cloud_digits, hist, err);
+                                                              (uint32_t*)tail, cloud_start, ncloud, cloud_plane, cloud_digits, hist, err);
     else if (dtype == 1)
         k_transform<int64_t, uint64_t><<<grid, 256, smem, s>>>((const int64_t*)coords, n, k, (uint64_t*)keys, stride,
-                                                              cloud_start, ncloud, cloud_plane, cloud_digits, hist, err);
+                                                              (uint64_t*)tail, cloud_start, ncloud, cloud_plane, cloud_digits, hist, err);
     else
         k_transform<float, uint32_t><<<grid, 256, smem, s>>>((const float*)coords, n, k, (uint32_t*)keys, stride,
-                                                            cloud_start, ncloud, cloud_plane, cloud_digits, hist, err);
+                                                            (uint32_t*)tail, cloud_start, ncloud, cloud_plane, cloud_digits, hist, err);
     return cudaGetLastError();
 }
 
@@ -785,25 +844,28 @@ size_t dedup_scratch_words(int64_t n) {
     return (size_t)((n + 31) / 32) + 2 * (size_t)tiles + 4;
 }
 
-cudaError_t launch_dedup(int key64, int64_t n, const void* key0, const uint32_t* ids, const void* keys,
-                         int64_t stride, int k, const uint32_t* cloud_plane, int cloud_digits, uint32_t* ids_out,
-                         uint32_t* scratch, int64_t* m_out, uint32_t* hist, int32_t* mcloud, int* err,
-                         cudaStream_t s) {
+cudaError_t launch_dedup(int key64, int64_t n, const void* key0, const uint32_t* ids, const void* tail, int k,
+                         const uint32_t* cloud_plane, int cloud_digits, uint32_t* ids_out, void* y1, void* y2,
+                         void* y1_out, void* y2_out, uint32_t* scratch, int64_t* m_out, uint32_t* hist,
+                         int32_t* mcloud, int* err, cudaStream_t s) {
     const int64_t tiles = (n + DEDUP_TILE - 1) / DEDUP_TILE;
     if (tiles == 0) return cudaSuccess;
     uint32_t* keepbits = scratch;
     uint32_t* tcnt = keepbits + (n + 31) / 32;
     uint32_t* toff = tcnt + tiles;
-    if (key64)
-        k_dedup_flags<uint64_t><<<(unsigned)tiles, 256, 0, s>>>(n, (const uint64_t*)key0, ids, (const uint64_t*)keys,
-                                                               stride, k, cloud_plane, cloud_digits, keepbits, tcnt,
-                                                               hist, mcloud, err);
-    else
-        k_dedup_flags<uint32_t><<<(unsigned)tiles, 256, 0, s>>>(n, (const uint32_t*)key0, ids, (const uint32_t*)keys,
-                                                               stride, k, cloud_plane, cloud_digits, keepbits, tcnt,
-                                                               hist, mcloud, err);
-    k_tile_scan<<<1, 1024, 0, s>>>(tiles, tcnt, toff, m_out);
-    k_dedup_compact<<<(unsigned)tiles, 256, 0, s>>>(n, ids, keepbits, toff, ids_out);
+#define KD_DEDUP(KW)                                                                                          \
+    k_dedup_flags<KW><<<(unsigned)tiles, 256, 0, s>>>(n, (const KW*)key0, ids, (const KW*)tail, k, cloud_plane, \
+                                                      cloud_digits, (KW*)y1, (KW*)y2, keepbits, tcnt, hist,   \
+                                                      mcloud, err);                                           \
+    k_tile_scan<<<1, 1024, 0, s>>>(tiles, tcnt, toff, m_out);                                                 \
+    k_dedup_compact<KW><<<(unsigned)tiles, 256, 0, s>>>(n, ids, keepbits, toff, ids_out, (const KW*)y1,       \
+                                                        (const KW*)y2, (KW*)y1_out, (KW*)y2_out);
+    if (key64) {
+        KD_DEDUP(uint64_t)
+    } else {
+        KD_DEDUP(uint32_t)
+    }
+#undef KD_DEDUP
     return cudaGetLastError();
 }
 

@@ -376,57 +376,77 @@ __global__ void __launch_bounds__(LEVEL_BLOCK)
 
 // Segmented inclusive scan over the tiles of a level step, one block per
 // bucket: incl[t][b] = cnt[t][b] + (head[t] ? 0 : incl[t-1][b]) (row stride
-// `stride`).
+// `stride`).  Each thread scans LS_V consecutive tiles, then the threads'
+// aggregates are scanned across the block; a chunk of 1024 * LS_V tiles per
+// iteration, carried into the next.
+constexpr int LS_V = 8;
 __global__ void __launch_bounds__(1024) k_level_scan(int ntiles, int stride, const uint32_t* __restrict__ cnt,
                                                      const uint32_t* __restrict__ head, uint32_t* __restrict__ incl) {
     __shared__ uint32_t s_f[32], s_v[32];
     const int b = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint32_t carry = 0;
-    for (int t0 = 0; t0 < ntiles; t0 += 1024) {
-        const int t = t0 + tid;
-        uint32_t f = t < ntiles ? head[t] : 1u;
-        uint32_t v = t < ntiles ? cnt[(int64_t)t * stride + b] : 0u;
+    for (int t0 = 0; t0 < ntiles; t0 += 1024 * LS_V) {
+        const int tb = t0 + tid * LS_V;
+        uint32_t lf[LS_V], lv[LS_V];
+#pragma unroll
+        for (int e = 0; e < LS_V; ++e) {
+            const int t = tb + e;
+            lf[e] = t < ntiles ? head[t] : 1u;
+            lv[e] = t < ntiles ? cnt[(int64_t)t * stride + b] : 0u;
+        }
+        // inclusive within the thread: a head starts a new segment
+#pragma unroll
+        for (int e = 1; e < LS_V; ++e) {
+            if (!lf[e]) lv[e] += lv[e - 1];
+            lf[e] |= lf[e - 1];
+        }
+        // (flag, value) pairs of the threads: inclusive scan within the warp
+        uint32_t xf = lf[LS_V - 1], xv = lv[LS_V - 1];
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t f2 = __shfl_up_sync(0xffffffffu, f, o);
-            const uint32_t v2 = __shfl_up_sync(0xffffffffu, v, o);
+            const uint32_t yf = __shfl_up_sync(0xffffffffu, xf, o);
+            const uint32_t yv = __shfl_up_sync(0xffffffffu, xv, o);
             if (lane >= o) {
-                if (!f) v += v2;
-                f |= f2;
+                if (!xf) xv += yv;
+                xf |= yf;
             }
         }
+        uint32_t ef = __shfl_up_sync(0xffffffffu, xf, 1), ev = __shfl_up_sync(0xffffffffu, xv, 1);
+        if (lane == 0) {
+            ef = 0;
+            ev = 0;
+        }
         if (lane == 31) {
-            s_f[warp] = f;
-            s_v[warp] = v;
+            s_f[warp] = xf;
+            s_v[warp] = xv;
         }
         __syncthreads();
         if (warp == 0) {
             uint32_t wf = s_f[lane], wv = s_v[lane];
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t f2 = __shfl_up_sync(0xffffffffu, wf, o);
-                const uint32_t v2 = __shfl_up_sync(0xffffffffu, wv, o);
+                const uint32_t yf = __shfl_up_sync(0xffffffffu, wf, o);
+                const uint32_t yv = __shfl_up_sync(0xffffffffu, wv, o);
                 if (lane >= o) {
-                    if (!wf) wv += v2;
-                    wf |= f2;
+                    if (!wf) wv += yv;
+                    wf |= yf;
                 }
             }
             s_f[lane] = wf;
             s_v[lane] = wv;
         }
         __syncthreads();
-        // prefix of earlier warps in this chunk, then the chunk carry
-        uint32_t pf = 0, pv = 0;
-        if (warp > 0) {
-            pf = s_f[warp - 1];
-            pv = s_v[warp - 1];
+        // everything before this thread: earlier chunks, earlier warps, earlier lanes
+        uint32_t pv = carry;
+        if (warp > 0) pv = s_f[warp - 1] ? s_v[warp - 1] : carry + s_v[warp - 1];
+        const uint32_t xv0 = ef ? ev : pv + ev;
+#pragma unroll
+        for (int e = 0; e < LS_V; ++e) {
+            const int t = tb + e;
+            if (t < ntiles) incl[(int64_t)t * stride + b] = lf[e] ? lv[e] : xv0 + lv[e];
         }
-        if (!pf) pv += carry;
-        if (!f) v += pv;
-        if (t < ntiles) incl[(int64_t)t * stride + b] = v;
-        const uint32_t lastf = s_f[31], lastv = s_v[31];
-        carry = lastf ? lastv : carry + lastv;
+        carry = s_f[31] ? s_v[31] : carry + s_v[31];
         __syncthreads();
     }
 }

@@ -18,6 +18,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "kd_oracle.c")
+_SRC_SEARCH = os.path.join(_HERE, "kd_search_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "libkd_oracle.so")
 
@@ -31,10 +32,13 @@ def build(force: bool = False, mutant: int = 0, out: str | None = None) -> str:
     kd_oracle.c (only the mutation tests do this)."""
     os.makedirs(_BUILD, exist_ok=True)
     lib = out or (_LIB if mutant == 0 else os.path.join(_BUILD, f"libkd_oracle_mutant{mutant}.so"))
-    if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_SEARCH))
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < newest:
         tmp = lib + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", f"-DKDO_MUTANT={int(mutant)}",
-                               "-shared", "-fPIC", _SRC, "-o", tmp])
+        # -ffp-contract=off: every floating-point operation of the search
+        # distances is rounded separately, as their definition states
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", f"-DKDO_MUTANT={int(mutant)}",
+                               "-shared", "-fPIC", _SRC, _SRC_SEARCH, "-o", tmp])
         os.replace(tmp, lib)
     return lib
 
@@ -54,6 +58,12 @@ def _load(mutant: int = 0):
                                         ctypes.POINTER(ctypes.c_int32)]
         for f in (lib.kdo_presort, lib.kdo_build, lib.kdo_first_split):
             f.restype = ctypes.c_int
+        lib.kdo_knn.argtypes = [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int64, vp,
+                                ctypes.c_int64, ctypes.c_int, vp, vp]
+        lib.kdo_knn.restype = ctypes.c_int
+        lib.kdo_region.argtypes = [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int64, vp, vp,
+                                   ctypes.c_int64, vp, vp, ctypes.c_int64]
+        lib.kdo_region.restype = ctypes.c_int64
         _libs[mutant] = lib
     return _libs[mutant]
 
@@ -117,3 +127,47 @@ def first_split(coords: np.ndarray, mutant: int = 0):
     if rc != 0:
         raise OracleError(rc)
     return out[:, : m.value].copy(), med.value
+
+
+def knn(coords: np.ndarray, queries: np.ndarray, kn: int, cand: np.ndarray | None = None):
+    """m nearest neighbours (squared Euclidean, ties by smaller index) of each
+    query among the distinct tuples (``cand``, default: the presort's
+    survivors).  Returns (idx nq x kn int32, dist2 nq x kn float64)."""
+    c, n, k, dt = _prep(coords)
+    q = np.ascontiguousarray(queries, dtype=c.dtype)
+    if q.ndim != 2 or q.shape[1] != k:
+        raise ValueError("queries must be nq x k")
+    if cand is None:
+        cand = presort(c)[0] if n else np.empty(0, np.int32)
+    cand = np.ascontiguousarray(cand, dtype=np.int32)
+    nq = q.shape[0]
+    idx = np.empty((max(nq, 1), kn), dtype=np.int32)
+    d2 = np.empty((max(nq, 1), kn), dtype=np.float64)
+    rc = _load().kdo_knn(c.ctypes.data, n, k, dt, cand.ctypes.data, cand.size, q.ctypes.data, nq, kn,
+                         idx.ctypes.data, d2.ctypes.data)
+    if rc != 0:
+        raise OracleError(rc)
+    return idx[:nq], d2[:nq]
+
+
+def region(coords: np.ndarray, lo: np.ndarray, hi: np.ndarray, cand: np.ndarray | None = None) -> list:
+    """For each box [lo[i], hi[i]] the sorted indices of the distinct tuples inside it."""
+    c, n, k, dt = _prep(coords)
+    lo = np.ascontiguousarray(lo, dtype=c.dtype)
+    hi = np.ascontiguousarray(hi, dtype=c.dtype)
+    if cand is None:
+        cand = presort(c)[0] if n else np.empty(0, np.int32)
+    cand = np.ascontiguousarray(cand, dtype=np.int32)
+    nq = lo.shape[0]
+    counts = np.empty(max(nq, 1), dtype=np.int64)
+    cap = max(1, nq * max(cand.size, 1))
+    out = np.empty(cap, dtype=np.int32)
+    tot = _load().kdo_region(c.ctypes.data, n, k, dt, cand.ctypes.data, cand.size, lo.ctypes.data, hi.ctypes.data,
+                             nq, counts.ctypes.data, out.ctypes.data, cap)
+    if tot < 0:
+        raise OracleError(int(tot))
+    res, o = [], 0
+    for i in range(nq):
+        res.append(np.sort(out[o:o + counts[i]]))
+        o += counts[i]
+    return res

@@ -197,6 +197,49 @@ const char *kd_last_error(kd_ctx *ctx);
 #define KD_NOALLOC_MAX_N 16384
 kd_status kd_presort_noalloc(kd_ctx *ctx, const kd_cloud *cloud, int32_t *arrays_out, int32_t *m_out);
 
+/*
+ * Searches over a built tree ("Nearest Neighbors" subsection of the paper,
+ * and the hyper-rectangular region search of its source-code subsection).
+ *
+ * kd_index_create: a search index for tree `tree` built from `cloud` (the
+ * same coordinates, host or device; the tree's node_tuple array host or
+ * device).  The index keeps the tuples in the tree's address order on the
+ * device (m x k coordinates and m tuple indices), allocated from the
+ * context; destroy it with kd_index_destroy before destroying the context.
+ */
+typedef struct kd_index_s *kd_index;
+kd_status kd_index_create(kd_ctx *ctx, const kd_cloud *cloud, const kd_tree *tree, kd_index *out);
+kd_status kd_index_destroy(kd_ctx *ctx, kd_index index);
+
+/*
+ * kd_knn: for each of nq query points (row-major nq x k, the index's dtype),
+ * its kn nearest tuples (1 <= kn <= KD_KNN_MAX) by squared Euclidean
+ * distance, nearest first, equal distances by the smaller tuple index.
+ * Distances are exact per dimension (integers: |a - b| as an unsigned
+ * 64-bit value, rounded to double; floats: the double difference), squared
+ * and summed in double in dimension order without fused multiply-add.
+ * idx_out: nq x kn tuple indices (-1 past the tree's m tuples); dist_out
+ * (optional): nq x kn squared distances (+inf past m).  on_device: queries
+ * and outputs are device pointers.  A NaN query coordinate gives KD_ENAN.
+ * Synchronises the stream.
+ */
+#define KD_KNN_MAX 32
+kd_status kd_knn(kd_ctx *ctx, kd_index index, const void *queries, int64_t nq, int kn, int on_device,
+                 int32_t *idx_out, double *dist_out);
+
+/*
+ * kd_region: for each of nq boxes [lo[i], hi[i]] (row-major nq x k,
+ * inclusive in every dimension), the indices of the tuples inside it.
+ * offsets (nq + 1 int64) receives the exclusive prefix of the per-box
+ * counts; box i's indices are idx_out[offsets[i] .. offsets[i+1]) in the
+ * order the walk meets them.  idx_out may be NULL (counts only); a
+ * capacity below the total gives KD_EINVAL (offsets are still written).
+ * on_device: boxes, offsets and idx_out are device pointers.  Synchronises
+ * the stream.
+ */
+kd_status kd_region(kd_ctx *ctx, kd_index index, const void *lo, const void *hi, int64_t nq, int on_device,
+                    int64_t *offsets, int32_t *idx_out, int64_t capacity);
+
 /* Kernels launched by this context since creation (instrumentation). */
 int64_t kd_launch_count(kd_ctx *ctx);
 

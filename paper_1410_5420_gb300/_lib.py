@@ -16,6 +16,7 @@ KD_I32, KD_I64, KD_F32 = 0, 1, 2
 KD_MAX_K = 8
 KD_MAX_N = (1 << 30) - 1
 KD_NOALLOC_MAX_N = 16384
+KD_KNN_MAX = 32
 STATUS_NAMES = {0: "KD_OK", -1: "KD_EINVAL", -2: "KD_ENOMEM", -3: "KD_EDEVICE", -4: "KD_ETIMEOUT",
                 -5: "KD_EBUSY", -6: "KD_ENAN"}
 
@@ -25,7 +26,7 @@ FAMILIES = ["transform", "sort_pass", "dedup", "records", "level_pass", "finish"
 EXPORTS = ["kd_create", "kd_presort", "kd_handle_info", "kd_handle_arrays", "kd_build", "kd_release",
            "kd_build_batch", "kd_submit", "kd_wait", "kd_serving_stats", "kd_destroy", "kd_last_error",
            "kd_launch_count", "kd_kernel_stats", "kd_kernel_stats_reset", "kd_trace_counters",
-           "kd_presort_noalloc"]
+           "kd_presort_noalloc", "kd_index_create", "kd_index_destroy", "kd_knn", "kd_region"]
 
 
 class KdConfig(ctypes.Structure):
@@ -78,6 +79,10 @@ def load():
         "kd_kernel_stats_reset": ([vp], ctypes.c_int),
         "kd_trace_counters": ([vp, P(ctypes.c_double), ctypes.c_int], ctypes.c_int),
         "kd_presort_noalloc": ([vp, P(KdCloud), vp, vp], ctypes.c_int),
+        "kd_index_create": ([vp, P(KdCloud), P(KdTree), P(vp)], ctypes.c_int),
+        "kd_index_destroy": ([vp, vp], ctypes.c_int),
+        "kd_knn": ([vp, vp, vp, i64, ctypes.c_int, ctypes.c_int, vp, vp], ctypes.c_int),
+        "kd_region": ([vp, vp, vp, vp, i64, ctypes.c_int, vp, vp, i64], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)

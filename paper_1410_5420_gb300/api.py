@@ -232,6 +232,102 @@ def kd_presort_noalloc(ctx: Context, coords, arrays_out=None, m_out=None):
     return arrays_out, m_out
 
 
+class Index:
+    """A kd_index: the tree's tuples in address order on the device."""
+
+    def __init__(self, ptr: int, k: int, dtype):
+        self.ptr = ctypes.c_void_p(ptr)
+        self.k = k
+        self.dtype = dtype
+
+
+def kd_index_create(ctx: Context, coords, tree: dict) -> Index:
+    """kd_index_create for a tree (as returned by kd_build / build_tree)
+    built from ``coords``."""
+    c, keep = _cloud(coords)
+    nt = tree["node_tuple"]
+    on_dev = bool(torch is not None and isinstance(nt, torch.Tensor) and nt.is_cuda)
+    if on_dev:
+        nt = nt.contiguous()
+        ptr = nt.data_ptr()
+    else:
+        nt = np.ascontiguousarray(nt if not hasattr(nt, "numpy") else nt.numpy(), dtype=np.int32)
+        ptr = nt.ctypes.data
+    t = KdTree(int(tree["m"]), -1, ctypes.c_void_p(ptr), None, None, None, int(on_dev))
+    out = ctypes.c_void_p()
+    ctx.check(_lib.load().kd_index_create(ctx.ptr, ctypes.byref(c), ctypes.byref(t), ctypes.byref(out)))
+    del keep, nt
+    dt = coords.dtype if hasattr(coords, "dtype") else None
+    return Index(out.value, c.k, dt)
+
+
+def kd_index_destroy(ctx: Context, index: Index) -> None:
+    if index.ptr:
+        ctx.check(_lib.load().kd_index_destroy(ctx.ptr, index.ptr))
+        index.ptr = ctypes.c_void_p(0)
+
+
+def _rows(x, k):
+    """(pointer, keep-alive, on_device, n) of an n x k query array."""
+    if torch is not None and isinstance(x, torch.Tensor):
+        t = x.contiguous()
+        if t.dim() != 2 or t.shape[1] != k:
+            raise ValueError("queries must be n x k")
+        return t.data_ptr(), t, bool(t.is_cuda), t.shape[0]
+    a = np.ascontiguousarray(x)
+    if a.ndim != 2 or a.shape[1] != k:
+        raise ValueError("queries must be n x k")
+    return a.ctypes.data, a, False, a.shape[0]
+
+
+def kd_knn(ctx: Context, index: Index, queries, kn: int, with_dist: bool = True):
+    """kd_knn: (idx nq x kn int32, dist2 nq x kn float64 or None); device
+    tensors when the queries are a CUDA tensor, numpy arrays otherwise."""
+    qp, keep, dev, nq = _rows(queries, index.k)
+    if dev:
+        idx = torch.empty((nq, kn), dtype=torch.int32, device=queries.device)
+        d2 = torch.empty((nq, kn), dtype=torch.float64, device=queries.device) if with_dist else None
+        ip, dp = idx.data_ptr(), (d2.data_ptr() if with_dist else None)
+    else:
+        idx = np.empty((nq, kn), dtype=np.int32)
+        d2 = np.empty((nq, kn), dtype=np.float64) if with_dist else None
+        ip, dp = idx.ctypes.data, (d2.ctypes.data if with_dist else None)
+    ctx.check(_lib.load().kd_knn(ctx.ptr, index.ptr, ctypes.c_void_p(qp), nq, kn, int(dev), ctypes.c_void_p(ip),
+                                 ctypes.c_void_p(dp) if dp else None))
+    del keep
+    return idx, d2
+
+
+def kd_region(ctx: Context, index: Index, lo, hi):
+    """kd_region: (offsets nq+1 int64, idx int32) with box i's tuples at
+    idx[offsets[i]:offsets[i+1]]; device tensors for CUDA boxes."""
+    lp, keep_lo, dev, nq = _rows(lo, index.k)
+    hp, keep_hi, dev2, nq2 = _rows(hi, index.k)
+    if dev != dev2 or nq != nq2:
+        raise ValueError("lo and hi must match")
+    lib = _lib.load()
+    if dev:
+        offs = torch.empty(nq + 1, dtype=torch.int64, device=lo.device)
+        op = offs.data_ptr()
+    else:
+        offs = np.empty(nq + 1, dtype=np.int64)
+        op = offs.ctypes.data
+    ctx.check(lib.kd_region(ctx.ptr, index.ptr, ctypes.c_void_p(lp), ctypes.c_void_p(hp), nq, int(dev),
+                            ctypes.c_void_p(op), None, 0))
+    total = int(offs[-1].item() if dev else offs[-1])
+    if dev:
+        idx = torch.empty(max(total, 1), dtype=torch.int32, device=lo.device)
+        ipt = idx.data_ptr()
+    else:
+        idx = np.empty(max(total, 1), dtype=np.int32)
+        ipt = idx.ctypes.data
+    if total:
+        ctx.check(lib.kd_region(ctx.ptr, index.ptr, ctypes.c_void_p(lp), ctypes.c_void_p(hp), nq, int(dev),
+                                ctypes.c_void_p(op), ctypes.c_void_p(ipt), total))
+    del keep_lo, keep_hi
+    return offs, idx[:total]
+
+
 def kd_launch_count(ctx: Context) -> int:
     return int(_lib.load().kd_launch_count(ctx.ptr))
 

@@ -1072,12 +1072,15 @@ kd_status start_serving(kd_ctx* ctx) {
 
 }  // namespace
 
-// Context access for the entry point in kd_noalloc.cu.
+// Context access for the entry points in kd_noalloc.cu and kd_search.cu.
 namespace kd {
 int ctx_device(const kd_ctx* ctx) { return ctx->device; }
 cudaStream_t ctx_stream(const kd_ctx* ctx) { return ctx->stream; }
 void ctx_set_error(kd_ctx* ctx, const std::string& msg) { ctx->last_error = msg; }
 void ctx_add_launches(kd_ctx* ctx, int n) { ctx->launches += n; }
+kd_status ctx_alloc(kd_ctx* ctx, void** p, size_t bytes) { return dev_alloc(ctx, p, bytes); }
+void ctx_free(kd_ctx* ctx, void* p) { dev_free(ctx, p); }
+std::recursive_mutex& ctx_mutex(kd_ctx* ctx) { return ctx->mu; }
 }  // namespace kd
 
 // =================================================================== C ABI

@@ -54,10 +54,10 @@ def parse():
                     help="cpu_baseline: oracle sample size in points (2^24: about 15 s of one core)")
     ap.add_argument("--ref-sample", type=int, default=1 << 21,
                     help="--impl reference: oracle sample per step in points (about 2 s of one core)")
-    ap.add_argument("--mode", default="plain", choices=["plain", "batched", "served", "sweep"],
+    ap.add_argument("--mode", default="plain", choices=["plain", "batched", "served", "sweep", "knn"],
                     help="plain: the 2^26 build (default line); batched: 4096 uneven clouds in one call "
                          "vs per-cloud calls; served: a Poisson request stream through kd_submit; "
-                         "sweep: n=2^22 at k=2..6")
+                         "sweep: n=2^22 at k=2..6; knn: searches over a 2^22-tuple tree")
     ap.add_argument("--clouds", type=int, default=4096)
     ap.add_argument("--requests", type=int, default=2000)
     return ap.parse_args()
@@ -292,6 +292,68 @@ def run_sweep(args):
     print(json.dumps(line), flush=True)
 
 
+def run_knn(args):
+    """Searches over a built tree, on the workload of the paper's Nearest
+    Neighbors measurement: n = 2^22 (x, y, z) tuples of int64 uniform in
+    [0, 2^40); the kn = 8 nearest neighbours of every tuple (all points),
+    the reverse nearest neighbours, and 2^20 region searches.  The CPU
+    baseline is the brute-force oracle on a sample of queries."""
+    import torch
+    import kdgen
+    from paper_1410_5420_gb300 import api
+    n = min(args.n, 1 << 22)
+    kn = 8
+    coords = kdgen.cloud_int_uniform(n, 3, 40, 6, np.int64)
+    x = torch.from_numpy(coords).cuda()
+    stream = torch.cuda.current_stream()
+    ctx = api.kd_create(0, stream=stream)
+    tree = api.build_tree(ctx, x, on_device=True)
+    m = tree["m"]
+    ix = api.kd_index_create(ctx, x, tree)
+    rng = np.random.default_rng(7)
+    centres = coords[rng.integers(0, n, 1 << 20)]
+    half = rng.integers(0, 1 << 33, centres.shape)  # boxes that hold a few tuples each
+    lo = torch.from_numpy(centres - half).cuda()
+    hi = torch.from_numpy(centres + half).cuda()
+
+    def timed(fn, reps):
+        for _ in range(max(1, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, r
+
+    ms_all, (idx, _) = timed(lambda: api.kd_knn_all(ctx, ix, m, kn, with_dist=False), args.steps)
+    ms_rev, _ = timed(lambda: api.kd_reverse_knn(ctx, ix, m, kn), args.steps)
+    ms_reg, (offs, _) = timed(lambda: api.kd_region(ctx, ix, lo, hi), args.steps)
+    found = int(offs[-1].item())
+    # CPU baseline: brute force over all tuples for a sample of queries
+    import oracle
+    sample = 32
+    cand = np.arange(n, dtype=np.int32)
+    t0 = time.perf_counter()
+    oracle.knn(coords, coords[:sample], kn + 1, cand)
+    cpu_qps = sample / (time.perf_counter() - t0)
+    line = {"metric": METRIC, "mode": "knn", "value": m / (ms_all / 1000.0), "unit": "queries/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_all, "higher_is_better": True,
+            "dtype": "i64", "data": "synthetic",
+            "config": {"workload": f"all-points {kn} nearest neighbours: n={n} (x,y,z) int64 uniform in [0, 2^40) "
+                                   f"(seed 6)", "m": m, "kn": kn},
+            "reverse_knn": {"ms": ms_rev, "points_per_s": m / (ms_rev / 1000.0)},
+            "region": {"boxes": int(lo.shape[0]), "ms": ms_reg, "boxes_per_s": lo.shape[0] / (ms_reg / 1000.0),
+                       "tuples_found": found},
+            "cpu_baseline": {"value": cpu_qps, "unit": "queries/s", "cores": 1, "kind": "oracle (brute force)",
+                             "sample": f"{sample} queries against all {n} tuples"}}
+    print(json.dumps(line), flush=True)
+    api.kd_index_destroy(ctx, ix)
+    ctx.close()
+
+
 def run_served(args):
     """Poisson stream of build requests through kd_submit / kd_wait: sizes
     log-uniform in [2^8, 2^20], k in {2,3,4}, int32 or float32 mixture
@@ -350,7 +412,7 @@ def main():
     rank, world, local = dist_env()
     if args.mode != "plain" and args.impl == "gb300":
         if rank == 0:
-            {"batched": run_batched, "served": run_served, "sweep": run_sweep}[args.mode](args)
+            {"batched": run_batched, "served": run_served, "sweep": run_sweep, "knn": run_knn}[args.mode](args)
         return
     if world > 1:
         import torch.distributed as dist

@@ -228,6 +228,25 @@ kd_status kd_knn(kd_ctx *ctx, kd_index index, const void *queries, int64_t nq, i
                  int32_t *idx_out, double *dist_out);
 
 /*
+ * kd_knn_all: the kn nearest neighbours of every tuple of the tree among
+ * the others (its own tuple excluded), as the first step of the paper's
+ * reverse-nearest-neighbours search.  Row a of idx_out (m x kn) belongs to
+ * the tuple at tree address a (node_tuple[a]); ordering and distances as
+ * kd_knn.  on_device: outputs are device pointers.
+ */
+kd_status kd_knn_all(kd_ctx *ctx, kd_index index, int kn, int on_device, int32_t *idx_out, double *dist_out);
+
+/*
+ * kd_reverse_knn: the reverse nearest neighbours of every tuple of the
+ * tree: for the tuple at address a, the tuples whose kn nearest neighbours
+ * (kd_knn_all) include it.  offsets (m + 1 int64) is the exclusive prefix
+ * of the list lengths; the tuple indices of list a are
+ * rev_out[offsets[a] .. offsets[a+1]), in no particular order (rev_out
+ * needs m * kn entries).  on_device: outputs are device pointers.
+ */
+kd_status kd_reverse_knn(kd_ctx *ctx, kd_index index, int kn, int on_device, int64_t *offsets, int32_t *rev_out);
+
+/*
  * kd_region: for each of nq boxes [lo[i], hi[i]] (row-major nq x k,
  * inclusive in every dimension), the indices of the tuples inside it.
  * offsets (nq + 1 int64) receives the exclusive prefix of the per-box

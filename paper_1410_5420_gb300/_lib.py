@@ -26,7 +26,8 @@ FAMILIES = ["transform", "sort_pass", "dedup", "records", "level_pass", "finish"
 EXPORTS = ["kd_create", "kd_presort", "kd_handle_info", "kd_handle_arrays", "kd_build", "kd_release",
            "kd_build_batch", "kd_submit", "kd_wait", "kd_serving_stats", "kd_destroy", "kd_last_error",
            "kd_launch_count", "kd_kernel_stats", "kd_kernel_stats_reset", "kd_trace_counters",
-           "kd_presort_noalloc", "kd_index_create", "kd_index_destroy", "kd_knn", "kd_region"]
+           "kd_presort_noalloc", "kd_index_create", "kd_index_destroy", "kd_knn", "kd_region",
+           "kd_knn_all", "kd_reverse_knn"]
 
 
 class KdConfig(ctypes.Structure):
@@ -83,6 +84,8 @@ def load():
         "kd_index_destroy": ([vp, vp], ctypes.c_int),
         "kd_knn": ([vp, vp, vp, i64, ctypes.c_int, ctypes.c_int, vp, vp], ctypes.c_int),
         "kd_region": ([vp, vp, vp, vp, i64, ctypes.c_int, vp, vp, i64], ctypes.c_int),
+        "kd_knn_all": ([vp, vp, ctypes.c_int, ctypes.c_int, vp, vp], ctypes.c_int),
+        "kd_reverse_knn": ([vp, vp, ctypes.c_int, ctypes.c_int, vp, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)

@@ -298,6 +298,38 @@ def kd_knn(ctx: Context, index: Index, queries, kn: int, with_dist: bool = True)
     return idx, d2
 
 
+def kd_knn_all(ctx: Context, index: Index, m: int, kn: int, on_device: bool = True, with_dist: bool = True):
+    """kd_knn_all: (idx m x kn, dist2 m x kn or None), row a for the tuple at
+    tree address a; ``m`` is the tree's tuple count."""
+    if on_device:
+        idx = torch.empty((m, kn), dtype=torch.int32, device="cuda")
+        d2 = torch.empty((m, kn), dtype=torch.float64, device="cuda") if with_dist else None
+        ip, dp = idx.data_ptr(), (d2.data_ptr() if with_dist else None)
+    else:
+        idx = np.empty((m, kn), dtype=np.int32)
+        d2 = np.empty((m, kn), dtype=np.float64) if with_dist else None
+        ip, dp = idx.ctypes.data, (d2.ctypes.data if with_dist else None)
+    ctx.check(_lib.load().kd_knn_all(ctx.ptr, index.ptr, kn, int(on_device), ctypes.c_void_p(ip),
+                                     ctypes.c_void_p(dp) if dp else None))
+    return idx, d2
+
+
+def kd_reverse_knn(ctx: Context, index: Index, m: int, kn: int, on_device: bool = True):
+    """kd_reverse_knn: (offsets m+1 int64, rev int32) with the reverse
+    neighbours of the tuple at address a in rev[offsets[a]:offsets[a+1]]."""
+    if on_device:
+        offs = torch.empty(m + 1, dtype=torch.int64, device="cuda")
+        rev = torch.empty(max(m * kn, 1), dtype=torch.int32, device="cuda")
+        op, rp = offs.data_ptr(), rev.data_ptr()
+    else:
+        offs = np.empty(m + 1, dtype=np.int64)
+        rev = np.empty(max(m * kn, 1), dtype=np.int32)
+        op, rp = offs.ctypes.data, rev.ctypes.data
+    ctx.check(_lib.load().kd_reverse_knn(ctx.ptr, index.ptr, kn, int(on_device), ctypes.c_void_p(op),
+                                         ctypes.c_void_p(rp)))
+    return offs, rev
+
+
 def kd_region(ctx: Context, index: Index, lo, hi):
     """kd_region: (offsets nq+1 int64, idx int32) with box i's tuples at
     idx[offsets[i]:offsets[i+1]]; device tensors for CUDA boxes."""

@@ -117,6 +117,8 @@ __device__ __forceinline__ void knn_insert(double* bd, int32_t* bi, int kn, doub
     bi[j] = t;
 }
 
+// queries == nullptr: every node is a query (row = its address) and its own
+// tuple is not a candidate.
 template <typename T>
 __global__ void __launch_bounds__(SEARCH_THREADS) k_knn(const T* __restrict__ nodes, const int32_t* __restrict__ tuple,
                                                         int32_t m, int k, const T* __restrict__ queries, int64_t nq,
@@ -124,6 +126,8 @@ __global__ void __launch_bounds__(SEARCH_THREADS) k_knn(const T* __restrict__ no
                                                         double* __restrict__ d_out, int* __restrict__ err) {
     const int64_t qi = (int64_t)blockIdx.x * SEARCH_THREADS + threadIdx.x;
     if (qi >= nq) return;
+    const int32_t self = queries ? -1 : tuple[qi];
+    if (!queries) queries = nodes;
     T q[MAXK];
     bool nan = false;
 #pragma unroll
@@ -154,7 +158,8 @@ __global__ void __launch_bounds__(SEARCH_THREADS) k_knn(const T* __restrict__ no
             const double u = abs_diff<T>(p[d], q[d]);
             acc = __dadd_rn(acc, __dmul_rn(u, u));
         }
-        knn_insert(bd, bi, kn, acc, tuple[mid]);
+        const int32_t tm = tuple[mid];
+        if (tm != self) knn_insert(bd, bi, kn, acc, tm);
         const int dim = e.depth % k;
         T qd = q[0], pd = p[0];
 #pragma unroll
@@ -272,6 +277,42 @@ __global__ void __launch_bounds__(SEARCH_THREADS) k_region(const T* __restrict__
         }
     }
     if (!out) counts[qi] = c;
+}
+
+// Reverse nearest neighbours: inv[tuple] = address, then per target
+// address the number of nodes listing it, then the lists.
+__global__ void __launch_bounds__(256) k_inv_map(const int32_t* __restrict__ tuple, int64_t m, int64_t n,
+                                                 int32_t* __restrict__ inv, int* __restrict__ err) {
+    for (int64_t a = (int64_t)blockIdx.x * 256 + threadIdx.x; a < m; a += (int64_t)gridDim.x * 256) {
+        const int32_t t = tuple[a];
+        if (t < 0 || t >= n) atomicOr(err, ERR_INTERNAL); else inv[t] = (int32_t)a;
+    }
+}
+__global__ void __launch_bounds__(256) k_rev_count(const int32_t* __restrict__ nn, int64_t total,
+                                                   const int32_t* __restrict__ inv, int64_t n,
+                                                   int64_t* __restrict__ cnt, int* __restrict__ err) {
+    for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < total; e += (int64_t)gridDim.x * 256) {
+        const int32_t t = nn[e];
+        if (t < 0) continue;
+        const int32_t a = t < n ? inv[t] : -1;
+        if (a < 0) atomicOr(err, ERR_INTERNAL); else atomicAdd((unsigned long long*)&cnt[a], 1ull);
+    }
+}
+__global__ void __launch_bounds__(256) k_rev_fill(const int32_t* __restrict__ nn, int64_t total, int kn,
+                                                  const int32_t* __restrict__ tuple, const int32_t* __restrict__ inv,
+                                                  int64_t n, int64_t* __restrict__ cursor, int32_t* __restrict__ rev,
+                                                  int* __restrict__ err) {
+    for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < total; e += (int64_t)gridDim.x * 256) {
+        const int32_t t = nn[e];
+        if (t < 0) continue;
+        const int32_t a = t < n ? inv[t] : -1;
+        if (a < 0) {
+            atomicOr(err, ERR_INTERNAL);
+            continue;
+        }
+        const int64_t pos = (int64_t)atomicAdd((unsigned long long*)&cursor[a], 1ull);
+        rev[pos] = tuple[e / kn];
+    }
 }
 
 // offs[i] = sum of counts[0..i), offs[n] = total; one block.
@@ -477,6 +518,111 @@ kd_status kd_knn(kd_ctx* ctx, kd_index ix, const void* queries, int64_t nq, int 
     if (!on_device) {
         cudaMemcpyAsync(idx_out, di, (size_t)nq * kn * 4, cudaMemcpyDeviceToHost, s);
         if (dist_out) cudaMemcpyAsync(dist_out, dd, (size_t)nq * kn * 8, cudaMemcpyDeviceToHost, s);
+    }
+    return read_err(ctx, d_err, s);
+}
+
+// m nearest neighbours of every node (address order), its own tuple excluded.
+static kd_status knn_all_device(kd_ctx* ctx, kd_index ix, int kn, int32_t* di, double* dd, int* d_err,
+                                cudaStream_t s) {
+    const int64_t m = ix->m;
+    const int g = grid_of(m, SEARCH_THREADS);
+    if (ix->dtype == KD_I32)
+        k_knn<int32_t><<<g, SEARCH_THREADS, 0, s>>>((const int32_t*)ix->node_coords, ix->node_tuple, (int32_t)m,
+                                                    ix->k, nullptr, m, kn, di, dd, d_err);
+    else if (ix->dtype == KD_I64)
+        k_knn<int64_t><<<g, SEARCH_THREADS, 0, s>>>((const int64_t*)ix->node_coords, ix->node_tuple, (int32_t)m,
+                                                    ix->k, nullptr, m, kn, di, dd, d_err);
+    else
+        k_knn<float><<<g, SEARCH_THREADS, 0, s>>>((const float*)ix->node_coords, ix->node_tuple, (int32_t)m, ix->k,
+                                                  nullptr, m, kn, di, dd, d_err);
+    kd::ctx_add_launches(ctx, 1);
+    return KD_OK;
+}
+
+kd_status kd_knn_all(kd_ctx* ctx, kd_index ix, int kn, int on_device, int32_t* idx_out, double* dist_out) {
+    if (!ctx || !ix) return KD_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(kd::ctx_mutex(ctx));
+    if (cudaSetDevice(kd::ctx_device(ctx)) != cudaSuccess) return sfail(ctx, KD_EDEVICE, "cudaSetDevice failed");
+    if (kn < 1 || kn > KD_KNN_MAX) return sfail(ctx, KD_EINVAL, "kn must be in [1, KD_KNN_MAX]");
+    if (ix->m > 0 && !idx_out) return sfail(ctx, KD_EINVAL, "idx_out is NULL");
+    if (ix->m == 0) return KD_OK;
+    cudaStream_t s = kd::ctx_stream(ctx);
+    CallScratch S(ctx);
+    int32_t* di = idx_out;
+    double* dd = dist_out;
+    int* d_err = nullptr;
+    kd_status st = KD_OK;
+    if (!on_device) {
+        st = S.get((void**)&di, (size_t)ix->m * kn * 4);
+        if (st == KD_OK && dist_out) st = S.get((void**)&dd, (size_t)ix->m * kn * 8);
+    }
+    if (st == KD_OK) st = S.get((void**)&d_err, sizeof(int));
+    if (st != KD_OK) return st;
+    cudaMemsetAsync(d_err, 0, sizeof(int), s);
+    knn_all_device(ctx, ix, kn, di, dd, d_err, s);
+    if (!on_device) {
+        cudaMemcpyAsync(idx_out, di, (size_t)ix->m * kn * 4, cudaMemcpyDeviceToHost, s);
+        if (dist_out) cudaMemcpyAsync(dist_out, dd, (size_t)ix->m * kn * 8, cudaMemcpyDeviceToHost, s);
+    }
+    return read_err(ctx, d_err, s);
+}
+
+kd_status kd_reverse_knn(kd_ctx* ctx, kd_index ix, int kn, int on_device, int64_t* offsets, int32_t* rev_out) {
+    if (!ctx || !ix) return KD_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(kd::ctx_mutex(ctx));
+    if (cudaSetDevice(kd::ctx_device(ctx)) != cudaSuccess) return sfail(ctx, KD_EDEVICE, "cudaSetDevice failed");
+    if (kn < 1 || kn > KD_KNN_MAX) return sfail(ctx, KD_EINVAL, "kn must be in [1, KD_KNN_MAX]");
+    if (!offsets || (ix->m > 0 && !rev_out)) return sfail(ctx, KD_EINVAL, "offsets or rev_out is NULL");
+    cudaStream_t s = kd::ctx_stream(ctx);
+    const int64_t m = ix->m, total = m * kn;
+    CallScratch S(ctx);
+    int32_t *nn = nullptr, *inv = nullptr, *rev = rev_out;
+    int64_t *cnt = nullptr, *offs = offsets, *cursor = nullptr;
+    int* d_err = nullptr;
+    int64_t n = 0;  // tuple indices are below the largest one + 1; the inverse map spans them
+    kd_status st = S.get((void**)&d_err, sizeof(int));
+    if (st != KD_OK) return st;
+    if (m == 0) {
+        int64_t z = 0;
+        if (on_device) cudaMemcpyAsync(offsets, &z, 8, cudaMemcpyHostToDevice, s); else offsets[0] = 0;
+        return cudaStreamSynchronize(s) == cudaSuccess ? KD_OK : sfail(ctx, KD_EDEVICE, "synchronise failed");
+    }
+    // the inverse map needs the largest tuple index
+    {
+        std::vector<int32_t> tmp;
+        int32_t mx = 0;
+        tmp.resize((size_t)m);
+        if (cudaMemcpyAsync(tmp.data(), ix->node_tuple, (size_t)m * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return sfail(ctx, KD_EDEVICE, "reading the index failed");
+        for (int32_t t : tmp) mx = std::max(mx, t);
+        n = (int64_t)mx + 1;
+    }
+    st = S.get((void**)&nn, (size_t)total * 4);
+    if (st == KD_OK) st = S.get((void**)&inv, (size_t)n * 4);
+    if (st == KD_OK) st = S.get((void**)&cnt, (size_t)m * 8);
+    if (st == KD_OK) st = S.get((void**)&cursor, (size_t)(m + 1) * 8);
+    if (st == KD_OK && !on_device) {
+        st = S.get((void**)&offs, (size_t)(m + 1) * 8);
+        if (st == KD_OK) st = S.get((void**)&rev, (size_t)std::max<int64_t>(total, 1) * 4);
+    }
+    if (st != KD_OK) return st;
+    cudaMemsetAsync(d_err, 0, sizeof(int), s);
+    cudaMemsetAsync(inv, 0xff, (size_t)n * 4, s);
+    cudaMemsetAsync(cnt, 0, (size_t)m * 8, s);
+    knn_all_device(ctx, ix, kn, nn, nullptr, d_err, s);
+    k_inv_map<<<grid_of(m, 256), 256, 0, s>>>(ix->node_tuple, m, n, inv, d_err);
+    k_rev_count<<<grid_of(total, 256), 256, 0, s>>>(nn, total, inv, n, cnt, d_err);
+    k_offsets<<<1, 1024, 0, s>>>(cnt, m, offs);
+    cudaMemcpyAsync(cursor, offs, (size_t)(m + 1) * 8, cudaMemcpyDeviceToDevice, s);
+    k_rev_fill<<<grid_of(total, 256), 256, 0, s>>>(nn, total, kn, ix->node_tuple, inv, n, cursor, rev, d_err);
+    kd::ctx_add_launches(ctx, 4);
+    int64_t tot = 0;
+    cudaMemcpyAsync(&tot, offs + m, 8, cudaMemcpyDeviceToHost, s);
+    if (!on_device) {
+        cudaMemcpyAsync(offsets, offs, (size_t)(m + 1) * 8, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(rev_out, rev, (size_t)total * 4, cudaMemcpyDeviceToHost, s);
     }
     return read_err(ctx, d_err, s);
 }

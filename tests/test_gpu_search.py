@@ -110,3 +110,37 @@ def test_region_equals_brute_force(cuda_lib, case):
         cuda_lib.kd_index_destroy(ctx, ix)
     finally:
         ctx.close()
+
+
+@pytest.mark.parametrize("case", [0, 1])
+def test_all_points_and_reverse_neighbours(cuda_lib, case):
+    import torch
+    name, gen, seed, kn = CASES[case]
+    coords = gen()[:6000]
+    ctx = cuda_lib.kd_create(0)
+    try:
+        tree = cuda_lib.build_tree(ctx, torch.from_numpy(coords).cuda())
+        ix = cuda_lib.kd_index_create(ctx, torch.from_numpy(coords).cuda(), tree)
+        m = tree["m"]
+        node = tree["node_tuple"].cpu().numpy()
+        gi, gd = cuda_lib.kd_knn_all(ctx, ix, m, kn)
+        gi, gd = gi.cpu().numpy(), gd.cpu().numpy()
+        # oracle: every tree tuple as a query, its own tuple (distance 0, first) dropped
+        ref_i, ref_d = oracle.knn(coords, coords[node], kn + 1)
+        assert (ref_i[:, 0] == node).all()
+        np.testing.assert_array_equal(gi, ref_i[:, 1:], err_msg=name)
+        np.testing.assert_array_equal(gd, ref_d[:, 1:], err_msg=name)
+        offs, rev = cuda_lib.kd_reverse_knn(ctx, ix, m, kn)
+        offs, rev = offs.cpu().numpy(), rev.cpu().numpy()
+        addr_of = {int(t): a for a, t in enumerate(node)}
+        lists = [[] for _ in range(m)]
+        for a in range(m):
+            for u in ref_i[a, 1:]:
+                if u >= 0:
+                    lists[addr_of[int(u)]].append(int(node[a]))
+        assert offs[-1] == sum(len(x) for x in lists)
+        for a in range(m):
+            assert sorted(rev[offs[a]:offs[a + 1]].tolist()) == sorted(lists[a]), (name, a)
+        cuda_lib.kd_index_destroy(ctx, ix)
+    finally:
+        ctx.close()

@@ -172,15 +172,24 @@ def traffic_for(kernel_family: str):
 
 
 def cpu_baseline(sample: int):
-    """The C oracle (as it stands) on a bounded sample of the same workload."""
+    """The C oracle (as it stands) on a bounded sample of the same workload,
+    and the paper's parallel execution scheme on 2^q host threads (q the
+    largest with 2^q <= the host's cores) on the same sample."""
     import kdgen
     import oracle
     coords = kdgen.large_gmm(n=sample)
     t0 = time.perf_counter()
     oracle.build_tree(coords)
     dt = time.perf_counter() - t0
+    levels = max(0, (os.cpu_count() or 1).bit_length() - 1)
+    t1 = time.perf_counter()
+    oracle.build_tree_parallel(coords, levels)
+    dtp = time.perf_counter() - t1
     return {"value": sample / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"n={sample} points of the same mixture (seed 2), one presort+build, {dt:.1f} s"}
+            "sample": f"n={sample} points of the same mixture (seed 2), one presort+build, {dt:.1f} s",
+            "parallel_scheme": {"value": sample / dtp, "unit": UNIT, "cores": 1 << levels,
+                                "kind": "the paper's parallel execution scheme (host threads)",
+                                "seconds": dtp}}
 
 
 def run_reference(args, rank, world):

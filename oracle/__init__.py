@@ -38,7 +38,7 @@ def build(force: bool = False, mutant: int = 0, out: str | None = None) -> str:
         # -ffp-contract=off: every floating-point operation of the search
         # distances is rounded separately, as their definition states
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", f"-DKDO_MUTANT={int(mutant)}",
-                               "-shared", "-fPIC", _SRC, _SRC_SEARCH, "-o", tmp])
+                               "-shared", "-fPIC", "-pthread", _SRC, _SRC_SEARCH, "-o", tmp])
         os.replace(tmp, lib)
     return lib
 
@@ -58,6 +58,9 @@ def _load(mutant: int = 0):
                                         ctypes.POINTER(ctypes.c_int32)]
         for f in (lib.kdo_presort, lib.kdo_build, lib.kdo_first_split):
             f.restype = ctypes.c_int
+        lib.kdo_build_parallel.argtypes = [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp,
+                                           vp, vp, i64p]
+        lib.kdo_build_parallel.restype = ctypes.c_int
         lib.kdo_knn.argtypes = [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int64, vp,
                                 ctypes.c_int64, ctypes.c_int, vp, vp]
         lib.kdo_knn.restype = ctypes.c_int
@@ -171,3 +174,22 @@ def region(coords: np.ndarray, lo: np.ndarray, hi: np.ndarray, cand: np.ndarray 
         res.append(np.sort(out[o:o + counts[i]]))
         o += counts[i]
     return res
+
+
+def build_tree_parallel(coords: np.ndarray, levels: int):
+    """The paper's parallel scheme on 2^levels host threads (a CPU baseline;
+    the same tree as build_tree).  Returns dict(m, node_tuple, left, right, dim)."""
+    c, n, k, dt = _prep(coords)
+    cap = max(n, 1)
+    node = np.full(cap, -2, dtype=np.int32)
+    left = np.full(cap, -2, dtype=np.int32)
+    right = np.full(cap, -2, dtype=np.int32)
+    dim = np.full(cap, 255, dtype=np.uint8)
+    m = ctypes.c_int64(0)
+    rc = _load().kdo_build_parallel(c.ctypes.data, n, k, dt, levels, node.ctypes.data, left.ctypes.data,
+                                    right.ctypes.data, dim.ctypes.data, ctypes.byref(m))
+    if rc != 0:
+        raise OracleError(rc)
+    mm = m.value
+    return {"m": mm, "node_tuple": node[:mm].copy(), "left": left[:mm].copy(), "right": right[:mm].copy(),
+            "dim": dim[:mm].copy()}

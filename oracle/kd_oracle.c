@@ -40,6 +40,7 @@
  * children are the medians of the left/right sub-ranges (-1 if empty);
  * dim[a] = depth mod k; root = (m - 1) / 2.
  */
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -360,4 +361,128 @@ int kdo_first_split(const void *coords, int64_t n, int k, int dtype,
     }
     free(tmp);
     return KDO_OK;
+}
+
+/*
+ * The paper's parallel execution scheme (Section "Parallel Execution"),
+ * a host baseline rather than a reference: the merge sorts and the
+ * recursive build split their ranges as above, and at the first `levels`
+ * levels of recursion the parent thread hands the lower half to a child
+ * thread, processes the upper half itself and then joins the child
+ * (2^levels threads).  Deeper levels run in the calling thread.  The result
+ * is the single-threaded result: the halves never overlap.
+ */
+typedef struct {
+    const tuples_t *t;
+    int32_t *idx, *tmp;
+    int64_t lo, hi;
+    int p, levels;
+} msort_job;
+
+static void merge_sort_mt(const tuples_t *t, int32_t *idx, int32_t *tmp, int64_t lo, int64_t hi, int p, int levels);
+
+static void *msort_thread(void *arg)
+{
+    msort_job *j = (msort_job *)arg;
+    merge_sort_mt(j->t, j->idx, j->tmp, j->lo, j->hi, j->p, j->levels);
+    return NULL;
+}
+
+static void merge_sort_mt(const tuples_t *t, int32_t *idx, int32_t *tmp, int64_t lo, int64_t hi, int p, int levels)
+{
+    if (levels <= 0 || hi - lo < 4096) {
+        merge_sort(t, idx, tmp, lo, hi, p);
+        return;
+    }
+    int64_t mid = lo + (hi - lo) / 2;
+    msort_job child = {t, idx, tmp, lo, mid, p, levels - 1};
+    pthread_t th;
+    int forked = pthread_create(&th, NULL, msort_thread, &child) == 0;
+    if (!forked)
+        merge_sort_mt(t, idx, tmp, lo, mid, p, levels - 1);
+    merge_sort_mt(t, idx, tmp, mid + 1, hi, p, levels - 1);
+    if (forked)
+        pthread_join(th, NULL);
+    int64_t i = lo, j = mid + 1, o = lo;
+    while (i <= mid && j <= hi)
+        tmp[o++] = (superkey_cmp(t, idx[j], idx[i], p) < 0) ? idx[j++] : idx[i++];
+    while (i <= mid)
+        tmp[o++] = idx[i++];
+    while (j <= hi)
+        tmp[o++] = idx[j++];
+    memcpy(idx + lo, tmp + lo, (size_t)(hi - lo + 1) * sizeof(int32_t));
+}
+
+typedef struct {
+    build_t *b;
+    int64_t lo, hi;
+    int depth, levels;
+} build_job;
+
+static void build_rec_mt(build_t *b, int64_t lo, int64_t hi, int depth, int levels);
+
+static void *build_thread(void *arg)
+{
+    build_job *j = (build_job *)arg;
+    build_rec_mt(j->b, j->lo, j->hi, j->depth, j->levels);
+    return NULL;
+}
+
+static void build_rec_mt(build_t *b, int64_t lo, int64_t hi, int depth, int levels)
+{
+    if (levels <= 0 || hi - lo < 4096) {
+        build_rec(b, lo, hi, depth);
+        return;
+    }
+    int32_t *A = b->arr[0];
+    int64_t mid = median_addr(lo, hi);
+    set_node(b, mid, A[mid], depth, child_addr(lo, mid - 1), child_addr(mid + 1, hi));
+    split_level(b, lo, hi, depth);
+    build_job child = {b, lo, mid - 1, depth + 1, levels - 1};
+    pthread_t th;
+    int forked = pthread_create(&th, NULL, build_thread, &child) == 0;
+    if (!forked)
+        build_rec_mt(b, lo, mid - 1, depth + 1, levels - 1);
+    build_rec_mt(b, mid + 1, hi, depth + 1, levels - 1);
+    if (forked)
+        pthread_join(th, NULL);
+}
+
+int kdo_build_parallel(const void *coords, int64_t n, int k, int dtype, int levels, int32_t *node_tuple,
+                       int32_t *left, int32_t *right, uint8_t *dim, int64_t *m_out)
+{
+    tuples_t t = {coords, n, k, dtype};
+    int rc = check_input(&t);
+    if (rc != KDO_OK)
+        return rc;
+    size_t cap = (size_t)(n > 0 ? n : 1);
+    int32_t *store = (int32_t *)malloc(cap * (size_t)k * sizeof(int32_t));
+    int32_t *temp = (int32_t *)malloc(cap * sizeof(int32_t));
+    if (!store || !temp) {
+        free(store);
+        free(temp);
+        return KDO_ENOMEM;
+    }
+    int64_t m = n;
+    for (int d = 0; d < k && rc == KDO_OK; d++) {
+        int32_t *a = store + (int64_t)d * n;
+        for (int64_t i = 0; i < n; i++)
+            a[i] = (int32_t)i;
+        merge_sort_mt(&t, a, temp, 0, n - 1, d, levels);
+        int64_t md = remove_duplicates(&t, a, n);
+        if (d > 0 && md != m)
+            rc = KDO_EINVAL;
+        m = md;
+    }
+    if (rc == KDO_OK) {
+        int32_t *roles[64];
+        for (int d = 0; d < k; d++)
+            roles[d] = store + (int64_t)d * n;
+        build_t b = {&t, roles, temp, NULL, node_tuple, left, right, dim, 1};
+        build_rec_mt(&b, 0, m - 1, 0, levels);
+        *m_out = m;
+    }
+    free(store);
+    free(temp);
+    return rc;
 }

@@ -227,3 +227,17 @@ def test_each_planted_mistake_fails_a_pin(mutant):
             caught.append("bruteforce")
             break
     assert caught, f"mutant {mutant} not detected by any pin"
+
+
+@pytest.mark.parametrize("levels", [1, 3])
+def test_parallel_scheme_builds_the_same_tree(levels):
+    """The paper's parallel execution scheme (a host baseline) gives the
+    single-threaded oracle's tree."""
+    import kdgen
+    for coords in (kdgen.cloud_int_uniform(40000, 3, 10, 41, np.int64, dup_frac=0.01),
+                   kdgen.cloud_gmm(30000, 4, 42)):
+        ref = oracle.build_tree(coords)
+        got = oracle.build_tree_parallel(coords, levels)
+        assert got["m"] == ref["m"]
+        for f in ("node_tuple", "left", "right", "dim"):
+            np.testing.assert_array_equal(got[f], ref[f])

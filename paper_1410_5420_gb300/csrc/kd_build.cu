@@ -254,6 +254,27 @@ __device__ __forceinline__ void tile_bounds(const uint32_t* rec, int32_t (&lo)[L
     }
 }
 
+// Single-segment tiles with every decision level: the medians of the
+// segment's K-1 decision levels held in registers (heap order, mh[1..]),
+// and an element's bucket found by K-1 compares.  Returns false for an
+// element equal to a median.
+template <int K>
+__device__ __forceinline__ bool route_fast(const uint32_t (&mh)[1 << (K - 1)], const uint32_t* r, uint32_t& bucket) {
+    uint32_t h = 1;
+    bool eq = false;
+#pragma unroll
+    for (int f = 0; f < K - 1; ++f) {
+        uint32_t mv = mh[1 << f];
+#pragma unroll
+        for (int c = (1 << f) + 1; c < (2 << f); ++c)
+            if (h == (uint32_t)c) mv = mh[c];
+        eq |= r[f] == mv;
+        h = 2 * h + (r[f] > mv ? 1u : 0u);
+    }
+    bucket = h - (1u << (K - 1));
+    return !eq;
+}
+
 // Bucket of an element of segment slot sj after F decision levels: r[f] is
 // its rank in super key (lev_in + f) mod K, compared with the medians of
 // the tile record; INV for an element equal to a median (the node itself).
@@ -328,22 +349,29 @@ __global__ void __launch_bounds__(LEVEL_BLOCK)
         const int32_t lo0 = tlo[0];
         const int F = M.F;
         if (ns == 1 && F == K - 1) {  // one segment, every decision level
-            const uint32_t* med = rec + TR_HEAD;
+            uint32_t mh[K <= 4 ? NBMAX : 1];
+            if constexpr (K <= 4) {
+#pragma unroll
+                for (int h = 0; h < NBMAX; ++h) mh[h] = rec[TR_HEAD + h];
+            }
 #pragma unroll
             for (int j = 0; j < IPT; ++j) {
                 const int o = wbase + j * 32 + lane;
                 const int32_t pos = M.pos0 + o;
                 if (o < M.npos && pos >= tlo[0] && pos <= thi[0]) {
-                    uint32_t h = 1;
-                    bool eq = false;
+                    uint32_t r[K];
 #pragma unroll
-                    for (int f = 0; f < K - 1; ++f) {
-                        const uint32_t r = st[TW + NBP + f * PST + M.shift + o];
-                        const uint32_t mv = med[h];
-                        eq |= r == mv;
-                        h = 2 * h + (r > mv ? 1u : 0u);
+                    for (int f = 0; f < K - 1; ++f) r[f] = st[TW + NBP + f * PST + M.shift + o];
+                    uint32_t b;
+                    bool keep;
+                    if constexpr (K <= 4) {
+                        keep = route_fast<K>(mh, r, b);
+                    } else {
+                        const uint32_t d = route_rec<K>(r, F, 0, rec);
+                        keep = d != INV;
+                        b = d;
                     }
-                    if (!eq) atomicAdd(&s_cnt[s][h - (uint32_t)NBMAX], 1u);
+                    if (keep) atomicAdd(&s_cnt[s][b], 1u);
                 }
             }
         } else {
@@ -485,7 +513,8 @@ __global__ void __launch_bounds__(LEVEL_BLOCK, K <= 3 ? 3 : 2)
     __shared__ __align__(8) uint64_t full[LEVEL_STAGES], empty[LEVEL_STAGES];
     __shared__ StageMeta meta[LEVEL_STAGES];
     __shared__ uint32_t s_wc[LEVEL_WARPS][NDMAX];
-    __shared__ int32_t s_dbase[NDMAX], s_dlo[NDMAX], s_dhi[NDMAX], s_dmid[NDMAX];
+    __shared__ int2 s_dlh[NDMAX];   // final segment [lo, hi] of each digit
+    __shared__ int32_t s_dmid[NDMAX];
     __shared__ int32_t s_segidx[LEVEL_NSMAX];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
@@ -528,7 +557,11 @@ __global__ void __launch_bounds__(LEVEL_BLOCK, K <= 3 ? 3 : 2)
         if (ns == 1 && F == K - 1) {
             // one segment and every decision level: compile-time routing and
             // K ballot bits (buckets 0 .. NB-1, marker NB)
-            const uint32_t* med = rec + TR_HEAD;
+            uint32_t mh[K <= 4 ? NBMAX : 1];
+            if constexpr (K <= 4) {
+#pragma unroll
+                for (int h = 0; h < NBMAX; ++h) mh[h] = rec[TR_HEAD + h];
+            }
 #pragma unroll
             for (int j = 0; j < IPT; ++j) {
                 const int o = wbase + j * 32 + lane;
@@ -540,15 +573,16 @@ __global__ void __launch_bounds__(LEVEL_BLOCK, K <= 3 ? 3 : 2)
 #pragma unroll
                     for (int f = 0; f < K; ++f) v[f][j] = st[TW + NBP + f * PST + M.shift + o];  // slot `own` is unused
                     if (pos >= tlo[0] && pos <= thi[0]) {
-                        uint32_t h = 1;
-                        bool eq = false;
+                        uint32_t r[K];
 #pragma unroll
-                        for (int f = 0; f < K - 1; ++f) {
-                            const uint32_t mv = med[h];
-                            eq |= v[f][j] == mv;
-                            h = 2 * h + (v[f][j] > mv ? 1u : 0u);
+                        for (int f = 0; f < K; ++f) r[f] = v[f][j];
+                        if constexpr (K <= 4) {
+                            uint32_t b;
+                            if (route_fast<K>(mh, r, b)) dig[j] = b;
+                        } else {
+                            const uint32_t d = route_rec<K>(r, F, 0, rec);
+                            if (d != INV) dig[j] = d;
                         }
-                        if (!eq) dig[j] = h - (uint32_t)NBMAX;
                     }
                 }
             }
@@ -580,13 +614,6 @@ __global__ void __launch_bounds__(LEVEL_BLOCK, K <= 3 ? 3 : 2)
         // segment; the first segment continues the scanned counts of earlier tiles
         const bool first_cont = ns > 0 && tlo[0] < M.pos0;
         for (int d = tid; d < ns * NB; d += LEVEL_THREADS) {
-            uint32_t c = 0;
-#pragma unroll
-            for (int w = 0; w < LEVEL_WARPS; ++w) {
-                const uint32_t x = s_wc[w][d];
-                s_wc[w][d] = c;
-                c += x;
-            }
             const int sj = d >> F;
             const int b = d - (sj << F);
             int32_t a = (int32_t)rec[1 + sj], z = (int32_t)rec[5 + sj];
@@ -594,10 +621,16 @@ __global__ void __launch_bounds__(LEVEL_BLOCK, K <= 3 ? 3 : 2)
                 const int32_t mid = a + ((z - a) >> 1);
                 if ((b >> f) & 1) a = mid + 1; else z = mid - 1;
             }
-            s_dlo[d] = a;
-            s_dhi[d] = z;
+            // each warp's row: the destination of its first element of digit d
+            uint32_t c = (uint32_t)(a + ((sj == 0 && first_cont && M.has_incl) ? (int32_t)st[TW + b] : 0));
+#pragma unroll
+            for (int w = 0; w < LEVEL_WARPS; ++w) {
+                const uint32_t x = s_wc[w][d];
+                s_wc[w][d] = c;
+                c += x;
+            }
+            s_dlh[d] = make_int2(a, z);
             s_dmid[d] = M.write_med ? a + ((z - a) >> 1) : -1;
-            s_dbase[d] = a + ((sj == 0 && first_cont && M.has_incl) ? (int32_t)st[TW + b] : 0);
         }
         if (tid < LEVEL_NSMAX) s_segidx[tid] = (int32_t)rec[9 + tid];
         consumer_sync<LEVEL_THREADS>();
@@ -610,12 +643,13 @@ __global__ void __launch_bounds__(LEVEL_BLOCK, K <= 3 ? 3 : 2)
             dest[j] = -1;
             const uint32_t d = dig[j];
             if (d < marker) {
-                const int32_t dd = s_dbase[d] + (int32_t)(s_wc[warp][d] + rank[j]);
+                const int32_t dd = (int32_t)(s_wc[warp][d] + rank[j]);
                 // the destination must lie in the element's final segment; any
                 // other value means inconsistent inputs and is never written
-                if (dd >= s_dlo[d] && dd <= s_dhi[d]) {
+                const int2 lh = s_dlh[d];
+                if (dd >= lh.x && dd <= lh.y) {
                     dest[j] = dd;
-                    if (dd == s_dmid[d]) {
+                    if (M.write_med && dd == s_dmid[d]) {
                         const int sj = (int)(d >> F);
                         const int32_t si = (s_segidx[sj] << F) + (int32_t)(d - ((uint32_t)sj << F));
                         // rank 0 of the median (its position in array 0) gives

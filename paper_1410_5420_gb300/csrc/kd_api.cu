@@ -56,8 +56,8 @@ size_t finish_smem(int k, int smax);
 cudaError_t init_presort_kernels();
 cudaError_t init_build_kernels();
 int finish_kmax(int smax);
-cudaError_t launch_finish(const AllBufs& bufs, int k, const int64_t* unit_prefix, int ncloud, int nunits,
-                          const CloudDev* clouds, const uint32_t* perm0, int smax, int* err,
+cudaError_t launch_finish(const AllBufs& bufs, int k, const int64_t* unit_prefix, int ncloud, int64_t unit_base,
+                          int nunits, const CloudDev* clouds, const uint32_t* perm0, int smax, int* err,
                           unsigned long long* phase_ns, cudaStream_t s);
 cudaError_t launch_top_nodes(const CloudDev* clouds, const int64_t* prefix, int ncloud, int64_t total, int k,
                              const uint32_t* perm0, uint32_t* medr, int all_nodes, cudaStream_t s);
@@ -113,6 +113,9 @@ struct kd_ctx {
     double fam_bytes[F_COUNT] = {0};
     double trace_ns[8] = {0};  // finisher phase block-time sums (debug bit 4)
     int64_t fam_launches[F_COUNT] = {0};
+    // copies of host outputs overlapping the finisher (created on first use)
+    cudaStream_t copy_stream = nullptr;
+    std::vector<cudaEvent_t> chunk_events;
     // pinned host scratch for small uploads
     void* pinned = nullptr;
     size_t pinned_bytes = 0;
@@ -267,6 +270,19 @@ void collect_timing(kd_ctx* ctx) {
     ctx->timed.clear();
 }
 
+// The context's copy stream and at least nev events (created on first use).
+kd_status ensure_copy_stream(kd_ctx* ctx, size_t nev) {
+    if (!ctx->copy_stream && cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(ctx, KD_EDEVICE, "cannot create the copy stream");
+    while (ctx->chunk_events.size() < nev) {
+        cudaEvent_t e;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+            return fail(ctx, KD_EDEVICE, "cannot create an event");
+        ctx->chunk_events.push_back(e);
+    }
+    return KD_OK;
+}
+
 kd_status check_device_err(kd_ctx* ctx, int* d_err) {
     int err = 0;
     CK(cudaMemcpyAsync(&err, d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
@@ -387,8 +403,15 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
     Scratch S(ctx);
     // coordinates on the device, clouds back to back
     const void* coords = nullptr;
+    // a single cloud on the host is uploaded in chunks on the copy stream,
+    // each transformed as soon as it has arrived
+    const int up_chunks = (count == 1 && !clouds[0].on_device && N >= (1 << 20)) ? 8 : 1;
     if (count == 1 && clouds[0].on_device) {
         coords = clouds[0].coords;
+    } else if (up_chunks > 1) {
+        unsigned char* cb = nullptr;
+        CKS(S.get(&cb, (size_t)N * k * tsz));
+        coords = cb;
     } else {
         unsigned char* cb = nullptr;
         CKS(S.get(&cb, (size_t)N * k * tsz));
@@ -431,7 +454,28 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
     CK(cudaMemcpyAsync(mcloud, nc32.data(), (size_t)count * 4, cudaMemcpyHostToDevice, s));
     if (count > 1)
         CK(cudaMemcpyAsync(cstart, H->in_off.data(), (size_t)(count + 1) * 8, cudaMemcpyHostToDevice, s));
-    {
+    if (up_chunks > 1) {
+        CKS(ensure_copy_stream(ctx, up_chunks + 1));
+        cudaStream_t cs = ctx->copy_stream;
+        CK(cudaEventRecord(ctx->chunk_events[up_chunks], s));  // the upload buffer is ready on s
+        CK(cudaStreamWaitEvent(cs, ctx->chunk_events[up_chunks], 0));
+        const size_t row = (size_t)k * tsz;
+        unsigned char* cb = (unsigned char*)coords;
+        for (int c = 0; c < up_chunks; ++c) {
+            const int64_t r0 = N * c / up_chunks, r1 = N * (c + 1) / up_chunks;
+            CK(cudaMemcpyAsync(cb + r0 * row, (const unsigned char*)clouds[0].coords + r0 * row, (r1 - r0) * row,
+                               cudaMemcpyHostToDevice, cs));
+            CK(cudaEventRecord(ctx->chunk_events[c], cs));
+        }
+        for (int c = 0; c < up_chunks; ++c) {
+            const int64_t r0 = N * c / up_chunks, r1 = N * (c + 1) / up_chunks;
+            CK(cudaStreamWaitEvent(s, ctx->chunk_events[c], 0));
+            LaunchTimer lt(ctx, F_TRANSFORM, (double)(r1 - r0), nullptr, (double)k * (tsz + w));
+            CK(launch_transform(dtype, cb + r0 * row, r1 - r0, k, keys + r0 * w, NS,
+                                tail ? tail + r0 * (k - 1) * w : nullptr, cstart, 1, cloud_plane, cloud_digits, hist,
+                                d_err, s));
+        }
+    } else {
         LaunchTimer lt(ctx, F_TRANSFORM, (double)N, nullptr, (double)k * (tsz + w) + (count > 1 ? 4 : 0));
         CK(launch_transform(dtype, coords, N, k, keys, NS, tail, cstart, count, cloud_plane, cloud_digits, hist, d_err,
                             s));
@@ -946,15 +990,53 @@ kd_status build_batch(kd_ctx* ctx, kd_presorted* H, kd_tree* outs) {
         CK(launch_level_pass(k, bufs, step_q[st], d_jobs + job_off[st], (int)step_jobs[st].size(),
                              (int)step_ntiles[st], d_cd, medr, H->perm0, d_status, d_err, s));
     }
+    // A single cloud with host outputs: the finisher runs in chunks of
+    // units and each chunk's address range (which also holds the nodes
+    // above the finisher level between its units, final by now) is copied
+    // to the host on a second stream while the next chunk runs.
+    const bool overlap_copy = any_host && count == 1 && nunits >= 64 && !(ctx->debug & 4) && !outs[0].on_device;
+    const int nchunks = overlap_copy ? 8 : 1;
+    if (overlap_copy) CKS(ensure_copy_stream(ctx, nchunks + 1));
     if (nunits > 0) {
-        LaunchTimer lt(ctx, F_FINISH, (double)M, nullptr,
-                       4.0 * (2 * k - 1) + 8.0 + (want_l ? 4 : 0) + (want_r ? 4 : 0) + (want_d ? 1 : 0));
         unsigned long long* phase = nullptr;
         if (ctx->debug & 4) {
             CKS(S.get(&phase, sizeof(unsigned long long) * 8));
             CK(cudaMemsetAsync(phase, 0, sizeof(unsigned long long) * 8, s));
         }
-        CK(launch_finish(bufs, k, d_uprefix, count, (int)nunits, d_cd, H->perm0, smax, d_err, phase, s));
+        const int64_t m0 = cd[0].m;
+        for (int c = 0; c < nchunks; ++c) {
+            const int64_t u0 = nunits * c / nchunks, u1 = nunits * (c + 1) / nchunks;
+            {
+                LaunchTimer lt(ctx, F_FINISH, (double)M * (u1 - u0) / nunits, nullptr,
+                               4.0 * (2 * k - 1) + 8.0 + (want_l ? 4 : 0) + (want_r ? 4 : 0) + (want_d ? 1 : 0));
+                CK(launch_finish(bufs, k, d_uprefix, count, u0, (int)(u1 - u0), d_cd, H->perm0, smax, d_err, phase,
+                                 s));
+            }
+            if (overlap_copy) {
+                // addresses [a0, a1): from the first unit's start (0 for the
+                // first chunk) to the next chunk's first unit (m for the last)
+                auto unit_lo = [&](int64_t u) {
+                    int32_t lo = 0, hi = (int32_t)m0 - 1;
+                    for (int l = lam[0] - 1; l >= 0; --l) {
+                        const int32_t mid = lo + ((hi - lo) >> 1);
+                        if ((u >> l) & 1) lo = mid + 1; else hi = mid - 1;
+                    }
+                    return (int64_t)lo;
+                };
+                const int64_t a0 = c == 0 ? 0 : unit_lo(u0), a1 = c + 1 == nchunks ? m0 : unit_lo(u1);
+                CK(cudaEventRecord(ctx->chunk_events[c], s));
+                CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->chunk_events[c], 0));
+                if (a1 > a0) {
+                    const size_t na = (size_t)(a1 - a0);
+                    cudaStream_t cs = ctx->copy_stream;
+                    CK(cudaMemcpyAsync(outs[0].node_tuple + a0, st_node + a0, na * 4, cudaMemcpyDeviceToHost, cs));
+                    if (outs[0].left) CK(cudaMemcpyAsync(outs[0].left + a0, st_left + a0, na * 4, cudaMemcpyDeviceToHost, cs));
+                    if (outs[0].right)
+                        CK(cudaMemcpyAsync(outs[0].right + a0, st_right + a0, na * 4, cudaMemcpyDeviceToHost, cs));
+                    if (outs[0].dim) CK(cudaMemcpyAsync(outs[0].dim + a0, st_dim + a0, na, cudaMemcpyDeviceToHost, cs));
+                }
+            }
+        }
         if (phase) {
             unsigned long long h[8];
             CK(cudaMemcpyAsync(h, phase, sizeof(h), cudaMemcpyDeviceToHost, s));
@@ -962,7 +1044,13 @@ kd_status build_batch(kd_ctx* ctx, kd_presorted* H, kd_tree* outs) {
             for (int i = 0; i < 8; ++i) ctx->trace_ns[i] += (double)h[i];
         }
     }
+    if (overlap_copy) {
+        // the caller's stream completes only after the copies
+        CK(cudaEventRecord(ctx->chunk_events[nchunks], ctx->copy_stream));
+        CK(cudaStreamWaitEvent(s, ctx->chunk_events[nchunks], 0));
+    }
     CKS(check_device_err(ctx, d_err));
+    if (overlap_copy) return KD_OK;  // check_device_err synchronised the stream after the copies
     if (any_host) {
         for (int i = 0; i < count; ++i) {
             if (outs[i].on_device || cd[i].m == 0) continue;
@@ -1300,6 +1388,8 @@ kd_status kd_destroy(kd_ctx* ctx) {
         for (auto e : ctx->event_pool) cudaEventDestroy(e);
         if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
         if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+        if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+        for (cudaEvent_t e : ctx->chunk_events) cudaEventDestroy(e);
     }
     delete ctx;
     return KD_OK;

@@ -855,8 +855,8 @@ __device__ __forceinline__ void fin_load_dispatch(const AllBufs& bufs, const Clo
 template <int SMAX>
 __global__ void __launch_bounds__(FIN_THREADS, SMAX >= 4096 ? 2 : 3)
     k_finish(const __grid_constant__ AllBufs bufs, int k, const int64_t* __restrict__ unit_prefix, int ncloud,
-             const CloudDev* __restrict__ clouds, const uint32_t* __restrict__ perm0, int* __restrict__ err,
-             unsigned long long* __restrict__ phase_ns) {
+             int64_t unit_base, const CloudDev* __restrict__ clouds, const uint32_t* __restrict__ perm0,
+             int* __restrict__ err, unsigned long long* __restrict__ phase_ns) {
     constexpr int GMAX = SMAX / FIN_THREADS;
     constexpr int smax = SMAX;
     extern __shared__ __align__(16) uint32_t sm[];
@@ -871,8 +871,9 @@ __global__ void __launch_bounds__(FIN_THREADS, SMAX >= 4096 ? 2 : 3)
     uint8_t* lab = reinterpret_cast<uint8_t*>(nodelid + smax);   // per lid: segment label at the current level
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     FinUnit U;
-    U.cloud = last_le(unit_prefix, ncloud + 1, blockIdx.x);
-    U.seg = (int32_t)(blockIdx.x - unit_prefix[U.cloud]);
+    const int64_t unit = unit_base + blockIdx.x;
+    U.cloud = last_le(unit_prefix, ncloud + 1, unit);
+    U.seg = (int32_t)(unit - unit_prefix[U.cloud]);
     const CloudDev& C = clouds[U.cloud];
     int32_t lo, hi;
     segment_bounds(C.m, C.lam, U.seg, lo, hi);
@@ -1212,18 +1213,22 @@ cudaError_t init_build_kernels() {
     return e;
 }
 
-cudaError_t launch_finish(const AllBufs& bufs, int k, const int64_t* unit_prefix, int ncloud, int nunits,
-                          const CloudDev* clouds, const uint32_t* perm0, int smax, int* err,
+// Finisher over units [unit_base, unit_base + nunits).
+cudaError_t launch_finish(const AllBufs& bufs, int k, const int64_t* unit_prefix, int ncloud, int64_t unit_base,
+                          int nunits, const CloudDev* clouds, const uint32_t* perm0, int smax, int* err,
                           unsigned long long* phase_ns, cudaStream_t s) {
     if (nunits == 0) return cudaSuccess;
     if (k > fin_kmax(smax)) return cudaErrorInvalidValue;
     const size_t smem = finish_smem(k, smax);
     if (smax == 2048)
-        k_finish<2048><<<nunits, FIN_THREADS, smem, s>>>(bufs, k, unit_prefix, ncloud, clouds, perm0, err, phase_ns);
+        k_finish<2048><<<nunits, FIN_THREADS, smem, s>>>(bufs, k, unit_prefix, ncloud, unit_base, clouds, perm0, err,
+                                                         phase_ns);
     else if (smax == 1024)
-        k_finish<1024><<<nunits, FIN_THREADS, smem, s>>>(bufs, k, unit_prefix, ncloud, clouds, perm0, err, phase_ns);
+        k_finish<1024><<<nunits, FIN_THREADS, smem, s>>>(bufs, k, unit_prefix, ncloud, unit_base, clouds, perm0, err,
+                                                         phase_ns);
     else if (smax == 4096)
-        k_finish<4096><<<nunits, FIN_THREADS, smem, s>>>(bufs, k, unit_prefix, ncloud, clouds, perm0, err, phase_ns);
+        k_finish<4096><<<nunits, FIN_THREADS, smem, s>>>(bufs, k, unit_prefix, ncloud, unit_base, clouds, perm0, err,
+                                                         phase_ns);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();

@@ -203,7 +203,7 @@ template <typename KW, int TILE, int SP>
 constexpr size_t rs_move_smem() {
     // two stages, then the sorted tile: keys, or key + payload pairs for
     // 32-bit keys with one payload plane
-    const size_t sorted = (sizeof(KW) == 4 && SP == 1) ? (size_t)TILE * 2 : (size_t)TILE * (sizeof(KW) / 4);
+    const size_t sorted = sizeof(KW) == 4 ? (size_t)TILE * (SP == 1 ? 2 : 3) : (size_t)TILE * 2;
     return ((size_t)2 * (RADIX + TILE * (sizeof(KW) / 4) + SP * TILE) + sorted) * 4;
 }
 
@@ -216,6 +216,7 @@ __global__ void __launch_bounds__(RS_BLOCK, TILE * (SP + 1) * sizeof(KW) <= 2048
     constexpr int KWW = sizeof(KW) / 4;
     constexpr int SW = RADIX + TILE * KWW + SP * TILE;  // stage words: offsets row | keys | payloads
     constexpr bool PAIR = sizeof(KW) == 4 && SP == 1;   // key and payload sorted together
+    constexpr bool TRIPLE = sizeof(KW) == 4 && SP >= 2;  // key and two payloads: an 8-byte and a 4-byte word
     extern __shared__ __align__(128) uint32_t rsm[];     // [2][SW] stages, then the sorted tile [TILE] keys
     __shared__ __align__(8) uint64_t full[2], empty[2];
     __shared__ SortMeta meta[2];
@@ -350,6 +351,45 @@ __global__ void __launch_bounds__(RS_BLOCK, TILE * (SP + 1) * sizeof(KW) <= 2048
                         if ((int64_t)dd < count) {
                             if (key_dst) key_dst[dd] = (KW)kv.x;
                             dst[dd] = kv.y;
+                        } else {
+                            atomicOr(err, ERR_INTERNAL);
+                        }
+                    }
+                }
+                continue;
+            }
+        }
+        if constexpr (TRIPLE) {
+            if (pay.n == 2) {
+                uint2* sb2 = reinterpret_cast<uint2*>(sb32);
+                uint32_t* sb1 = sb32 + 2 * TILE;
+                const uint32_t* src0 = pay.src[0];
+                const uint32_t* src1 = pay.src[1];
+                const uint32_t* sp0 = st + RADIX + TILE * KWW;
+                const uint32_t* sp1 = sp0 + TILE;
+#pragma unroll
+                for (int j = 0; j < IPT; ++j) {
+                    const int o = wbase + j * 32 + lane;
+                    if (dig[j] < RADIX) {
+                        sb2[slot[j]] = make_uint2((uint32_t)skeys[o], src0 ? sp0[o] : (uint32_t)(M.base + o));
+                        sb1[slot[j]] = src1 ? sp1[o] : (uint32_t)(M.base + o);
+                    }
+                }
+                consumer_sync<RS_THREADS>();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[s]);  // every read of the stage is behind the barrier
+                uint32_t* dst0 = pay.dst[0];
+                uint32_t* dst1 = pay.dst[1];
+#pragma unroll
+                for (int r = 0; r < IPT; ++r) {
+                    const int i = r * RS_THREADS + tid;
+                    if (i < M.n) {
+                        const uint2 kv = sb2[i];
+                        const uint32_t dd = s_goff[digit_of((KW)kv.x, shift)] + (uint32_t)i;
+                        if ((int64_t)dd < count) {
+                            if (key_dst) key_dst[dd] = (KW)kv.x;
+                            dst0[dd] = kv.y;
+                            dst1[dd] = sb1[i];
                         } else {
                             atomicOr(err, ERR_INTERNAL);
                         }
@@ -783,7 +823,7 @@ cudaError_t launch_sort_pass(int key64, const int64_t* count_ptr, int64_t max_co
                                                  g_rs_occ[3], err, s)
                     : rs_pass<uint64_t, 2048, 1>(count_ptr, max_count, key_src, key_dst, pay, digit_base, shift, A,
                                                  g_rs_occ[2], err, s);
-    return many ? rs_pass<uint32_t, 2048, 4>(count_ptr, max_count, key_src, key_dst, pay, digit_base, shift, A,
+    return many ? rs_pass<uint32_t, 2048, 2>(count_ptr, max_count, key_src, key_dst, pay, digit_base, shift, A,
                                              g_rs_occ[1], err, s)
                 : rs_pass<uint32_t, 2048, 1>(count_ptr, max_count, key_src, key_dst, pay, digit_base, shift, A,
                                              g_rs_occ[0], err, s);
@@ -812,7 +852,7 @@ cudaError_t init_presort_kernels() {
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g_rs_sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = init_rs_move<uint32_t, 2048, 1>(&g_rs_occ[0]);
-    if (e == cudaSuccess) e = init_rs_move<uint32_t, 2048, 4>(&g_rs_occ[1]);
+    if (e == cudaSuccess) e = init_rs_move<uint32_t, 2048, 2>(&g_rs_occ[1]);
     if (e == cudaSuccess) e = init_rs_move<uint64_t, 2048, 1>(&g_rs_occ[2]);
     if (e == cudaSuccess) e = init_rs_move<uint64_t, 1024, 4>(&g_rs_occ[3]);
     return e;

@@ -257,7 +257,11 @@ void collect_timing(kd_ctx* ctx) {
         double u = t.units;
         if (t.units_dev) {
             int64_t v = 0;
-            cudaMemcpy(&v, t.units_dev, sizeof(v), cudaMemcpyDeviceToHost);
+            cudaPointerAttributes pa{};
+            if (cudaPointerGetAttributes(&pa, t.units_dev) == cudaSuccess && pa.type == cudaMemoryTypeDevice)
+                cudaMemcpy(&v, t.units_dev, sizeof(v), cudaMemcpyDeviceToHost);
+            else
+                cudaGetLastError();
             u = (double)v;
         }
         ctx->fam_ms[t.family] += ms;
@@ -1268,8 +1272,8 @@ kd_status kd_build(kd_ctx* ctx, kd_handle h, kd_tree* out) {
     cudaSetDevice(ctx->device);
     ctx->last_error.clear();
     kd_status st = out ? build_batch(ctx, h, out) : fail(ctx, KD_EINVAL, "tree output is NULL");
-    release_handle(ctx, h);
     if (st == KD_OK && (ctx->debug & 2)) collect_timing(ctx);
+    release_handle(ctx, h);
     return st;
 }
 
@@ -1289,8 +1293,10 @@ kd_status kd_build_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_tree
     kd_status st = presort_batch(ctx, clouds, count, &h);
     if (st != KD_OK) return st;
     st = build_batch(ctx, h, outs);
-    release_handle(ctx, h);
+    // timing first: presort launches read their element counts from the
+    // handle's device memory
     if (st == KD_OK && (ctx->debug & 2)) collect_timing(ctx);
+    release_handle(ctx, h);
     return st;
 }
 

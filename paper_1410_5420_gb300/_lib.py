@@ -68,7 +68,7 @@ def load():
         "kd_handle_arrays": ([vp, vp, vp, ctypes.c_int], ctypes.c_int),
         "kd_build": ([vp, vp, P(KdTree)], ctypes.c_int),
         "kd_release": ([vp, vp], ctypes.c_int),
-        "kd_build_batch": ([vp, P(KdCloud), ctypes.c_int, P(KdTree)], ctypes.c_int),
+        "kd_build_batch": ([vp, vp, ctypes.c_int, vp], ctypes.c_int),
         "kd_submit": ([vp, P(KdCloud), P(KdTree), P(i64)], ctypes.c_int),
         "kd_wait": ([vp, i64, ctypes.c_int], ctypes.c_int),
         "kd_serving_stats": ([vp, P(i64), P(ctypes.c_double), P(ctypes.c_double)], ctypes.c_int),

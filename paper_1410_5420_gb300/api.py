@@ -164,24 +164,74 @@ def build_tree(ctx: Context, coords, children: bool = True, on_device: bool | No
     return kd_build(ctx, kd_presort(ctx, coords), children=children, on_device=on_device)
 
 
-def kd_build_batch(ctx: Context, clouds: list, children: bool = True, on_device: bool | None = None) -> list:
-    """kd_build_batch over a list of clouds (same k and dtype)."""
-    cs, keep = [], []
+def _np_struct(ctype) -> np.dtype:
+    """numpy dtype with the layout of a ctypes Structure of scalar fields."""
+    names, formats, offsets = [], [], []
+    conv = {ctypes.c_int: np.int32, ctypes.c_int32: np.int32, ctypes.c_int64: np.int64,
+            ctypes.c_void_p: np.uint64, ctypes.c_size_t: np.uint64}
+    for name, t in ctype._fields_:
+        names.append(name)
+        formats.append(conv[t])
+        offsets.append(getattr(ctype, name).offset)
+    return np.dtype({"names": names, "formats": formats, "offsets": offsets, "itemsize": ctypes.sizeof(ctype)})
+
+
+class BatchTrees:
+    """The trees of a batch: one output buffer per field for all clouds,
+    cloud i at offs[i] .. offs[i] + n_i; ``trees[i]`` is cloud i's dict
+    (views of the shared buffers)."""
+
+    def __init__(self, m, root, offs, arrays):
+        self.m, self.root, self.offs, self.arrays = m, root, offs, arrays
+
+    def __len__(self):
+        return len(self.m)
+
+    def __getitem__(self, i):
+        o, mi = int(self.offs[i]), int(self.m[i])
+        out = {"m": mi, "root": int(self.root[i])}
+        for key, a in self.arrays.items():
+            if a is not None:
+                out[key] = a[o:o + mi]
+        return out
+
+    def __iter__(self):
+        return (self[i] for i in range(len(self)))
+
+
+def kd_build_batch(ctx: Context, clouds: list, children: bool = True, on_device: bool | None = None) -> BatchTrees:
+    """kd_build_batch over a list of clouds (same k and dtype).  Outputs
+    live in one buffer per field (device when the first cloud is a CUDA
+    tensor, unless ``on_device`` says otherwise)."""
+    count = len(clouds)
+    cdt, tdt = _np_struct(KdCloud), _np_struct(KdTree)
+    rows, keep = [], []
+    tdts = _torch_dt() if torch is not None else {}
     for c in clouds:
-        s, kk = _cloud(c)
-        cs.append(s)
-        keep.append(kk)
-    arr_c = (KdCloud * len(cs))(*cs)
-    trees, arrays = [], []
-    for s in cs:
-        dev = bool(s.on_device) if on_device is None else on_device
-        t, a = _alloc_tree(s.n, dev, ctx.device, children)
-        trees.append(t)
-        arrays.append(a)
-    arr_t = (KdTree * len(trees))(*trees)
-    ctx.check(_lib.load().kd_build_batch(ctx.ptr, arr_c, len(cs), arr_t))
+        if torch is not None and isinstance(c, torch.Tensor) and c.dim() == 2 and c.is_contiguous() \
+                and c.dtype in tdts:
+            rows.append((c.data_ptr(), c.shape[0], c.shape[1], tdts[c.dtype], int(c.is_cuda)))
+        else:
+            s, kk = _cloud(c)
+            keep.append(kk)
+            rows.append((s.coords or 0, s.n, s.k, s.dtype, s.on_device))
+    ca = np.array(rows, dtype=cdt) if rows else np.zeros(0, dtype=cdt)
+    ns = ca["n"].astype(np.int64)
+    offs = np.zeros(count + 1, dtype=np.int64)
+    np.cumsum(ns, out=offs[1:])
+    dev = bool(ca["on_device"][0]) if on_device is None else on_device
+    tree, arrays = _alloc_tree(int(offs[-1]), dev, ctx.device, children)
+    ta = np.zeros(count, dtype=tdt)
+    ta["root"] = -1
+    for name, size in (("node_tuple", 4), ("left", 4), ("right", 4), ("dim", 1)):
+        base = getattr(tree, name)
+        if base:
+            ta[name] = np.uint64(base) + offs[:-1].astype(np.uint64) * np.uint64(size)
+    ta["on_device"] = int(dev)
+    ctx.check(_lib.load().kd_build_batch(ctx.ptr, ctypes.c_void_p(ca.ctypes.data), count,
+                                         ctypes.c_void_p(ta.ctypes.data)))
     del keep
-    return [_result(arr_t[i], arrays[i]) for i in range(len(cs))]
+    return BatchTrees(ta["m"].copy(), ta["root"].copy(), offs, arrays)
 
 
 class Ticket:

@@ -33,6 +33,7 @@ cudaError_t launch_sort_pass(int key64, const int64_t* count_ptr, int64_t max_co
                              void* key_dst, const PayloadArgs& pay, const uint32_t* digit_base, int shift,
                              uint32_t* status, int* err, cudaStream_t s);
 cudaError_t launch_digit_bases(const uint32_t* hist, int nrows, uint32_t* bases, cudaStream_t s);
+cudaError_t launch_pack_clouds(const PackDesc* d, int count, void* dst, cudaStream_t s);
 cudaError_t launch_gather(int key64, const int64_t* count_ptr, int64_t max_count, const void* plane,
                           const uint32_t* ids, void* out, int* err, cudaStream_t s);
 size_t dedup_scratch_words(int64_t n);
@@ -287,6 +288,16 @@ kd_status ensure_copy_stream(kd_ctx* ctx, size_t nev) {
     return KD_OK;
 }
 
+// Page-locked host memory (copies from and to it run asynchronously).
+bool pinned_host(const void* p) {
+    cudaPointerAttributes a{};
+    if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
 kd_status check_device_err(kd_ctx* ctx, int* d_err) {
     int err = 0;
     CK(cudaMemcpyAsync(&err, d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
@@ -407,9 +418,10 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
     Scratch S(ctx);
     // coordinates on the device, clouds back to back
     const void* coords = nullptr;
-    // a single cloud on the host is uploaded in chunks on the copy stream,
+    // a single cloud in page-locked host memory is uploaded in chunks on the copy stream,
     // each transformed as soon as it has arrived
-    const int up_chunks = (count == 1 && !clouds[0].on_device && N >= (1 << 20)) ? 8 : 1;
+    const int up_chunks =
+        (count == 1 && !clouds[0].on_device && N >= (1 << 20) && pinned_host(clouds[0].coords)) ? 8 : 1;
     if (count == 1 && clouds[0].on_device) {
         coords = clouds[0].coords;
     } else if (up_chunks > 1) {
@@ -419,12 +431,26 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
     } else {
         unsigned char* cb = nullptr;
         CKS(S.get(&cb, (size_t)N * k * tsz));
-        for (int i = 0; i < count; ++i)
-            if (clouds[i].n)
-                CK(cudaMemcpyAsync(cb + (size_t)H->in_off[i] * k * tsz, clouds[i].coords,
-                                   (size_t)clouds[i].n * k * tsz,
-                                   clouds[i].on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-        coords = cb;
+        // device clouds: one packing kernel over a descriptor table; host
+        // clouds: one copy each
+        std::vector<PackDesc> pk;
+        for (int i = 0; i < count; ++i) {
+            if (!clouds[i].n) continue;
+            const size_t bytes = (size_t)clouds[i].n * k * tsz;
+            if (clouds[i].on_device)
+                pk.push_back(PackDesc{clouds[i].coords, (int64_t)(bytes / 4), (int64_t)(H->in_off[i] * k * tsz / 4)});
+            else
+                CK(cudaMemcpyAsync(cb + (size_t)H->in_off[i] * k * tsz, clouds[i].coords, bytes,
+                                   cudaMemcpyHostToDevice, s));
+        }
+        if (!pk.empty()) {
+            PackDesc* d_pk = nullptr;
+            CKS(S.get(&d_pk, pk.size() * sizeof(PackDesc)));
+            CK(cudaMemcpyAsync(d_pk, pk.data(), pk.size() * sizeof(PackDesc), cudaMemcpyHostToDevice, s));
+            LaunchTimer lt(ctx, F_OTHER, 0.0);
+            CK(launch_pack_clouds(d_pk, (int)pk.size(), cb, s));
+        }
+        coords = cb;  // (a copy from pageable memory has read pk by the time it returns)
     }
     unsigned char* keys = nullptr;
     uint32_t *cloud_plane = nullptr, *hist = nullptr;
@@ -994,11 +1020,14 @@ kd_status build_batch(kd_ctx* ctx, kd_presorted* H, kd_tree* outs) {
         CK(launch_level_pass(k, bufs, step_q[st], d_jobs + job_off[st], (int)step_jobs[st].size(),
                              (int)step_ntiles[st], d_cd, medr, H->perm0, d_status, d_err, s));
     }
-    // A single cloud with host outputs: the finisher runs in chunks of
+    // A single cloud with page-locked host outputs: the finisher runs in chunks of
     // units and each chunk's address range (which also holds the nodes
     // above the finisher level between its units, final by now) is copied
     // to the host on a second stream while the next chunk runs.
-    const bool overlap_copy = any_host && count == 1 && nunits >= 64 && !(ctx->debug & 4) && !outs[0].on_device;
+    const bool overlap_copy = any_host && count == 1 && nunits >= 64 && !(ctx->debug & 4) && !outs[0].on_device &&
+                              pinned_host(outs[0].node_tuple) && (!outs[0].left || pinned_host(outs[0].left)) &&
+                              (!outs[0].right || pinned_host(outs[0].right)) &&
+                              (!outs[0].dim || pinned_host(outs[0].dim));
     const int nchunks = overlap_copy ? 8 : 1;
     if (overlap_copy) CKS(ensure_copy_stream(ctx, nchunks + 1));
     if (nunits > 0) {

@@ -450,6 +450,13 @@ struct PayloadArgs {
 
 enum KeyMode { KEY_DIRECT = 0, KEY_GATHER = 1, KEY_BUF = 2 };
 
+// One device cloud's coordinates to be packed into a batch's buffer.
+struct PackDesc {
+    const void* src;
+    int64_t words;     // 32-bit words
+    int64_t dst_word;  // first destination word
+};
+
 // Per-cloud facts the build kernels need (one entry per cloud of a batch).
 struct CloudDev {
     int64_t off;        // first position of the cloud in the batched arrays

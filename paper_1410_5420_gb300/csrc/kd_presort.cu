@@ -737,6 +737,23 @@ static int grid_for(int64_t work, int per_block, int cap) {
 // 64-bit keys plus 2 cloud-id digit rows, and the 256-point coordinate tile.
 constexpr size_t TRANSFORM_SMEM_MAX = (size_t)(MAXK * 8 + 4) * RADIX * 4 + 256 * MAXK * 8;
 
+// Concatenation of device clouds: block b copies the 32-bit words of the
+// clouds whose descriptors it strides over (src, words, destination word).
+__global__ void __launch_bounds__(256) k_pack_clouds(const PackDesc* __restrict__ d, int count,
+                                                     uint32_t* __restrict__ dst) {
+    for (int c = blockIdx.x; c < count; c += gridDim.x) {
+        const PackDesc e = d[c];
+        const uint32_t* src = static_cast<const uint32_t*>(e.src);
+        for (int64_t i = threadIdx.x; i < e.words; i += 256) dst[e.dst_word + i] = src[i];
+    }
+}
+
+cudaError_t launch_pack_clouds(const PackDesc* d, int count, void* dst, cudaStream_t s) {
+    if (count == 0) return cudaSuccess;
+    k_pack_clouds<<<std::min(count, 152 * 16), 256, 0, s>>>(d, count, static_cast<uint32_t*>(dst));
+    return cudaGetLastError();
+}
+
 cudaError_t launch_transform(int dtype, const void* coords, int64_t n, int k, void* keys, int64_t stride, void* tail,
                              const int64_t* cloud_start, int ncloud, uint32_t* cloud_plane,
                              int cloud_digits, uint32_t* hist, int* err, cudaStream_t s) {

@@ -569,18 +569,35 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
     auto plane64 = [&](int plane) { return plane >= 0 ? key64 : 0; };
 
     // S_0: ids by super key 0 (all n tuples) ----------------------------
+    // With 32-bit keys, the passes of plane k-1 carry plane k-2 along as a
+    // second payload, so that plane k-2's first pass reads its keys in order
+    // instead of gathering them at random (a gather reads a few 32-byte
+    // sectors per 4-byte key; the carry adds 8 streamed bytes per pass).
+    const int carry_plane = (k >= 2 && !key64) ? k - 2 : -1;
+    int cy = 0;                       // carried plane: current ping-pong buffer
+    const uint32_t* carried = nullptr;  // plane k-2 in the current order, once carried
     int kc = 0, ic = 0;  // current key / id buffer
     for (size_t i = 0; i < s0.size(); ++i) {
         const Pass& P = s0[i];
         const bool last = i + 1 == s0.size();
+        const bool carry = carry_plane >= 0 && P.plane == k - 1;
+        const bool from_carry = carry_plane >= 0 && P.plane == carry_plane && P.mode == KEY_GATHER;
         const bool next_gathers = !last && s0[i + 1].mode != KEY_BUF;
         PayloadArgs pay{};
         pay.n = 1;
         pay.src[0] = P.mode == KEY_DIRECT ? nullptr : ibuf[ic];
         pay.dst[0] = ibuf[ic ^ 1];
+        if (carry) {
+            pay.n = 2;
+            pay.src[1] = P.mode == KEY_DIRECT ? (const uint32_t*)plane_ptr(carry_plane) : pbuf[cy][0];
+            pay.dst[1] = pbuf[cy ^ 1][0];
+        }
         const void* ksrc = P.mode == KEY_BUF ? (const void*)kbuf[kc] : plane_ptr(P.plane);
         void* kdst = next_gathers ? nullptr : (void*)kbuf[kc ^ 1];
-        if (P.mode == KEY_GATHER) {  // gather the new plane's keys into order first
+        if (from_carry) {
+            if (!carried) return fail(ctx, KD_EINVAL, "internal: carried plane missing");
+            ksrc = carried;
+        } else if (P.mode == KEY_GATHER) {  // gather the new plane's keys into order first
             LaunchTimer lg(ctx, F_GATHER, (double)N, nullptr, 4.0 + 2.0 * P.w);
             CK(launch_gather(plane64(P.plane), d_n, N, plane_ptr(P.plane), ibuf[ic], kbuf[kc], d_err, s));
             ksrc = kbuf[kc];
@@ -591,6 +608,10 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
                             bases_all + (size_t)row_of(P.plane, P.digit) * RADIX, 8 * P.digit, status, d_err, s));
         kc ^= 1;
         ic ^= 1;
+        if (carry) {
+            cy ^= 1;
+            carried = pbuf[cy][0];
+        }
     }
     // dedup ---------------------------------------------------------------
     uint32_t* dedup_out = count == 1 ? H->perm0 : ibuf[ic ^ 1];

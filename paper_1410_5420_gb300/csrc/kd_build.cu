@@ -404,10 +404,11 @@ __global__ void __launch_bounds__(LEVEL_BLOCK)
 
 // Segmented inclusive scan over the tiles of a level step, one block per
 // bucket: incl[t][b] = cnt[t][b] + (head[t] ? 0 : incl[t-1][b]) (row stride
-// `stride`).  Each thread scans LS_V consecutive tiles, then the threads'
-// aggregates are scanned across the block; a chunk of 1024 * LS_V tiles per
-// iteration, carried into the next.
-constexpr int LS_V = 8;
+// `stride`).  Each thread loads LS_V consecutive tiles at once (all loads in
+// flight together) and scans them in registers, then the threads'
+// (flag, value) aggregates are scanned across the block; a chunk of
+// 1024 * LS_V tiles per iteration, carried into the next.
+constexpr int LS_V = 16;
 __global__ void __launch_bounds__(1024) k_level_scan(int ntiles, int stride, const uint32_t* __restrict__ cnt,
                                                      const uint32_t* __restrict__ head, uint32_t* __restrict__ incl) {
     __shared__ uint32_t s_f[32], s_v[32];
@@ -416,21 +417,36 @@ __global__ void __launch_bounds__(1024) k_level_scan(int ntiles, int stride, con
     uint32_t carry = 0;
     for (int t0 = 0; t0 < ntiles; t0 += 1024 * LS_V) {
         const int tb = t0 + tid * LS_V;
-        uint32_t lf[LS_V], lv[LS_V];
+        uint32_t lv[LS_V];
+        uint32_t hf = 0;  // bit e: tile tb + e starts a segment (tiles past the end count as heads)
+        if (tb + LS_V <= ntiles) {
+            const uint4* h4 = reinterpret_cast<const uint4*>(head + tb);  // tb is a multiple of LS_V
+#pragma unroll
+            for (int e = 0; e < LS_V / 4; ++e) {
+                const uint4 h = h4[e];
+                hf |= ((h.x != 0u) ? 1u : 0u) << (4 * e);
+                hf |= ((h.y != 0u) ? 1u : 0u) << (4 * e + 1);
+                hf |= ((h.z != 0u) ? 1u : 0u) << (4 * e + 2);
+                hf |= ((h.w != 0u) ? 1u : 0u) << (4 * e + 3);
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < LS_V; ++e) {
+                const int t = tb + e;
+                hf |= ((t >= ntiles || head[t] != 0u) ? 1u : 0u) << e;
+            }
+        }
 #pragma unroll
         for (int e = 0; e < LS_V; ++e) {
             const int t = tb + e;
-            lf[e] = t < ntiles ? head[t] : 1u;
             lv[e] = t < ntiles ? cnt[(int64_t)t * stride + b] : 0u;
         }
         // inclusive within the thread: a head starts a new segment
 #pragma unroll
-        for (int e = 1; e < LS_V; ++e) {
-            if (!lf[e]) lv[e] += lv[e - 1];
-            lf[e] |= lf[e - 1];
-        }
+        for (int e = 1; e < LS_V; ++e)
+            if (!((hf >> e) & 1u)) lv[e] += lv[e - 1];
         // (flag, value) pairs of the threads: inclusive scan within the warp
-        uint32_t xf = lf[LS_V - 1], xv = lv[LS_V - 1];
+        uint32_t xf = hf != 0u ? 1u : 0u, xv = lv[LS_V - 1];
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t yf = __shfl_up_sync(0xffffffffu, xf, o);
@@ -472,7 +488,9 @@ __global__ void __launch_bounds__(1024) k_level_scan(int ntiles, int stride, con
 #pragma unroll
         for (int e = 0; e < LS_V; ++e) {
             const int t = tb + e;
-            if (t < ntiles) incl[(int64_t)t * stride + b] = lf[e] ? lv[e] : xv0 + lv[e];
+            // a head at or before e inside this thread cuts the carried prefix
+            const bool cut = (hf << (31 - e)) != 0u;
+            if (t < ntiles) incl[(int64_t)t * stride + b] = cut ? lv[e] : xv0 + lv[e];
         }
         carry = s_f[31] ? s_v[31] : carry + s_v[31];
         __syncthreads();

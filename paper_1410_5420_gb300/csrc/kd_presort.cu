@@ -177,9 +177,13 @@ __global__ void __launch_bounds__(256) k_rs_scan(const int64_t* __restrict__ cou
     if (c >= nchunks) return;
     const int64_t t0 = c * RS_CHUNK;
     const int64_t t1 = t0 + RS_CHUNK < ntiles ? t0 + RS_CHUNK : ntiles;
+    // the chunk's counts of digit tid, all loads in flight together
+    uint32_t v[RS_CHUNK];
     uint32_t sum = 0;
-#pragma unroll 8
-    for (int64_t t = t0; t < t1; ++t) sum += cnt[t * RADIX + tid];
+#pragma unroll
+    for (int j = 0; j < RS_CHUNK; ++j) v[j] = t0 + j < t1 ? cnt[(t0 + j) * RADIX + tid] : 0u;
+#pragma unroll
+    for (int j = 0; j < RS_CHUNK; ++j) sum += v[j];
     if (c == 0) inc[tid] = sum;
     else agg[c * RADIX + tid] = sum;
     __syncthreads();
@@ -192,10 +196,10 @@ __global__ void __launch_bounds__(256) k_rs_scan(const int64_t* __restrict__ cou
         if (tid == 0) publish_flag(flags, c, FLAG_INC);
     }
     uint32_t run = digit_base[tid] + excl;
-    for (int64_t t = t0; t < t1; ++t) {
-        const uint32_t v = cnt[t * RADIX + tid];
-        offs[t * RADIX + tid] = run;
-        run += v;
+#pragma unroll
+    for (int j = 0; j < RS_CHUNK; ++j) {
+        if (t0 + j < t1) offs[(t0 + j) * RADIX + tid] = run;
+        run += v[j];
     }
 }
 

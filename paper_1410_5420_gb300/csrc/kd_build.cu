@@ -12,7 +12,7 @@
 //                 (its halves are in place); the pass then applies the
 //                 splits of levels L+1..L+k-1, whose medians come from the
 //                 arrays that were primary there, as a stable 2^(k-1)-way
-//                 segmented multisplit (warp ballot ranking, smem-staged
+//                 segmented multisplit (warp match ranking, smem-staged
 //                 coalesced scatter).  The counts of a segment's elements in
 //                 earlier tiles come from a count pass (k_level_count, which
 //                 reads only the decision planes) and a segmented scan over
@@ -526,7 +526,6 @@ __global__ void __launch_bounds__(LEVEL_BLOCK, K <= 3 ? 3 : 2)
     constexpr int NBP = level_nbp(K);
     constexpr int TW = trec_words(K);
     constexpr int SW = TW + NBP + K * PST;
-    constexpr int DBITS = 2 + (K - 1) + 1;  // enough for digits 0 .. LEVEL_NSMAX * NBMAX (the marker)
     extern __shared__ __align__(128) uint32_t lsm[];
     __shared__ __align__(8) uint64_t full[LEVEL_STAGES], empty[LEVEL_STAGES];
     __shared__ StageMeta meta[LEVEL_STAGES];
@@ -567,14 +566,13 @@ __global__ void __launch_bounds__(LEVEL_BLOCK, K <= 3 ? 3 : 2)
         const int F = M.F;
         const int NB = 1 << F;
         const uint32_t marker = (uint32_t)(ns * NB);
-        const int nbits = 32 - __clz(marker);
         const int own = q != 0 ? (q - M.lev_in % K + K) % K : -1;  // slot of the array's own plane: not carried
         uint32_t v[K][IPT];
         uint32_t dig[IPT];
         uint32_t rank[IPT];
         if (ns == 1 && F == K - 1) {
             // one segment and every decision level: compile-time routing and
-            // K ballot bits (buckets 0 .. NB-1, marker NB)
+            // (buckets 0 .. NB-1, marker NB)
             uint32_t mh[K <= 4 ? NBMAX : 1];
             if constexpr (K <= 4) {
 #pragma unroll
@@ -604,7 +602,7 @@ __global__ void __launch_bounds__(LEVEL_BLOCK, K <= 3 ? 3 : 2)
                     }
                 }
             }
-            warp_rank<IPT, K>(dig, marker, K, s_wc[warp], rank);
+            warp_rank<IPT>(dig, marker, s_wc[warp], rank);
         } else {
 #pragma unroll
             for (int j = 0; j < IPT; ++j) {
@@ -625,7 +623,7 @@ __global__ void __launch_bounds__(LEVEL_BLOCK, K <= 3 ? 3 : 2)
                     }
                 }
             }
-            warp_rank<IPT, DBITS>(dig, marker, nbits, s_wc[warp], rank);
+            warp_rank<IPT>(dig, marker, s_wc[warp], rank);
         }
         consumer_sync<LEVEL_THREADS>();
         // per digit: prefix over warps; base, bounds and middle of its final
@@ -749,8 +747,7 @@ __device__ __forceinline__ void fin_label_rank(const uint16_t* __restrict__ A, i
         const uint32_t x = i < S ? lab[lid[j]] : LAB_DONE;
         dig[j] = x == LAB_DONE ? marker : x;
     }
-    constexpr int MAXB = 32 - __builtin_clz((unsigned)fin_labels(SMAX));  // bits of the marker
-    warp_rank<IPT, MAXB>(dig, marker, l + 1, s_wc[warp], rank);
+    warp_rank<IPT>(dig, marker, s_wc[warp], rank);
     __syncthreads();
     for (int X = tid; X < (int)marker; X += FIN_THREADS) {
         uint32_t c = 0;

@@ -532,23 +532,16 @@ __device__ __forceinline__ LevelTile job_tile(const LevelJob* __restrict__ jobs,
 }
 
 // Stable warp ranking of digits below `marker` (the marker: no element):
-// lanes with equal digits from ballots over the low `nbits` <= MAXBITS digit
-// bits; the lowest such lane advances the warp's counter of the digit.
-template <int IPT, int MAXBITS>
-__device__ __forceinline__ void warp_rank(const uint32_t (&dig)[IPT], uint32_t marker, int nbits,
-                                          uint32_t* __restrict__ wc, uint32_t (&rank)[IPT]) {
+// the lanes holding an equal digit come from one match instruction; the
+// lowest of them advances the warp's counter of the digit.
+template <int IPT>
+__device__ __forceinline__ void warp_rank(const uint32_t (&dig)[IPT], uint32_t marker, uint32_t* __restrict__ wc,
+                                          uint32_t (&rank)[IPT]) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int j = 0; j < IPT; ++j) {
         const uint32_t d = dig[j];
-        uint32_t peers = 0xffffffffu;
-#pragma unroll
-        for (int bit = 0; bit < MAXBITS; ++bit) {
-            if (bit < nbits) {
-                const uint32_t bb = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
-                peers &= ((d >> bit) & 1u) ? bb : ~bb;
-            }
-        }
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
         const int leader = __ffs(peers) - 1;
         uint32_t old = 0;
         if (lane == leader && d < marker) old = atomicAdd(&wc[d], (uint32_t)__popc(peers));
@@ -557,32 +550,60 @@ __device__ __forceinline__ void warp_rank(const uint32_t (&dig)[IPT], uint32_t m
     }
 }
 
-// Stable warp ranking through shared-memory match words (digits below
-// `marker`; the marker: no element).  Each lane ORs its bit into its
-// digit's word, reads back the lanes sharing its digit, and the highest of
-// them advances the warp's counter of the digit (wc) and clears the word,
-// so `match` is all zero between calls.
+// Stable warp ranking that picks its method per call: the first key is
+// ranked with a match instruction, and the number of distinct digits among
+// the warp's 32 first keys decides the rest.  Few distinct digits (long
+// runs, as in the top bytes of clustered coordinates) stay with the match
+// instruction; many go through shared-memory match words: each lane ORs its
+// bit into its digit's word, reads back the lanes sharing its digit, and
+// the highest of them advances the warp's counter of the digit and clears
+// the word, so `match` is all zero between calls.  Both leave the same
+// per-warp counts in wc.  Digits below `marker` (the marker: no element).
+#ifndef KD_RANK_DISTINCT
+#define KD_RANK_DISTINCT 16
+#endif
 template <int IPT>
-__device__ __forceinline__ void warp_rank_words(const uint32_t (&dig)[IPT], uint32_t marker, uint32_t* __restrict__ wc,
-                                                uint32_t* __restrict__ match, uint32_t (&rank)[IPT]) {
+__device__ __forceinline__ void warp_rank_adaptive(const uint32_t (&dig)[IPT], uint32_t marker,
+                                                   uint32_t* __restrict__ wc, uint32_t* __restrict__ match,
+                                                   uint32_t (&rank)[IPT]) {
     const int lane = threadIdx.x & 31;
+    const uint32_t lt = lanemask_lt();
+    uint32_t peers = __match_any_sync(0xffffffffu, dig[0]);
+    int leader = __ffs(peers) - 1;
+    uint32_t old = 0;
+    if (lane == leader && dig[0] < marker) old = atomicAdd(&wc[dig[0]], (uint32_t)__popc(peers));
+    rank[0] = __shfl_sync(0xffffffffu, old, leader) + __popc(peers & lt);
+    const int distinct = __popc(__ballot_sync(0xffffffffu, lane == leader));
+    if (distinct <= KD_RANK_DISTINCT) {
 #pragma unroll
-    for (int j = 0; j < IPT; ++j) {
-        const uint32_t d = dig[j];
-        if (d < marker) atomicOr(&match[d], 1u << lane);
-        __syncwarp();
-        const uint32_t peers = d < marker ? match[d] : (1u << lane);
-        __syncwarp();
-        const int leader = 31 - __clz(peers);
-        uint32_t old = 0;
-        if (lane == leader && d < marker) {
-            old = wc[d];
-            wc[d] = old + (uint32_t)__popc(peers);
-            match[d] = 0;
+        for (int j = 1; j < IPT; ++j) {
+            const uint32_t d = dig[j];
+            peers = __match_any_sync(0xffffffffu, d);
+            leader = __ffs(peers) - 1;
+            old = 0;
+            if (lane == leader && d < marker) old = atomicAdd(&wc[d], (uint32_t)__popc(peers));
+            rank[j] = __shfl_sync(0xffffffffu, old, leader) + __popc(peers & lt);
         }
+    } else {
         __syncwarp();
-        old = __shfl_sync(0xffffffffu, old, leader);
-        rank[j] = old + __popc(peers & lanemask_lt());
+#pragma unroll
+        for (int j = 1; j < IPT; ++j) {
+            const uint32_t d = dig[j];
+            if (d < marker) atomicOr(&match[d], 1u << lane);
+            __syncwarp();
+            const uint32_t pw = d < marker ? match[d] : (1u << lane);
+            __syncwarp();
+            const int ld = 31 - __clz(pw);
+            uint32_t o = 0;
+            if (lane == ld && d < marker) {
+                o = wc[d];
+                wc[d] = o + (uint32_t)__popc(pw);
+                match[d] = 0;
+            }
+            __syncwarp();
+            o = __shfl_sync(0xffffffffu, o, ld);
+            rank[j] = o + __popc(pw & lt);
+        }
     }
 }
 

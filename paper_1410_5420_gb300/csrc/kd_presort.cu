@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(RS_BLOCK, TILE * (SP + 1) * sizeof(KW) <= 2048
             const int o = wbase + j * 32 + lane;
             dig[j] = o < M.n ? digit_of(skeys[o], shift) : (uint32_t)RADIX;
         }
-        warp_rank_words<IPT>(dig, RADIX, s_wc[warp], s_match[warp], slot);
+        warp_rank_adaptive<IPT>(dig, RADIX, s_wc[warp], s_match[warp], slot);
         consumer_sync<RS_THREADS>();
         // digit tid: prefix over warps in place, tile count, tile start
         uint32_t c = 0;

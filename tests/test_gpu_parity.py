@@ -108,6 +108,18 @@ def test_small_switch_threshold_runs_many_level_passes(cuda_lib, k):
         ctx.close()
 
 
+@pytest.mark.parametrize("k,threshold", [(2, 4096), (3, 4096), (4, 2048), (3, 1024), (8, 1024)])
+def test_each_on_chip_subtree_size(cuda_lib, k, threshold):
+    """Every on-chip subtree capacity (1024, 2048, 4096 tuples) finishes the
+    same tree, including ragged units and narrow integers with ties."""
+    ctx = cuda_lib.kd_create(0, switch_threshold=threshold)
+    try:
+        coords = kdgen.cloud_int_uniform(50000 + 11 * k, k, 12, 3000 + k, np.int64, dup_frac=0.01)
+        assert_same_tree(gpu_tree(cuda_lib, ctx, coords), oracle.build_tree(coords))
+    finally:
+        ctx.close()
+
+
 def test_small_workload_bit_exact(cuda_lib, ctx):
     coords = kdgen.small_int64()  # n=16384, k=3, int64 in [0, 2^20), 1% duplicates
     ref = oracle.build_tree(coords)

@@ -76,10 +76,11 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 }
 __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
+    // suspend for up to 1 us per poll while the phase is incomplete
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(1000u)
         : "memory");
     return ok != 0;
 }
@@ -103,7 +104,7 @@ __device__ __forceinline__ bool consumer_or(bool v) {
     return r != 0;
 }
 // Wait for phase `parity` of an mbarrier to complete; false after
-// SPIN_LIMIT polls (each poll may itself block for a bounded time).
+// SPIN_LIMIT polls (each poll suspends for at most 1 us: about 17 s in all).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     for (uint32_t spins = 0; spins < SPIN_LIMIT; ++spins)
         if (mbar_test(bar, parity)) return true;

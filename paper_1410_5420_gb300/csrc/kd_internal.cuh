@@ -21,14 +21,8 @@ constexpr int ERR_NAN = 1;
 constexpr int ERR_TIMEOUT = 2;
 constexpr int ERR_INTERNAL = 4;
 
-// Decoupled look-back status word: 2 flag bits above a 30-bit count.
-constexpr uint32_t ST_AGG = 1u << 30;
-constexpr uint32_t ST_INC = 2u << 30;
-constexpr uint32_t ST_FLAGS = 3u << 30;
-constexpr uint32_t ST_COUNT = (1u << 30) - 1;
-
-// Spin limit of a look-back wait.  A predecessor tile took its tile id (and
-// so was already running) before the waiter did, so the wait normally ends
+// Poll limit of every wait (look-back flags, mbarriers).  The awaited block
+// or copy was already running when the wait began, so a wait normally ends
 // within microseconds; the bound only keeps a fault from hanging the GPU.
 constexpr uint32_t SPIN_LIMIT = 1u << 24;
 
@@ -111,50 +105,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     return false;
 }
 
-// Walk back from tile `tile - 1` over the status words (stride `stride`
-// words per tile, word `slot` of each) until an inclusive prefix is found;
-// returns the sum of everything before `tile`.  A window of W predecessor
-// words is loaded at once (independent loads), so a walk over many tiles
-// that have only published their aggregates costs one memory round trip per
-// W tiles.  Sets ERR_TIMEOUT and returns what it has if the wait for a
-// not-yet-published word exceeds SPIN_LIMIT polls.
-template <int W>
-__device__ __forceinline__ uint32_t lookback(const uint32_t* status, int64_t tile, int stride, int slot,
-                                             int* err) {
-    uint32_t excl = 0;
-    int64_t t = tile - 1;
-    uint32_t spins = 0;
-    while (t >= 0) {
-        uint32_t s[W];
-#pragma unroll
-        for (int w = 0; w < W; ++w) s[w] = (t - w >= 0) ? ld_volatile(status + (t - w) * stride + slot) : ST_INC;
-        int used = 0;
-        bool done = false, stalled = false;
-#pragma unroll
-        for (int w = 0; w < W; ++w) {
-            if (!done && !stalled) {
-                if ((s[w] & ST_FLAGS) == 0) {
-                    stalled = true;
-                } else {
-                    excl += s[w] & ST_COUNT;
-                    ++used;
-                    if ((s[w] & ST_FLAGS) == ST_INC) done = true;
-                }
-            }
-        }
-        if (done) break;
-        t -= used;
-        if (stalled) {
-            if (++spins > SPIN_LIMIT) {
-                atomicOr(err, ERR_TIMEOUT);
-                break;
-            }
-            __nanosleep(32);
-        }
-    }
-    return excl;
-}
-
 // Exclusive scan of one value per thread over a 256-thread block; *total
 // (if not null) receives the block sum.  s_warp holds 8 words.
 __device__ __forceinline__ uint32_t block_excl_scan256(uint32_t v, uint32_t* s_warp, uint32_t* total) {
@@ -180,112 +130,6 @@ __device__ __forceinline__ uint32_t block_excl_scan256(uint32_t v, uint32_t* s_w
     uint32_t excl = x - v + (warp > 0 ? s_warp[warp - 1] : 0u);
     if (total) *total = s_warp[7];
     __syncthreads();
-    return excl;
-}
-
-// Vector look-backs over slot-major status rows (row[tile], rows padded to
-// a multiple of 4 tiles and 16-byte aligned), so one 16-byte load reads 4
-// consecutive tiles' words.
-__device__ __forceinline__ uint4 ld_volatile_v4(const uint32_t* p) {
-    uint4 v;
-    asm volatile("ld.volatile.global.v4.u32 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-                 : "l"(p));
-    return v;
-}
-__device__ __forceinline__ uint32_t v4_get(const uint4& v, int e) {
-    return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
-}
-
-// One thread per slot: walk back from tile-1 reading 4*NV predecessor words
-// per round trip.  Returns the sum of the slot's counts over all earlier
-// tiles.  Bounded wait as lookback().
-template <int NV>
-__device__ __forceinline__ uint32_t lookback_row(const uint32_t* row, int64_t tile, int* err) {
-    uint32_t excl = 0;
-    int64_t hi = tile - 1;
-    uint32_t spins = 0;
-    while (hi >= 0) {
-        const int64_t c0 = hi >> 2;
-        uint4 v[NV];
-#pragma unroll
-        for (int i = 0; i < NV; ++i)
-            v[i] = (c0 - i >= 0) ? ld_volatile_v4(row + 4 * (c0 - i)) : make_uint4(ST_INC, ST_INC, ST_INC, ST_INC);
-        bool done = false, stalled = false;
-        int64_t next = 4 * (c0 - NV + 1) - 1;
-#pragma unroll
-        for (int i = 0; i < NV; ++i) {
-#pragma unroll
-            for (int e = 3; e >= 0; --e) {
-                const int64_t te = 4 * (c0 - i) + e;
-                if (done || stalled || te > hi) continue;
-                const uint32_t w = v4_get(v[i], e);
-                if ((w & ST_FLAGS) == 0) {
-                    stalled = true;
-                    next = te;
-                } else {
-                    excl += w & ST_COUNT;
-                    if ((w & ST_FLAGS) == ST_INC) done = true;
-                }
-            }
-        }
-        if (done) break;
-        hi = next;
-        if (stalled) {
-            if (++spins > SPIN_LIMIT) {
-                atomicOr(err, ERR_TIMEOUT);
-                break;
-            }
-            __nanosleep(32);
-        }
-    }
-    return excl;
-}
-
-// A whole warp walks back one slot's row: lane l reads the 4 tiles of chunk
-// (hi/4 - l), so one round trip covers 128 predecessors.  Every lane returns
-// the same sum.  Bounded wait as lookback().
-__device__ __forceinline__ uint32_t warp_lookback_row(const uint32_t* row, int64_t tile, int* err) {
-    const int lane = threadIdx.x & 31;
-    uint32_t excl = 0;
-    int64_t hi = tile - 1;
-    uint32_t spins = 0;
-    while (hi >= 0) {
-        const int64_t c = (hi >> 2) - lane;
-        const uint4 v = c >= 0 ? ld_volatile_v4(row + 4 * c) : make_uint4(ST_INC, ST_INC, ST_INC, ST_INC);
-        uint32_t sum = 0;
-        bool inc = false, notready = false;
-#pragma unroll
-        for (int e = 3; e >= 0; --e) {
-            const int64_t te = 4 * c + e;
-            if (te > hi || inc || notready) continue;
-            const uint32_t w = v4_get(v, e);
-            if ((w & ST_FLAGS) == 0) {
-                notready = true;
-            } else {
-                sum += w & ST_COUNT;
-                if ((w & ST_FLAGS) == ST_INC) inc = true;
-            }
-        }
-        const uint32_t binc = __ballot_sync(0xffffffffu, inc);
-        const uint32_t bnr = __ballot_sync(0xffffffffu, notready);
-        const int L = binc ? __ffs(binc) - 1 : 32;  // nearest lane holding an inclusive prefix
-        const uint32_t upto = L >= 31 ? 0xffffffffu : ((2u << L) - 1u);
-        if (bnr & upto) {  // a word between us and that prefix is not published yet
-            if (++spins > SPIN_LIMIT) {
-                if (lane == 0) atomicOr(err, ERR_TIMEOUT);
-                break;
-            }
-            __nanosleep(32);
-            continue;
-        }
-        uint32_t part = (lane <= L) ? sum : 0u;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-        excl += part;
-        if (L < 32) break;
-        hi = 4 * ((hi >> 2) - 31) - 1;
-    }
     return excl;
 }
 

@@ -101,11 +101,15 @@ template <int K>
 __global__ void __launch_bounds__(256) k_level_tiles(const LevelJob* __restrict__ jobs, int njobs, int ntiles,
                                                      const CloudDev* __restrict__ clouds,
                                                      const uint32_t* __restrict__ medr, uint32_t* __restrict__ trec,
-                                                     uint32_t* __restrict__ ctrs, int* __restrict__ err) {
+                                                     uint32_t* __restrict__ ctrs, uint32_t* __restrict__ scan_flags,
+                                                     int nflags, int* __restrict__ err) {
     constexpr int NBMAX = 1 << (K - 1);
     constexpr int TW = trec_words(K);
     constexpr int TILE = level_tile_of(K);
-    if (blockIdx.x == 0 && threadIdx.x < 2) ctrs[threadIdx.x] = 0;  // tile counters of the two passes
+    if (blockIdx.x == 0) {
+        if (threadIdx.x < 3) ctrs[threadIdx.x] = 0;  // tile counters of the two passes, scan ticket
+        for (int i = threadIdx.x; i < nflags; i += blockDim.x) scan_flags[i] = 0;
+    }
     const int lane = threadIdx.x & 31;
     const int t = blockIdx.x * 8 + (threadIdx.x >> 5);
     if (t >= ntiles) return;
@@ -402,98 +406,127 @@ __global__ void __launch_bounds__(LEVEL_BLOCK)
     }
 }
 
-// Segmented inclusive scan over the tiles of a level step, one block per
-// bucket: incl[t][b] = cnt[t][b] + (head[t] ? 0 : incl[t-1][b]) (row stride
-// `stride`).  Each thread loads LS_V consecutive tiles at once (all loads in
-// flight together) and scans them in registers, then the threads'
-// (flag, value) aggregates are scanned across the block; a chunk of
-// 1024 * LS_V tiles per iteration, carried into the next.
-constexpr int LS_V = 16;
-__global__ void __launch_bounds__(1024) k_level_scan(int ntiles, int stride, const uint32_t* __restrict__ cnt,
-                                                     const uint32_t* __restrict__ head, uint32_t* __restrict__ incl) {
+// Segmented inclusive scan over the tiles of a level step:
+// incl[t][b] = cnt[t][b] + (head[t] ? 0 : incl[t-1][b]) (row stride
+// `stride`), one block per (chunk of LS_CHUNK tiles, bucket b), ids taken
+// in launch order from a ticket.  Each thread loads LS_V consecutive tiles
+// at once and scans them in registers; the threads' (flag, value) pairs are
+// scanned across the block; a chunk then publishes what it carries out
+// (inclusive at once when it holds a head) and takes what comes in by a
+// decoupled look-back over the earlier chunks of its bucket.
+constexpr int LS_V = 4;
+constexpr int LS_CHUNK = 1024 * LS_V;
+__host__ __device__ __forceinline__ int level_scan_chunks(int ntiles) { return (ntiles + LS_CHUNK - 1) / LS_CHUNK; }
+
+__global__ void __launch_bounds__(1024) k_level_scan(int ntiles, int ncol, int stride, const uint32_t* __restrict__ cnt,
+                                                     const uint32_t* __restrict__ head, uint32_t* __restrict__ incl,
+                                                     uint32_t* __restrict__ lb, uint32_t* __restrict__ ticket,
+                                                     int* __restrict__ err) {
     __shared__ uint32_t s_f[32], s_v[32];
-    const int b = blockIdx.x;
+    __shared__ uint32_t s_ctl, s_id, s_carry;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    uint32_t carry = 0;
-    for (int t0 = 0; t0 < ntiles; t0 += 1024 * LS_V) {
-        const int tb = t0 + tid * LS_V;
-        uint32_t lv[LS_V];
-        uint32_t hf = 0;  // bit e: tile tb + e starts a segment (tiles past the end count as heads)
-        if (tb + LS_V <= ntiles) {
-            const uint4* h4 = reinterpret_cast<const uint4*>(head + tb);  // tb is a multiple of LS_V
-#pragma unroll
-            for (int e = 0; e < LS_V / 4; ++e) {
-                const uint4 h = h4[e];
-                hf |= ((h.x != 0u) ? 1u : 0u) << (4 * e);
-                hf |= ((h.y != 0u) ? 1u : 0u) << (4 * e + 1);
-                hf |= ((h.z != 0u) ? 1u : 0u) << (4 * e + 2);
-                hf |= ((h.w != 0u) ? 1u : 0u) << (4 * e + 3);
-            }
-        } else {
-#pragma unroll
-            for (int e = 0; e < LS_V; ++e) {
-                const int t = tb + e;
-                hf |= ((t >= ntiles || head[t] != 0u) ? 1u : 0u) << e;
-            }
-        }
+    if (tid == 0) s_id = atomicAdd(ticket, 1u);
+    __syncthreads();
+    const int nch = level_scan_chunks(ntiles);
+    const int id = (int)s_id;
+    const int c = id / ncol, b = id - (id / ncol) * ncol;
+    if (c >= nch) return;
+    uint32_t* flags = lb + (size_t)b * nch;  // [ncol][nch] flags, aggregates, inclusive values
+    uint32_t* agg = lb + (size_t)(ncol + b) * nch;
+    uint32_t* inc = lb + (size_t)(2 * ncol + b) * nch;
+    const int tb = c * LS_CHUNK + tid * LS_V;
+    uint32_t lv[LS_V];
+    uint32_t hf = 0;  // bit e: tile tb + e starts a segment (tiles past the end count as heads)
+    if (tb + LS_V <= ntiles) {
+        const uint4 h = *reinterpret_cast<const uint4*>(head + tb);  // tb is a multiple of LS_V
+        hf = (h.x != 0u ? 1u : 0u) | (h.y != 0u ? 2u : 0u) | (h.z != 0u ? 4u : 0u) | (h.w != 0u ? 8u : 0u);
+    } else {
 #pragma unroll
         for (int e = 0; e < LS_V; ++e) {
             const int t = tb + e;
-            lv[e] = t < ntiles ? cnt[(int64_t)t * stride + b] : 0u;
+            hf |= ((t >= ntiles || head[t] != 0u) ? 1u : 0u) << e;
         }
-        // inclusive within the thread: a head starts a new segment
+    }
 #pragma unroll
-        for (int e = 1; e < LS_V; ++e)
-            if (!((hf >> e) & 1u)) lv[e] += lv[e - 1];
-        // (flag, value) pairs of the threads: inclusive scan within the warp
-        uint32_t xf = hf != 0u ? 1u : 0u, xv = lv[LS_V - 1];
+    for (int e = 0; e < LS_V; ++e) {
+        const int t = tb + e;
+        lv[e] = t < ntiles ? cnt[(int64_t)t * stride + b] : 0u;
+    }
+    // inclusive within the thread: a head starts a new segment
+#pragma unroll
+    for (int e = 1; e < LS_V; ++e)
+        if (!((hf >> e) & 1u)) lv[e] += lv[e - 1];
+    // (flag, value) pairs of the threads: inclusive scan within the warp
+    uint32_t xf = hf != 0u ? 1u : 0u, xv = lv[LS_V - 1];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t yf = __shfl_up_sync(0xffffffffu, xf, o);
+        const uint32_t yv = __shfl_up_sync(0xffffffffu, xv, o);
+        if (lane >= o) {
+            if (!xf) xv += yv;
+            xf |= yf;
+        }
+    }
+    uint32_t ef = __shfl_up_sync(0xffffffffu, xf, 1), ev = __shfl_up_sync(0xffffffffu, xv, 1);
+    if (lane == 0) {
+        ef = 0;
+        ev = 0;
+    }
+    if (lane == 31) {
+        s_f[warp] = xf;
+        s_v[warp] = xv;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t wf = s_f[lane], wv = s_v[lane];
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t yf = __shfl_up_sync(0xffffffffu, xf, o);
-            const uint32_t yv = __shfl_up_sync(0xffffffffu, xv, o);
+            const uint32_t yf = __shfl_up_sync(0xffffffffu, wf, o);
+            const uint32_t yv = __shfl_up_sync(0xffffffffu, wv, o);
             if (lane >= o) {
-                if (!xf) xv += yv;
-                xf |= yf;
+                if (!wf) wv += yv;
+                wf |= yf;
             }
         }
-        uint32_t ef = __shfl_up_sync(0xffffffffu, xf, 1), ev = __shfl_up_sync(0xffffffffu, xv, 1);
-        if (lane == 0) {
-            ef = 0;
-            ev = 0;
+        s_f[lane] = wf;
+        s_v[lane] = wv;
+    }
+    __syncthreads();
+    // what the chunk carries out, ignoring what comes in: inclusive when the
+    // chunk holds a head (or is the first)
+    const bool blk_head = s_f[31] != 0u;
+    if (tid == 0) {
+        if (c == 0 || blk_head) {
+            inc[c] = s_v[31];
+            publish_flag(flags, c, FLAG_INC);
+        } else {
+            agg[c] = s_v[31];
+            publish_flag(flags, c, FLAG_AGG);
         }
-        if (lane == 31) {
-            s_f[warp] = xf;
-            s_v[warp] = xv;
-        }
-        __syncthreads();
-        if (warp == 0) {
-            uint32_t wf = s_f[lane], wv = s_v[lane];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t yf = __shfl_up_sync(0xffffffffu, wf, o);
-                const uint32_t yv = __shfl_up_sync(0xffffffffu, wv, o);
-                if (lane >= o) {
-                    if (!wf) wv += yv;
-                    wf |= yf;
-                }
+    }
+    uint32_t carry = 0;
+    if (c > 0) {
+        const uint32_t ex = block_lookback<uint32_t>(flags, agg, inc, 1, c, &s_ctl, err, 1);
+        if (tid == 0) {
+            s_carry = ex;
+            if (!blk_head) {
+                inc[c] = ex + s_v[31];
+                publish_flag(flags, c, FLAG_INC);
             }
-            s_f[lane] = wf;
-            s_v[lane] = wv;
         }
         __syncthreads();
-        // everything before this thread: earlier chunks, earlier warps, earlier lanes
-        uint32_t pv = carry;
-        if (warp > 0) pv = s_f[warp - 1] ? s_v[warp - 1] : carry + s_v[warp - 1];
-        const uint32_t xv0 = ef ? ev : pv + ev;
+        carry = s_carry;
+    }
+    // everything before this thread: earlier chunks, earlier warps, earlier lanes
+    uint32_t pv = carry;
+    if (warp > 0) pv = s_f[warp - 1] ? s_v[warp - 1] : carry + s_v[warp - 1];
+    const uint32_t xv0 = ef ? ev : pv + ev;
 #pragma unroll
-        for (int e = 0; e < LS_V; ++e) {
-            const int t = tb + e;
-            // a head at or before e inside this thread cuts the carried prefix
-            const bool cut = (hf << (31 - e)) != 0u;
-            if (t < ntiles) incl[(int64_t)t * stride + b] = cut ? lv[e] : xv0 + lv[e];
-        }
-        carry = s_f[31] ? s_v[31] : carry + s_v[31];
-        __syncthreads();
+    for (int e = 0; e < LS_V; ++e) {
+        const int t = tb + e;
+        // a head at or before e inside this thread cuts the carried prefix
+        const bool cut = (hf << (31 - e)) != 0u;
+        if (t < ntiles) incl[(int64_t)t * stride + b] = cut ? lv[e] : xv0 + lv[e];
     }
 }
 
@@ -1134,8 +1167,11 @@ static int g_num_sms = 0;
 // counts [t][nbp], scanned counts [t][nbp], head flags [t], tile records
 // [t][trec_words], two tile counters.
 struct LevelStatus {
-    uint32_t *cnt, *incl, *head, *trec, *ctrs;
+    uint32_t *cnt, *incl, *head, *trec, *lb, *ctrs;
 };
+static size_t level_lb_words(int k, int ntiles) {
+    return ((size_t)3 * level_nbp(k) * level_scan_chunks(ntiles) + 3) & ~(size_t)3;
+}
 static LevelStatus level_status_layout(int k, int ntiles, uint32_t* status) {
     const size_t t4 = ((size_t)ntiles + 3) & ~(size_t)3;
     const size_t nbp = (size_t)level_nbp(k);
@@ -1144,13 +1180,14 @@ static LevelStatus level_status_layout(int k, int ntiles, uint32_t* status) {
     L.incl = L.cnt + t4 * nbp;
     L.head = L.incl + t4 * nbp;
     L.trec = L.head + t4;
-    L.ctrs = L.trec + t4 * (size_t)trec_words(k);
+    L.lb = L.trec + t4 * (size_t)trec_words(k);
+    L.ctrs = L.lb + level_lb_words(k, ntiles);
     return L;
 }
 
 size_t level_status_words(int k, int ntiles) {
     const size_t t4 = ((size_t)ntiles + 3) & ~(size_t)3;
-    return t4 * (2 * (size_t)level_nbp(k) + 1 + (size_t)trec_words(k)) + 4;
+    return t4 * (2 * (size_t)level_nbp(k) + 1 + (size_t)trec_words(k)) + level_lb_words(k, ntiles) + 4;
 }
 
 cudaError_t launch_level_pass(int k, const AllBufs& bufs, int q, const LevelJob* jobs, int njobs, int ntiles,
@@ -1160,15 +1197,18 @@ cudaError_t launch_level_pass(int k, const AllBufs& bufs, int q, const LevelJob*
     if (k < 2 || k > MAXK || g_num_sms == 0) return cudaErrorInvalidValue;
     const LevelStatus L = level_status_layout(k, ntiles, status);
     const int nbmax = 1 << (k - 1);
+    const int nch = level_scan_chunks(ntiles);
+    const int nflags = nbmax * nch;  // look-back flags of the scan, [bucket][chunk]
     const int gc = std::min(ntiles, g_num_sms * g_level_occ[0][k]);
     const int gm = std::min(ntiles, g_num_sms * g_level_occ[1][k]);
 #define KD_LEVEL_CASE(KK)                                                                                      \
     case KK:                                                                                                 \
         k_level_tiles<KK><<<(ntiles + 7) / 8, 256, 0, s>>>(jobs, njobs, ntiles, clouds, medr, L.trec, L.ctrs,   \
-                                                           err);                                             \
+                                                           L.lb, nflags, err);                               \
         k_level_count<KK><<<gc, LEVEL_BLOCK, level_smem_bytes<KK>(false), s>>>(                              \
             bufs, q, jobs, njobs, ntiles, clouds, L.trec, L.cnt, L.head, L.ctrs, err);                       \
-        k_level_scan<<<nbmax, 1024, 0, s>>>(ntiles, level_nbp(KK), L.cnt, L.head, L.incl);                   \
+        k_level_scan<<<nbmax * nch, 1024, 0, s>>>(ntiles, nbmax, level_nbp(KK), L.cnt, L.head, L.incl, L.lb,  \
+                                                  L.ctrs + 2, err);                                          \
         k_level_pass<KK><<<gm, LEVEL_BLOCK, level_smem_bytes<KK>(true), s>>>(                                \
             bufs, q, jobs, njobs, ntiles, clouds, medr, perm0, L.trec, L.incl, L.ctrs + 1, err);             \
         break;

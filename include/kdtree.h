@@ -39,7 +39,7 @@ extern "C" {
 #endif
 
 #define KD_MAX_K 8
-#define KD_MAX_N 1073741823LL /* 2^30 - 1: look-back status words hold 30-bit counts */
+#define KD_MAX_N 1073741823LL /* 2^30 - 1: the range the kernels' 32-bit positions and counts are sized for */
 
 typedef enum {
     KD_OK = 0,

@@ -90,8 +90,10 @@ __global__ void __launch_bounds__(256) k_transform(const T* __restrict__ coords,
 //   k_rs_move   persistent: a producer warp streams each tile's offsets row,
 //               keys and up to SP payload planes into a shared-memory stage
 //               with bulk async copies (full/empty mbarriers); eight consumer
-//               warps rank the keys stably (ballots over the digit bits, per-
-//               warp counters), order the tile by digit in shared memory and
+//               warps rank the keys stably (match instruction or match
+//               words, chosen per warp and tile by how many distinct digits
+//               the first 32 keys hold; per-warp counters), order the tile
+//               by digit in shared memory and
 //               write every plane with runs of equal digits to consecutive
 //               addresses.
 // Stability: within a tile, elements are ranked in position order (warp by

@@ -115,49 +115,64 @@ __device__ __forceinline__ uint32_t digit_of(KW key, int shift) {
     return (uint32_t)(key >> shift) & 255u;
 }
 
+constexpr int RS_CT = 2;  // tiles counted per block (their loads in flight together)
+
 template <typename KW, int TILE>
 __global__ void __launch_bounds__(256) k_rs_count(const int64_t* __restrict__ count_ptr, const KW* __restrict__ key_src,
                                                   int shift, uint32_t* __restrict__ cnt,
                                                   uint32_t* __restrict__ scan_flags, int nflags,
                                                   uint32_t* __restrict__ scan_ctr) {
     constexpr int V = 16 / sizeof(KW);            // keys per 16-byte load
-    constexpr int NV = TILE / V / 256;            // loads per thread
-    __shared__ uint32_t s_h[8][RADIX];
+    constexpr int NV = TILE / V / 256;            // loads per thread and tile
+    __shared__ uint32_t s_h[RS_CT][8][RADIX];
     const int tid = threadIdx.x, warp = tid >> 5;
     if (blockIdx.x == 0) {  // the scan of this pass starts from cleared flags
         for (int i = tid; i < nflags; i += 256) scan_flags[i] = 0;
         if (tid == 0) *scan_ctr = 0;
     }
-    for (int i = tid; i < 8 * RADIX; i += 256) (&s_h[0][0])[i] = 0;
+    for (int i = tid; i < RS_CT * 8 * RADIX; i += 256) (&s_h[0][0][0])[i] = 0;
     __syncthreads();
     const int64_t count = *count_ptr;
-    const int64_t base = (int64_t)blockIdx.x * TILE;
-    if (base >= count) return;
-    const int n = (int)(count - base < TILE ? count - base : (int64_t)TILE);
-    const KW* src = key_src + base;
-    uint4 x[NV];
+    const int64_t ntiles = (count + TILE - 1) / TILE;
+    uint4 x[RS_CT][NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-        const int o = (v * 256 + tid) * V;
-        x[v] = o + V <= n ? *reinterpret_cast<const uint4*>(src + o) : make_uint4(0, 0, 0, 0);
+    for (int c = 0; c < RS_CT; ++c) {
+        const int64_t base = ((int64_t)blockIdx.x * RS_CT + c) * TILE;
+        const int n = base >= count ? 0 : (int)(count - base < TILE ? count - base : (int64_t)TILE);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const int o = (v * 256 + tid) * V;
+            x[c][v] = o + V <= n ? *reinterpret_cast<const uint4*>(key_src + base + o) : make_uint4(0, 0, 0, 0);
+        }
     }
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-        const int o = (v * 256 + tid) * V;
-        if (o + V <= n) {
-            const KW* kv = reinterpret_cast<const KW*>(&x[v]);
+    for (int c = 0; c < RS_CT; ++c) {
+        const int64_t base = ((int64_t)blockIdx.x * RS_CT + c) * TILE;
+        const int n = base >= count ? 0 : (int)(count - base < TILE ? count - base : (int64_t)TILE);
+        const KW* src = key_src + base;
 #pragma unroll
-            for (int e = 0; e < V; ++e) atomicAdd(&s_h[warp][digit_of(kv[e], shift)], 1u);
-        } else {
-            for (int e = 0; e < V; ++e)
-                if (o + e < n) atomicAdd(&s_h[warp][digit_of(src[o + e], shift)], 1u);
+        for (int v = 0; v < NV; ++v) {
+            const int o = (v * 256 + tid) * V;
+            if (o + V <= n) {
+                const KW* kv = reinterpret_cast<const KW*>(&x[c][v]);
+#pragma unroll
+                for (int e = 0; e < V; ++e) atomicAdd(&s_h[c][warp][digit_of(kv[e], shift)], 1u);
+            } else {
+                for (int e = 0; e < V; ++e)
+                    if (o + e < n) atomicAdd(&s_h[c][warp][digit_of(src[o + e], shift)], 1u);
+            }
         }
     }
     __syncthreads();
-    uint32_t c = 0;
 #pragma unroll
-    for (int w = 0; w < 8; ++w) c += s_h[w][tid];
-    cnt[(int64_t)blockIdx.x * RADIX + tid] = c;
+    for (int c = 0; c < RS_CT; ++c) {
+        const int64_t t = (int64_t)blockIdx.x * RS_CT + c;
+        if (t >= ntiles) break;
+        uint32_t sum = 0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) sum += s_h[c][w][tid];
+        cnt[t * RADIX + tid] = sum;
+    }
 }
 
 // offs[t][d] = digit_base[d] + (elements of digit d in tiles before t).
@@ -819,7 +834,7 @@ static cudaError_t rs_pass(const int64_t* count_ptr, int64_t max_count, const vo
                            int occ, int* err, cudaStream_t s) {
     const int64_t tiles = (max_count + TILE - 1) / TILE;
     const int64_t chunks = (tiles + RS_CHUNK - 1) / RS_CHUNK;
-    k_rs_count<KW, TILE><<<(unsigned)tiles, 256, 0, s>>>(count_ptr, (const KW*)key_src, shift, A.cnt, A.flags,
+    k_rs_count<KW, TILE><<<(unsigned)((tiles + RS_CT - 1) / RS_CT), 256, 0, s>>>(count_ptr, (const KW*)key_src, shift, A.cnt, A.flags,
                                                           (int)A.nchunks, A.ctrs);
     k_rs_scan<<<(unsigned)chunks, 256, 0, s>>>(count_ptr, TILE, A.cnt, digit_base, A.offs, A.flags, A.agg, A.inc,
                                                A.ctrs, A.ctrs + 1, err);

@@ -106,6 +106,8 @@ __global__ void __launch_bounds__(256) k_level_tiles(const LevelJob* __restrict_
     constexpr int NBMAX = 1 << (K - 1);
     constexpr int TW = trec_words(K);
     constexpr int TILE = level_tile_of(K);
+    pdl_wait();  // the previous step's counters and medians
+    pdl_trigger();
     if (blockIdx.x == 0) {
         if (threadIdx.x < 3) ctrs[threadIdx.x] = 0;  // tile counters of the two passes, scan ticket
         for (int i = threadIdx.x; i < nflags; i += blockDim.x) scan_flags[i] = 0;
@@ -329,6 +331,8 @@ __global__ void __launch_bounds__(LEVEL_BLOCK)
     }
     for (int i = tid; i < LEVEL_STAGES * NDMAX; i += LEVEL_BLOCK) (&s_cnt[0][0])[i] = 0;
     __syncthreads();
+    pdl_wait();  // the tile records and counters
+    pdl_trigger();
     if (warp == LEVEL_WARPS) {
         if (lane == 0)
             level_producer<K, false>(bufs, q, jobs, njobs, ntiles, clouds, trec, nullptr, ctr, lsm, meta, full, empty,
@@ -425,6 +429,8 @@ __global__ void __launch_bounds__(1024) k_level_scan(int ntiles, int ncol, int s
     __shared__ uint32_t s_f[32], s_v[32];
     __shared__ uint32_t s_ctl, s_id, s_carry;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    pdl_wait();
+    pdl_trigger();
     if (tid == 0) s_id = atomicAdd(ticket, 1u);
     __syncthreads();
     const int nch = level_scan_chunks(ntiles);
@@ -576,6 +582,8 @@ __global__ void __launch_bounds__(LEVEL_BLOCK, K <= 3 ? 3 : 2)
     }
     for (int i = tid; i < LEVEL_WARPS * NDMAX; i += LEVEL_BLOCK) (&s_wc[0][0])[i] = 0;
     __syncthreads();
+    pdl_wait();  // the scanned counts
+    pdl_trigger();
     if (warp == LEVEL_WARPS) {
         if (lane == 0)
             level_producer<K, true>(bufs, q, jobs, njobs, ntiles, clouds, trec, incl, ctr, lsm, meta, full, empty, err);
@@ -1201,16 +1209,23 @@ cudaError_t launch_level_pass(int k, const AllBufs& bufs, int q, const LevelJob*
     const int nflags = nbmax * nch;  // look-back flags of the scan, [bucket][chunk]
     const int gc = std::min(ntiles, g_num_sms * g_level_occ[0][k]);
     const int gm = std::min(ntiles, g_num_sms * g_level_occ[1][k]);
+    cudaError_t e = cudaSuccess;
 #define KD_LEVEL_CASE(KK)                                                                                      \
     case KK:                                                                                                 \
-        k_level_tiles<KK><<<(ntiles + 7) / 8, 256, 0, s>>>(jobs, njobs, ntiles, clouds, medr, L.trec, L.ctrs,   \
-                                                           L.lb, nflags, err);                               \
-        k_level_count<KK><<<gc, LEVEL_BLOCK, level_smem_bytes<KK>(false), s>>>(                              \
-            bufs, q, jobs, njobs, ntiles, clouds, L.trec, L.cnt, L.head, L.ctrs, err);                       \
-        k_level_scan<<<nbmax * nch, 1024, 0, s>>>(ntiles, nbmax, level_nbp(KK), L.cnt, L.head, L.incl, L.lb,  \
-                                                  L.ctrs + 2, err);                                          \
-        k_level_pass<KK><<<gm, LEVEL_BLOCK, level_smem_bytes<KK>(true), s>>>(                                \
-            bufs, q, jobs, njobs, ntiles, clouds, medr, perm0, L.trec, L.incl, L.ctrs + 1, err);             \
+        e = launch_dependent(k_level_tiles<KK>, dim3((ntiles + 7) / 8), dim3(256), 0, s, jobs, njobs, ntiles,    \
+                             clouds, (const uint32_t*)medr, L.trec, L.ctrs, L.lb, nflags, err);              \
+        if (e == cudaSuccess)                                                                                \
+            e = launch_dependent(k_level_count<KK>, dim3(gc), dim3(LEVEL_BLOCK), level_smem_bytes<KK>(false), s, bufs, \
+                             q, jobs, njobs, ntiles, clouds, (const uint32_t*)L.trec, L.cnt, L.head, L.ctrs, err);  \
+        if (e == cudaSuccess)                                                                                \
+            e = launch_dependent(k_level_scan, dim3(nbmax * nch), dim3(1024), 0, s, ntiles, nbmax,            \
+                                 level_nbp(KK), (const uint32_t*)L.cnt, (const uint32_t*)L.head, L.incl, L.lb, \
+                                 L.ctrs + 2, err);                                                           \
+        if (e == cudaSuccess)                                                                                \
+            e = launch_dependent(k_level_pass<KK>, dim3(gm), dim3(LEVEL_BLOCK), level_smem_bytes<KK>(true), s, \
+                                 bufs, q, jobs, njobs, ntiles, clouds, medr, perm0, (const uint32_t*)L.trec,   \
+                                 (const uint32_t*)L.incl, L.ctrs + 1, err);                                  \
+        if (e != cudaSuccess) return e;                                                                      \
         break;
     switch (k) {
         KD_LEVEL_CASE(2)

@@ -2,6 +2,8 @@
 // kernel files and the host orchestration of the GB300 k-d tree builder.
 #pragma once
 
+#include <utility>
+
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -81,6 +83,34 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
+// Programmatic dependent launch.  A kernel launched by launch_dependent()
+// may start while the previous kernel on its stream is still running; it
+// calls pdl_wait() before its first global-memory access, which returns once
+// that kernel has completed and its writes are visible (at once when the
+// kernel was launched without the attribute).  pdl_trigger() lets the
+// dependent grid launch as soon as every block of this grid has issued it.
+#ifndef KD_PDL
+#define KD_PDL 1
+#endif
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... P, typename... A>
+inline cudaError_t launch_dependent(void (*kern)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                                    A&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = KD_PDL;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<A>(args)...);
+}
+
 // Named barrier 1 over the first NT threads of the block (the consumer
 // warps of a kernel whose last warp is a producer that never joins it).
 template <int NT>

@@ -126,6 +126,8 @@ __global__ void __launch_bounds__(256) k_rs_count(const int64_t* __restrict__ co
     constexpr int NV = TILE / V / 256;            // loads per thread and tile
     __shared__ uint32_t s_h[RS_CT][8][RADIX];
     const int tid = threadIdx.x, warp = tid >> 5;
+    pdl_wait();  // the previous pass's keys
+    pdl_trigger();
     if (blockIdx.x == 0) {  // the scan of this pass starts from cleared flags
         for (int i = tid; i < nflags; i += 256) scan_flags[i] = 0;
         if (tid == 0) *scan_ctr = 0;
@@ -184,6 +186,8 @@ __global__ void __launch_bounds__(256) k_rs_scan(const int64_t* __restrict__ cou
                                                  uint32_t* __restrict__ move_ctr, int* __restrict__ err) {
     __shared__ uint32_t s_chunk, s_ctl;
     const int tid = threadIdx.x;
+    pdl_wait();
+    pdl_trigger();
     if (tid == 0) s_chunk = atomicAdd(scan_ctr, 1u);
     if (blockIdx.x == 0 && tid == 0) *move_ctr = 0;  // the move pass starts after this kernel
     __syncthreads();
@@ -258,6 +262,8 @@ __global__ void __launch_bounds__(RS_BLOCK, TILE * (SP + 1) * sizeof(KW) <= 2048
         (&s_match[0][0])[i] = 0;
     }
     __syncthreads();
+    pdl_wait();  // the scan's offsets and tile counter
+    pdl_trigger();
     const int64_t count = *count_ptr;
     const int64_t ntiles = (count + TILE - 1) / TILE;
     if (warp == RS_WARPS) {  // producer
@@ -834,13 +840,18 @@ static cudaError_t rs_pass(const int64_t* count_ptr, int64_t max_count, const vo
                            int occ, int* err, cudaStream_t s) {
     const int64_t tiles = (max_count + TILE - 1) / TILE;
     const int64_t chunks = (tiles + RS_CHUNK - 1) / RS_CHUNK;
-    k_rs_count<KW, TILE><<<(unsigned)((tiles + RS_CT - 1) / RS_CT), 256, 0, s>>>(count_ptr, (const KW*)key_src, shift, A.cnt, A.flags,
-                                                          (int)A.nchunks, A.ctrs);
-    k_rs_scan<<<(unsigned)chunks, 256, 0, s>>>(count_ptr, TILE, A.cnt, digit_base, A.offs, A.flags, A.agg, A.inc,
-                                               A.ctrs, A.ctrs + 1, err);
+    cudaError_t e = launch_dependent(k_rs_count<KW, TILE>, dim3((unsigned)((tiles + RS_CT - 1) / RS_CT)), dim3(256), 0,
+                                     s, count_ptr, (const KW*)key_src, shift, A.cnt, A.flags, (int)A.nchunks, A.ctrs);
+    if (e != cudaSuccess) return e;
+    e = launch_dependent(k_rs_scan, dim3((unsigned)chunks), dim3(256), 0, s, count_ptr, TILE,
+                                     (const uint32_t*)A.cnt, digit_base, A.offs, A.flags, A.agg, A.inc, A.ctrs,
+                                     A.ctrs + 1, err);
+    if (e != cudaSuccess) return e;
     const int64_t grid = std::min<int64_t>(tiles, (int64_t)g_rs_sms * occ);
-    k_rs_move<KW, TILE, SP><<<(unsigned)grid, RS_BLOCK, rs_move_smem<KW, TILE, SP>(), s>>>(
-        count_ptr, (const KW*)key_src, (KW*)key_dst, pay, A.offs, shift, A.ctrs + 1, err);
+    e = launch_dependent(k_rs_move<KW, TILE, SP>, dim3((unsigned)grid), dim3(RS_BLOCK), rs_move_smem<KW, TILE, SP>(),
+                         s, count_ptr, (const KW*)key_src, (KW*)key_dst, pay, (const uint32_t*)A.offs, shift,
+                         A.ctrs + 1, err);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

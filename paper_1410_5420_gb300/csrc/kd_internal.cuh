@@ -2,9 +2,9 @@
 // kernel files and the host orchestration of the GB300 k-d tree builder.
 #pragma once
 
+#include <cstdint>
 #include <utility>
 
-#include <cstdint>
 #include <cuda_runtime.h>
 
 namespace kd {
@@ -89,9 +89,6 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // that kernel has completed and its writes are visible (at once when the
 // kernel was launched without the attribute).  pdl_trigger() lets the
 // dependent grid launch as soon as every block of this grid has issued it.
-#ifndef KD_PDL
-#define KD_PDL 1
-#endif
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
@@ -105,7 +102,7 @@ inline cudaError_t launch_dependent(void (*kern)(P...), dim3 grid, dim3 block, s
     cfg.stream = s;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = KD_PDL;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kern, std::forward<A>(args)...);
@@ -434,9 +431,7 @@ __device__ __forceinline__ void warp_rank(const uint32_t (&dig)[IPT], uint32_t m
 // the highest of them advances the warp's counter of the digit and clears
 // the word, so `match` is all zero between calls.  Both leave the same
 // per-warp counts in wc.  Digits below `marker` (the marker: no element).
-#ifndef KD_RANK_DISTINCT
-#define KD_RANK_DISTINCT 16
-#endif
+constexpr int RANK_DISTINCT_MAX = 16;  // at most this many distinct first digits: match instruction
 template <int IPT>
 __device__ __forceinline__ void warp_rank_adaptive(const uint32_t (&dig)[IPT], uint32_t marker,
                                                    uint32_t* __restrict__ wc, uint32_t* __restrict__ match,
@@ -449,7 +444,7 @@ __device__ __forceinline__ void warp_rank_adaptive(const uint32_t (&dig)[IPT], u
     if (lane == leader && dig[0] < marker) old = atomicAdd(&wc[dig[0]], (uint32_t)__popc(peers));
     rank[0] = __shfl_sync(0xffffffffu, old, leader) + __popc(peers & lt);
     const int distinct = __popc(__ballot_sync(0xffffffffu, lane == leader));
-    if (distinct <= KD_RANK_DISTINCT) {
+    if (distinct <= RANK_DISTINCT_MAX) {
 #pragma unroll
         for (int j = 1; j < IPT; ++j) {
             const uint32_t d = dig[j];

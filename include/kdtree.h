@@ -58,7 +58,7 @@ typedef struct {
     void *cuda_stream;       /* cudaStream_t to order work on; NULL: the library makes its own */
     size_t mem_budget_bytes; /* cap on the library's device workspace; 0: no cap */
     int tile_T;              /* 0: default.  Reserved for the autotuner */
-    int switch_threshold;    /* subtree size finished on chip; 0: default per k */
+    int switch_threshold;    /* subtree size finished on chip (rounded up to 1024, 2048 or 4096, capped by k); 0: 1024 */
     int debug;               /* nonzero: synchronise and check after every phase */
 } kd_config;
 

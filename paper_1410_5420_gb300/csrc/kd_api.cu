@@ -849,8 +849,10 @@ kd_status build_batch(kd_ctx* ctx, kd_presorted* H, kd_tree* outs) {
     CKS(S.get(&d_err, 4));
     CK(cudaMemsetAsync(d_err, 0, 4, s));
     // subtree size finished on chip: a power of two in [1024, 4096] (the
-    // level-pass tiles of 2048 positions need segments of at least 683)
-    int smax = k <= 4 ? 2048 : 1024;
+    // level-pass tiles of 2048 positions need segments of at least 683).
+    // 1024 by default: one more level step costs less than the finisher's
+    // extra block level at 2048 (k = 2..4, 2^22..2^26 tuples).
+    int smax = 1024;
     if (ctx->smax_override) {
         smax = 1024;
         while (smax < ctx->smax_override && smax < 4096) smax *= 2;

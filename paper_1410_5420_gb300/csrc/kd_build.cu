@@ -908,8 +908,13 @@ __device__ __forceinline__ void fin_load_dispatch(const AllBufs& bufs, const Clo
         *bad = 1;
 }
 
+// Blocks per SM the finisher is compiled for: at 1024 tuples five blocks
+// fit the shared memory, and trading registers for them (a few spills)
+// hides more of the shared-memory latency.
+__host__ __device__ constexpr int fin_min_blocks(int smax) { return smax >= 4096 ? 2 : (smax <= 1024 ? 5 : 3); }
+
 template <int SMAX>
-__global__ void __launch_bounds__(FIN_THREADS, SMAX >= 4096 ? 2 : 3)
+__global__ void __launch_bounds__(FIN_THREADS, fin_min_blocks(SMAX))
     k_finish(const __grid_constant__ AllBufs bufs, int k, const int64_t* __restrict__ unit_prefix, int ncloud,
              int64_t unit_base, const CloudDev* __restrict__ clouds, const uint32_t* __restrict__ perm0,
              int* __restrict__ err, unsigned long long* __restrict__ phase_ns) {

@@ -1,6 +1,7 @@
-"""Host logic of bench.py's multi-rank (replica) runs, on CPU with gloo at
-world size 2: the step time is the maximum over ranks and the reported
-value counts the points of every rank."""
+"""Host logic of bench.py: multi-rank (replica) runs on CPU with gloo at
+world size 2 (the step time is the maximum over ranks and the reported
+value counts the points of every rank), and the rule that the roofline's
+DRAM traffic is reported only for the kernel source it was measured on."""
 import os
 import socket
 import sys
@@ -52,3 +53,23 @@ def test_single_rank_is_identity():
     import bench
     assert bench.max_over_ranks(3.5, 1) == 3.5
     assert bench.whole_job_value(1, 100, 0.5) == 200.0
+
+
+def test_traffic_is_reported_only_for_the_source_it_was_measured_on(tmp_path, monkeypatch):
+    """The roofline's DRAM traffic comes from a committed ncu summary and is
+    dropped (null) once the kernel source differs from the one measured."""
+    import hashlib
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+    src = tmp_path / "kern.cu"
+    src.write_text("// kernel v1\n")
+    (tmp_path / "profiles").mkdir()
+    entry = {"source": "kern.cu", "sha256": hashlib.sha256(src.read_bytes()).hexdigest(),
+             "bytes_per_element": 24.5, "launches_per_step": 20}
+    (tmp_path / "profiles" / "dram_traffic.json").write_text(json.dumps({"sort_pass": entry}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.traffic_for("sort_pass") == pytest.approx(24.5)
+    assert bench.traffic_for("level_pass") is None
+    src.write_text("// kernel v2\n")
+    assert bench.traffic_for("sort_pass") is None

@@ -59,7 +59,11 @@ typedef struct {
     size_t mem_budget_bytes; /* cap on the library's device workspace; 0: no cap */
     int tile_T;              /* 0: default.  Reserved for the autotuner */
     int switch_threshold;    /* subtree size finished on chip (rounded up to 1024, 2048 or 4096, capped by k); 0: 1024 */
-    int debug;               /* nonzero: synchronise and check after every phase */
+    int debug;               /* bit 1: synchronise after the presort; bit 2: time every launch
+                                (kd_kernel_stats); bit 4: finisher phase counters; bit 8
+                                (failure-detection tests): bound the device waits to a few
+                                thousand polls and make the next presort's first look-back
+                                wait run out once, which it reports as KD_ETIMEOUT */
 } kd_config;
 
 typedef struct {
@@ -164,25 +168,27 @@ kd_status kd_destroy(kd_ctx *ctx);
 const char *kd_last_error(kd_ctx *ctx);
 
 /*
- * kd_presort_noalloc -- the presort of kd_presort (Section 2.1: index arrays
- * sorted by the k cyclic super keys, duplicate tuples removed) for one small
- * cloud, without allocating any memory.  The paper has no counterpart: it
- * exists for callers that cannot let a library allocate during a call, such
- * as a process whose device memory is all owned by its own allocator, or a
- * latency-bound loop that cannot absorb a pool growth or a device-wide
- * synchronising free.  Its workspace is one static device array of about
- * 1 MiB per device, sized for KD_NOALLOC_MAX_N tuples of up to KD_MAX_K
- * coordinates.
+ * kd_presort_noalloc -- what kd_presort + kd_handle_arrays compute, for one
+ * small cloud, without allocating any memory.  The paper has no
+ * counterpart: it exists for callers that cannot let a library allocate
+ * during a call, such as a process whose device memory is all owned by its
+ * own allocator, or a latency-bound loop that cannot absorb a pool growth
+ * or a device-wide synchronising free.  Its workspace is one static device
+ * array of about 1 MiB per device, sized for KD_NOALLOC_MAX_N tuples of up
+ * to KD_MAX_K coordinates.
  *
- *  cloud       coordinates in device memory (cloud->on_device must be 1),
- *              n <= KD_NOALLOC_MAX_N; larger clouds return KD_EINVAL with
- *              the limit in kd_last_error (use kd_presort for them).
- *  arrays_out  device memory, k rows of n int32 (row stride n): row d
- *              receives the deduplicated super-key-d order, the same values
- *              kd_handle_arrays gives for the same cloud, in its first m
- *              entries; the rest of the row is left untouched.
- *  m_out       device memory, one int32: m, or KD_ENAN if a float
- *              coordinate is NaN (arrays_out is then left untouched).
+ *  cloud       coordinates in device memory on the context's device
+ *              (cloud->on_device must be 1), n <= KD_NOALLOC_MAX_N; larger
+ *              clouds return KD_EINVAL with the limit in kd_last_error (use
+ *              kd_presort for them).
+ *  arrays_out  device memory on the context's device, k rows of n int32
+ *              (row stride n): row d receives the deduplicated super-key-d
+ *              order, the same values kd_handle_arrays gives for the same
+ *              cloud, in its first m entries; the rest of the row is left
+ *              untouched.
+ *  m_out       device memory on the context's device, one int32: m, or
+ *              KD_ENAN if a float coordinate is NaN (arrays_out is then
+ *              left untouched).
  *
  * Asynchronous: the work is ordered on the context's stream and the call
  * returns without waiting; read *m_out after the stream.  Argument errors

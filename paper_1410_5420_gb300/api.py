@@ -263,6 +263,14 @@ def kd_serving_stats(ctx: Context) -> dict:
     return {"completed": n.value, "p50_us": p50.value, "p99_us": p99.value}
 
 
+def _check_out_buffer(name: str, t, dev, need: int) -> None:
+    """An output the library writes through a raw pointer: a contiguous
+    int32 tensor on ``dev`` holding at least ``need`` elements."""
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.int32 or not t.is_contiguous() \
+            or t.device != dev or t.numel() < need:
+        raise ValueError(f"{name} must be a contiguous int32 tensor on {dev} with at least {need} elements")
+
+
 def kd_presort_noalloc(ctx: Context, coords, arrays_out=None, m_out=None):
     """kd_presort_noalloc: presort + duplicate removal of one small cloud
     (device tensor, n <= KD_NOALLOC_MAX_N) into caller-owned device buffers;
@@ -276,6 +284,10 @@ def kd_presort_noalloc(ctx: Context, coords, arrays_out=None, m_out=None):
         arrays_out = torch.empty((c.k, max(c.n, 1)), dtype=torch.int32, device=dev)
     if m_out is None:
         m_out = torch.empty(1, dtype=torch.int32, device=dev)
+    # the library writes through raw pointers: k rows of n int32 at stride n
+    # and one int32, on the context's device
+    _check_out_buffer("arrays_out", arrays_out, dev, c.k * c.n)
+    _check_out_buffer("m_out", m_out, dev, 1)
     ctx.check(_lib.load().kd_presort_noalloc(ctx.ptr, ctypes.byref(c), ctypes.c_void_p(arrays_out.data_ptr()),
                                              ctypes.c_void_p(m_out.data_ptr())))
     del keep

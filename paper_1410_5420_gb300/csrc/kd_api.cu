@@ -31,7 +31,8 @@ cudaError_t launch_transform(int dtype, const void* coords, int64_t n, int k, vo
 size_t sort_status_words(int64_t max_count);
 cudaError_t launch_sort_pass(int key64, const int64_t* count_ptr, int64_t max_count, const void* key_src,
                              void* key_dst, const PayloadArgs& pay, const uint32_t* digit_base, int shift,
-                             uint32_t* status, int* err, cudaStream_t s);
+                             uint32_t* status, int* err, cudaStream_t s, uint32_t spin_limit = SPIN_LIMIT,
+                             int withhold = 0);
 cudaError_t launch_digit_bases(const uint32_t* hist, int nrows, uint32_t* bases, cudaStream_t s);
 cudaError_t launch_pack_clouds(const PackDesc* d, int count, void* dst, cudaStream_t s);
 cudaError_t launch_gather(int key64, const int64_t* count_ptr, int64_t max_count, const void* plane,
@@ -102,6 +103,12 @@ struct kd_ctx {
     size_t in_use = 0;
     int debug = 0;
     int smax_override = 0;
+    // Failure-detection tests (debug bit 8): the look-back polls are bounded
+    // by a few thousand instead of 2^24, and the next presort's first sort
+    // pass has its chunk 0 withhold its flag (once), so that the other
+    // chunks' waits run out and the call reports KD_ETIMEOUT.
+    uint32_t spin_limit = SPIN_LIMIT;
+    bool inject_timeout = false;
     std::string last_error;
     std::recursive_mutex mu;
     std::unordered_map<void*, size_t> sizes;
@@ -602,10 +609,18 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
             CK(launch_gather(plane64(P.plane), d_n, N, plane_ptr(P.plane), ibuf[ic], kbuf[kc], d_err, s));
             ksrc = kbuf[kc];
         }
-        LaunchTimer lt(ctx, F_SORT, (double)N, nullptr, pass_bytes(P, kdst != nullptr, pay.n));
-        ctx->launches += 2;  // count and scan kernels of the pass
-        CK(launch_sort_pass(plane64(P.plane), d_n, N, ksrc, kdst, pay,
-                            bases_all + (size_t)row_of(P.plane, P.digit) * RADIX, 8 * P.digit, status, d_err, s));
+        const bool inject = ctx->inject_timeout && i == 0;
+        {
+            LaunchTimer lt(ctx, F_SORT, (double)N, nullptr, pass_bytes(P, kdst != nullptr, pay.n));
+            ctx->launches += 2;  // count and scan kernels of the pass
+            CK(launch_sort_pass(plane64(P.plane), d_n, N, ksrc, kdst, pay,
+                                bases_all + (size_t)row_of(P.plane, P.digit) * RADIX, 8 * P.digit, status, d_err, s,
+                                ctx->spin_limit, inject ? 1 : 0));
+        }
+        if (inject) {  // the injected wait: report it before anything else runs
+            ctx->inject_timeout = false;
+            CKS(check_device_err(ctx, d_err));
+        }
         kc ^= 1;
         ic ^= 1;
         if (carry) {
@@ -656,7 +671,8 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
         LaunchTimer lt(ctx, F_SORT, 0.0, H->d_m, pass_bytes(P, !last, 1));
         ctx->launches += 2;  // count and scan kernels of the pass
         CK(launch_sort_pass(0, H->d_m, N, ksrc, last ? nullptr : (void*)kbuf[kc ^ 1], pay,
-                            bases_kept + (size_t)row_of(-1, P.digit) * RADIX, 8 * P.digit, status, d_err, s));
+                            bases_kept + (size_t)row_of(-1, P.digit) * RADIX, 8 * P.digit, status, d_err, s,
+                            ctx->spin_limit));
         kc ^= 1;
         ic ^= 1;
     }
@@ -726,7 +742,7 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
                 ctx->launches += 2;  // count and scan kernels of the pass
                 CK(launch_sort_pass(plane64(P.plane), H->d_m, N, ksrc, kdst, pay,
                                     bases_kept + (size_t)row_of(P.plane, P.digit) * RADIX, 8 * P.digit, status,
-                                    d_err, s));
+                                    d_err, s, ctx->spin_limit));
                 kc ^= 1;
                 if (carry_id) cur_id = new_id;
                 for (size_t j = 0; j < ranks.size(); ++j) rsrc[j] = last ? H->rec.p[d][ranks[j]] : pbuf[pb][j];
@@ -775,7 +791,8 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
                 {
                     LaunchTimer lt(ctx, F_RECORDS, 0.0, H->d_m, 4.0 + 8.0 * nv + 4.0);
                     ctx->launches += 2;  // count and scan kernels of the pass
-                    CK(launch_sort_pass(0, H->d_m, N, H->rec.p[1][d], gdest, pay, pbases, shift, status, d_err, s));
+                    CK(launch_sort_pass(0, H->d_m, N, H->rec.p[1][d], gdest, pay, pbases, shift, status, d_err, s,
+                                        ctx->spin_limit));
                 }
                 PayloadArgs sc{};
                 sc.n = nv;
@@ -1247,6 +1264,10 @@ kd_status kd_create(kd_ctx** out, const kd_config* cfg) {
     ctx->budget = c.mem_budget_bytes;
     ctx->debug = c.debug;
     ctx->smax_override = c.switch_threshold;
+    if (c.debug & 8) {
+        ctx->spin_limit = 4096;
+        ctx->inject_timeout = true;
+    }
     if (cudaSetDevice(c.device) != cudaSuccess) return KD_EDEVICE;
     // kernel attributes are per device: set them once for each device used
     static std::mutex init_mu;

@@ -21,11 +21,16 @@
 //                 in every super-key order, so each compare is one integer
 //                 compare (super keys are unique after deduplication).
 //   k_finish      once segments hold at most a few thousand tuples, one CTA
-//                 finishes a whole subtree in shared memory: per level the
-//                 primary array's medians become nodes and the other arrays
-//                 are stably partitioned with a segmented block scan, down
-//                 to single elements (same result as the paper's 1/2/3
-//                 element termination).
+//                 finishes a whole subtree in shared memory.  Every tuple
+//                 carries a segment label; while segments exceed 32 tuples,
+//                 each level is one pass over the primary array ranking
+//                 tuples within their labels (the median offset becomes the
+//                 node, the others take their half's label).  A stable
+//                 multisplit by label then orders every array within the
+//                 remaining segments, and one warp finishes each segment of
+//                 at most 32 tuples with per-dimension precedence masks,
+//                 down to single elements (same result as the paper's
+//                 1/2/3 element termination).
 //   k_top_nodes   children and split dimension of the nodes above the
 //                 finisher level (pure functions of m and the address).
 #include <algorithm>

@@ -210,11 +210,15 @@ __device__ __forceinline__ void publish_flag(uint32_t* flags, int64_t tile, uint
 
 // Called by the whole block (uniform control flow).  Thread `tid < nslot`
 // receives the exclusive prefix of slot tid in *excl.  AggT is the word type
-// of aggregate records.  s_ctl: one shared word.  Bounded wait.
+// of aggregate records.  s_ctl: one shared word.  Bounded wait: after
+// `spin_limit` polls that find a predecessor without a record, the block
+// sets ERR_TIMEOUT, *timed_out (if given) becomes true for every thread and
+// the returned prefix is meaningless.
 template <typename AggT>
 __device__ __forceinline__ uint32_t block_lookback(const uint32_t* flags, const AggT* aggrec, const uint32_t* increc,
                                                    int nslot, int64_t tile, uint32_t* s_ctl, int* err,
-                                                   int stride = 0) {
+                                                   int stride = 0, uint32_t spin_limit = SPIN_LIMIT,
+                                                   bool* timed_out = nullptr) {
     if (stride == 0) stride = nslot;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint32_t excl = 0;
@@ -234,8 +238,9 @@ __device__ __forceinline__ uint32_t block_lookback(const uint32_t* flags, const 
         const uint32_t L = *s_ctl;
         __syncthreads();
         if (L == 0xffffffffu) {
-            if (++spins > SPIN_LIMIT) {
+            if (++spins > spin_limit) {
                 if (tid == 0) atomicOr(err, ERR_TIMEOUT);
+                if (timed_out) *timed_out = true;
                 break;
             }
             __nanosleep(32);

@@ -182,13 +182,24 @@ cudaError_t noalloc_setup(int device, uint64_t** ws) {
     return cudaSuccess;
 }
 
-bool on_device_memory(const void* p) {
+// Device (or managed) memory owned by `device`: a buffer on another GPU
+// would be read or written through peer access, which need not be enabled.
+bool on_device_memory(const void* p, int device) {
     cudaPointerAttributes a{};
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
+        cudaGetLastError();  // the query's own error, raised just now
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == device;
+}
+
+// Launch with the error returned by the launch call itself, so that an
+// error pending from the caller's earlier work is neither reported as this
+// call's nor cleared.
+template <typename... P>
+cudaError_t na_launch(void (*kern)(P...), int grid, int block, size_t smem, cudaStream_t s, P... args) {
+    void* argv[] = {static_cast<void*>(&args)...};
+    return cudaLaunchKernel(reinterpret_cast<const void*>(kern), dim3(grid), dim3(block), argv, smem, s);
 }
 
 kd_status na_fail(kd_ctx* ctx, kd_status code, const std::string& msg) {
@@ -214,9 +225,11 @@ extern "C" kd_status kd_presort_noalloc(kd_ctx* ctx, const kd_cloud* cloud, int3
     const int dev = kd::ctx_device(ctx);
     cudaError_t e = cudaSetDevice(dev);
     if (e != cudaSuccess) return na_fail(ctx, KD_EDEVICE, cudaGetErrorString(e));
-    if (!on_device_memory(m_out)) return na_fail(ctx, KD_EINVAL, "m_out must be device memory");
-    if (n > 0 && (!cloud->coords || !arrays_out || !on_device_memory(cloud->coords) || !on_device_memory(arrays_out)))
-        return na_fail(ctx, KD_EINVAL, "coords and arrays_out must be non-null device memory");
+    if (!on_device_memory(m_out, dev))
+        return na_fail(ctx, KD_EINVAL, "m_out must be device memory on the context's device");
+    if (n > 0 && (!cloud->coords || !arrays_out || !on_device_memory(cloud->coords, dev) ||
+                  !on_device_memory(arrays_out, dev)))
+        return na_fail(ctx, KD_EINVAL, "coords and arrays_out must be non-null device memory on the context's device");
     uint64_t* ws = nullptr;
     e = noalloc_setup(dev, &ws);
     if (e != cudaSuccess) return na_fail(ctx, KD_EDEVICE, std::string("set-up: ") + cudaGetErrorString(e));
@@ -232,20 +245,23 @@ extern "C" kd_status kd_presort_noalloc(kd_ctx* ctx, const kd_cloud* cloud, int3
     if (grid > 1024) grid = 1024;
     switch (cloud->dtype) {
         case KD_I32:
-            k_noalloc_keys<<<grid, NA_KEYS_THREADS, 0, s>>>(static_cast<const int32_t*>(cloud->coords), ni, k, ws);
+            e = na_launch(k_noalloc_keys<int32_t>, grid, NA_KEYS_THREADS, 0, s,
+                          static_cast<const int32_t*>(cloud->coords), ni, k, ws);
             break;
         case KD_I64:
-            k_noalloc_keys<<<grid, NA_KEYS_THREADS, 0, s>>>(static_cast<const int64_t*>(cloud->coords), ni, k, ws);
+            e = na_launch(k_noalloc_keys<int64_t>, grid, NA_KEYS_THREADS, 0, s,
+                          static_cast<const int64_t*>(cloud->coords), ni, k, ws);
             break;
         default:
-            k_noalloc_keys<<<grid, NA_KEYS_THREADS, 0, s>>>(static_cast<const float*>(cloud->coords), ni, k, ws);
+            e = na_launch(k_noalloc_keys<float>, grid, NA_KEYS_THREADS, 0, s, static_cast<const float*>(cloud->coords),
+                          ni, k, ws);
             break;
     }
+    if (e != cudaSuccess) return na_fail(ctx, KD_EDEVICE, std::string("launch: ") + cudaGetErrorString(e));
     int npow2 = 2;
     while (npow2 < ni) npow2 <<= 1;
     const size_t smem = (size_t)npow2 * (sizeof(uint64_t) + sizeof(uint32_t));
-    k_noalloc_sort<<<k, NA_THREADS, smem, s>>>(ni, npow2, k, ws, arrays_out, m_out);
-    e = cudaGetLastError();
+    e = na_launch(k_noalloc_sort, k, NA_THREADS, smem, s, ni, npow2, k, (const uint64_t*)ws, arrays_out, m_out);
     if (e != cudaSuccess) return na_fail(ctx, KD_EDEVICE, std::string("launch: ") + cudaGetErrorString(e));
     kd::ctx_add_launches(ctx, 2);
     return KD_OK;

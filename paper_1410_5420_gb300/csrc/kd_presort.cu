@@ -178,12 +178,17 @@ __global__ void __launch_bounds__(256) k_rs_count(const int64_t* __restrict__ co
 }
 
 // offs[t][d] = digit_base[d] + (elements of digit d in tiles before t).
+// spin_limit bounds the look-back's polls; a chunk whose wait runs out
+// stores nothing and reports ERR_TIMEOUT.  withhold (failure-detection
+// tests only): chunk 0 never publishes its flag, so every later chunk's
+// wait runs out.
 __global__ void __launch_bounds__(256) k_rs_scan(const int64_t* __restrict__ count_ptr, int tile,
                                                  const uint32_t* __restrict__ cnt,
                                                  const uint32_t* __restrict__ digit_base, uint32_t* __restrict__ offs,
                                                  uint32_t* __restrict__ flags, uint32_t* __restrict__ agg,
                                                  uint32_t* __restrict__ inc, uint32_t* __restrict__ scan_ctr,
-                                                 uint32_t* __restrict__ move_ctr, int* __restrict__ err) {
+                                                 uint32_t* __restrict__ move_ctr, int* __restrict__ err,
+                                                 uint32_t spin_limit, int withhold) {
     __shared__ uint32_t s_chunk, s_ctl;
     const int tid = threadIdx.x;
     pdl_wait();
@@ -208,10 +213,14 @@ __global__ void __launch_bounds__(256) k_rs_scan(const int64_t* __restrict__ cou
     if (c == 0) inc[tid] = sum;
     else agg[c * RADIX + tid] = sum;
     __syncthreads();
-    if (tid == 0) publish_flag(flags, c, c == 0 ? FLAG_INC : FLAG_AGG);
+    if (tid == 0 && !(withhold && c == 0)) publish_flag(flags, c, c == 0 ? FLAG_INC : FLAG_AGG);
     uint32_t excl = 0;
     if (c > 0) {
-        excl = block_lookback<uint32_t>(flags, agg, inc, RADIX, c, &s_ctl, err);
+        __shared__ bool s_late;
+        if (tid == 0) s_late = false;
+        __syncthreads();
+        excl = block_lookback<uint32_t>(flags, agg, inc, RADIX, c, &s_ctl, err, 0, spin_limit, &s_late);
+        if (s_late) return;  // uniform: set by the look-back for the whole block
         inc[c * RADIX + tid] = excl + sum;
         __syncthreads();
         if (tid == 0) publish_flag(flags, c, FLAG_INC);
@@ -837,7 +846,7 @@ static int g_rs_sms = 0;
 template <typename KW, int TILE, int SP>
 static cudaError_t rs_pass(const int64_t* count_ptr, int64_t max_count, const void* key_src, void* key_dst,
                            const PayloadArgs& pay, const uint32_t* digit_base, int shift, const SortStatusArea& A,
-                           int occ, int* err, cudaStream_t s) {
+                           int occ, int* err, uint32_t spin_limit, int withhold, cudaStream_t s) {
     const int64_t tiles = (max_count + TILE - 1) / TILE;
     const int64_t chunks = (tiles + RS_CHUNK - 1) / RS_CHUNK;
     cudaError_t e = launch_dependent(k_rs_count<KW, TILE>, dim3((unsigned)((tiles + RS_CT - 1) / RS_CT)), dim3(256), 0,
@@ -845,7 +854,7 @@ static cudaError_t rs_pass(const int64_t* count_ptr, int64_t max_count, const vo
     if (e != cudaSuccess) return e;
     e = launch_dependent(k_rs_scan, dim3((unsigned)chunks), dim3(256), 0, s, count_ptr, TILE,
                                      (const uint32_t*)A.cnt, digit_base, A.offs, A.flags, A.agg, A.inc, A.ctrs,
-                                     A.ctrs + 1, err);
+                                     A.ctrs + 1, err, spin_limit, withhold);
     if (e != cudaSuccess) return e;
     const int64_t grid = std::min<int64_t>(tiles, (int64_t)g_rs_sms * occ);
     e = launch_dependent(k_rs_move<KW, TILE, SP>, dim3((unsigned)grid), dim3(RS_BLOCK), rs_move_smem<KW, TILE, SP>(),
@@ -859,23 +868,25 @@ static cudaError_t rs_pass(const int64_t* count_ptr, int64_t max_count, const vo
 // (key >> shift) & 255: keys from key_src (written to key_dst when not
 // NULL), payload planes moved along (a NULL source means the position).
 // Key, payload and plane buffers must be 16-byte aligned and readable up to
-// the count rounded up to a multiple of 4 elements.
+// the count rounded up to a multiple of 4 elements.  spin_limit bounds the
+// scan's look-back polls; withhold is the failure-detection tests' switch
+// (k_rs_scan).
 cudaError_t launch_sort_pass(int key64, const int64_t* count_ptr, int64_t max_count, const void* key_src,
                              void* key_dst, const PayloadArgs& pay, const uint32_t* digit_base, int shift,
-                             uint32_t* status, int* err, cudaStream_t s) {
+                             uint32_t* status, int* err, cudaStream_t s, uint32_t spin_limit, int withhold) {
     if (max_count == 0) return cudaSuccess;
     if (g_rs_sms == 0) return cudaErrorInvalidValue;
     const SortStatusArea A = sort_status_layout(max_count, status);
     const bool many = pay.n > 1;
     if (key64)
         return many ? rs_pass<uint64_t, 1024, 4>(count_ptr, max_count, key_src, key_dst, pay, digit_base, shift, A,
-                                                 g_rs_occ[3], err, s)
+                                                 g_rs_occ[3], err, spin_limit, withhold, s)
                     : rs_pass<uint64_t, 2048, 1>(count_ptr, max_count, key_src, key_dst, pay, digit_base, shift, A,
-                                                 g_rs_occ[2], err, s);
+                                                 g_rs_occ[2], err, spin_limit, withhold, s);
     return many ? rs_pass<uint32_t, 2048, 2>(count_ptr, max_count, key_src, key_dst, pay, digit_base, shift, A,
-                                             g_rs_occ[1], err, s)
+                                             g_rs_occ[1], err, spin_limit, withhold, s)
                 : rs_pass<uint32_t, 2048, 1>(count_ptr, max_count, key_src, key_dst, pay, digit_base, shift, A,
-                                             g_rs_occ[0], err, s);
+                                             g_rs_occ[0], err, spin_limit, withhold, s);
 }
 
 template <typename KW, int TILE, int SP>

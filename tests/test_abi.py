@@ -60,3 +60,21 @@ def test_null_arguments_are_rejected_without_a_gpu(lib):
     assert lib.kd_build(None, None, None) == -1
     assert lib.kd_destroy(None) == -1
     assert lib.kd_launch_count(None) == 0
+
+
+def test_noalloc_binding_refuses_unsafe_output_buffers():
+    """The allocation-free entry point writes through raw pointers; the
+    binding refuses a buffer of the wrong type, size, layout or device
+    before any call (a tensor on another device needs no second GPU to
+    check: a CPU tensor stands for it)."""
+    import torch
+    from paper_1410_5420_gb300 import api
+    with pytest.raises(ValueError):  # a buffer on another device than the context's
+        api._check_out_buffer("arrays_out", torch.empty((3, 10), dtype=torch.int32), torch.device("cuda", 1), 30)
+    here = torch.device("cpu")
+    api._check_out_buffer("arrays_out", torch.empty((3, 10), dtype=torch.int32), here, 30)
+    for t in (torch.empty((3, 9), dtype=torch.int32),                     # too small
+              torch.empty((3, 10), dtype=torch.int64),                    # wrong type
+              torch.empty((10, 3), dtype=torch.int32).t()):               # not contiguous
+        with pytest.raises(ValueError):
+            api._check_out_buffer("arrays_out", t, here, 30)

@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 import kdgen
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -43,6 +44,8 @@ def test_noalloc_equals_kd_presort_two_calls(cuda_lib, case):
     try:
         dev = torch.from_numpy(np.ascontiguousarray(coords)).cuda()
         ref, m_ref = reference_arrays(cuda_lib, ctx, dev)
+        # the existing entry point and the oracle agree on this cloud
+        np.testing.assert_array_equal(ref, oracle.presort(coords), err_msg=name)
         n, k = coords.shape
         out = torch.full((k, n), -7, dtype=torch.int32, device="cuda")
         m_out = torch.full((1,), -7, dtype=torch.int32, device="cuda")
@@ -51,7 +54,9 @@ def test_noalloc_equals_kd_presort_two_calls(cuda_lib, case):
             torch.cuda.synchronize()
             m = int(m_out.item())
             assert m == m_ref, (name, call)
-            np.testing.assert_array_equal(out[:, :m].cpu().numpy(), ref, err_msg=f"{name} call {call}")
+            got = out.cpu().numpy()
+            np.testing.assert_array_equal(got[:, :m], ref, err_msg=f"{name} call {call}")
+            assert (got[:, m:] == -7).all(), f"{name} call {call}: entries past m were written"
             out.fill_(-7)
             m_out.fill_(-7)
     finally:
@@ -72,9 +77,21 @@ def test_noalloc_limits_and_errors(cuda_lib):
         assert e.value.code == -1
         bad = kdgen.cloud_gmm(300, 3, 5)
         bad[17, 2] = np.nan
-        out, m_out = cuda_lib.kd_presort_noalloc(ctx, torch.from_numpy(bad).cuda())
+        out = torch.full((3, 300), -7, dtype=torch.int32, device="cuda")
+        out, m_out = cuda_lib.kd_presort_noalloc(ctx, torch.from_numpy(bad).cuda(), out)
         torch.cuda.synchronize()
         assert int(m_out.item()) == -6
+        assert (out.cpu().numpy() == -7).all(), "a NaN must leave arrays_out untouched"
+        # buffers the library cannot write safely are refused before the call
+        okc = torch.from_numpy(kdgen.cloud_gmm(300, 3, 6)).cuda()
+        for bad_out in (torch.empty((3, 299), dtype=torch.int32, device="cuda"),
+                        torch.empty((3, 300), dtype=torch.int64, device="cuda"),
+                        torch.empty((300, 3), dtype=torch.int32, device="cuda").t(),
+                        torch.empty((3, 300), dtype=torch.int32)):
+            with pytest.raises(ValueError):
+                cuda_lib.kd_presort_noalloc(ctx, okc, bad_out)
+        with pytest.raises(ValueError):
+            cuda_lib.kd_presort_noalloc(ctx, okc, None, torch.empty(1, dtype=torch.int64, device="cuda"))
         # the context and the workspace stay usable after the NaN report
         ok = torch.from_numpy(kdgen.cloud_gmm(300, 3, 6)).cuda()
         ref, m_ref = reference_arrays(cuda_lib, ctx, ok)

@@ -3,13 +3,21 @@ cloud on one GB300, through the C ABI.
 
 One step = kd_presort + kd_build of the whole cloud (transform, presort,
 dedup, rank records, every tree level, on-chip finisher, tree outputs).
-``value``: points/s with the coordinates already resident in HBM.
+``value``: points/s with the coordinates already resident in HBM, timed with
+CUDA events around the steps (no per-launch events in that region).
 ``e2e``: the same call fed from pinned host memory with host outputs
 (host->device copy of the coordinates and device->host copy of the whole
 tree inside the timed region).  ``roofline``: the dominant kernel family's
-algorithmic bytes / its CUDA-event time on the library's stream, against
-the measured HBM copy bandwidth.  ``cpu_baseline``: the single-threaded C
-oracle on a bounded sample of the same workload.
+bytes per launch under the fixed byte model of the scope table (sort pass:
+2(w+4) B per element; level step: 12(k-1) B per element; ...) divided by its
+average launch time, from CUDA events recorded around every launch on the
+library's stream over a second timed region of the same steps; the
+builder's own per-kernel byte model is reported beside it.
+``cpu_baseline``: the single-threaded C oracle on a bounded sample of the
+same workload.  ``batched``: the 4096-cloud workload in one kd_build_batch
+call against per-cloud builds (serial, and pipelined over host threads).
+``served``: the 20000-request Poisson stream through kd_submit / kd_wait
+against serial plain builds.
 
 Multi-GPU: the build does not shard; ``--gpus N`` under torchrun runs N
 independent replicas (weak scaling, no collective on the data path).
@@ -50,16 +58,18 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--n", type=int, default=N_POINTS, help="points per cloud (default 2^26)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched and served results inside the default line")
     ap.add_argument("--cpu-sample", type=int, default=1 << 24,
                     help="cpu_baseline: oracle sample size in points (2^24: about 15 s of one core)")
     ap.add_argument("--ref-sample", type=int, default=1 << 21,
                     help="--impl reference: oracle sample per step in points (about 2 s of one core)")
     ap.add_argument("--mode", default="plain", choices=["plain", "batched", "served", "sweep", "knn"],
-                    help="plain: the 2^26 build (default line); batched: 4096 uneven clouds in one call "
-                         "vs per-cloud calls; served: a Poisson request stream through kd_submit; "
-                         "sweep: n=2^22 at k=2..6; knn: searches over a 2^22-tuple tree")
+                    help="plain: the 2^26 build (default line, with batched and served inside); batched / "
+                         "served: only those results; sweep: n=2^22 at k=2..6; knn: searches over a "
+                         "2^22-tuple tree")
     ap.add_argument("--clouds", type=int, default=4096)
-    ap.add_argument("--requests", type=int, default=2000)
+    ap.add_argument("--requests", type=int, default=20000)
     return ap.parse_args()
 
 
@@ -95,6 +105,31 @@ def measured_peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return FALLBACK_HBM_GBS, "fallback"
+
+
+NOMINAL_HBM_GBS = 8000.0
+
+
+def scope_byte_model(k: int, s: int, w: int, W: int, m: int) -> dict:
+    """The algorithmic byte model fixed before the build (per point, and per
+    unit of each kernel family).  k dimensions, s coordinate bytes, w key
+    word bytes, W significant key bits per coordinate, m tuples after
+    duplicate removal; D = ceil(W / 8) digit passes per coordinate, L =
+    ceil(log2(m + 1)) levels, L_g = max(0, L - 11) levels in HBM."""
+    D = (W + 7) // 8
+    L = max(1, int(m).bit_length())
+    Lg = max(0, L - 11)
+    per_unit = {
+        "transform": 2 * k * s,             # per input tuple
+        "sort_pass": 2 * (w + 4),           # per element of a digit pass
+        "gather": w,                        # per element of a key gather
+        "dedup": 8 + k * w,                 # per input tuple
+        "level_pass": (k - 1) * 12,         # per element of a level step
+        "finish": k * 8 + 4,                # per tuple
+    }
+    per_point = (per_unit["transform"] + (2 * k - 1) * D * per_unit["sort_pass"] + (2 * k - 1) * w
+                 + per_unit["dedup"] + Lg * per_unit["level_pass"] + per_unit["finish"])
+    return {"per_point": per_point, "per_unit": per_unit, "D": D, "L": L, "L_g": Lg}
 
 
 class ClockSampler:
@@ -220,47 +255,78 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def run_batched(args):
-    """4096 clouds, sizes floor(2^U(6,16)), float32 unit cube, 0.5% duplicates:
-    one kd_build_batch call vs one kd_presort + kd_build per cloud."""
+def batched_result(args, dev_index=0):
+    """4096 clouds, sizes floor(2^U(6,16)), float32 unit cube, 0.5% duplicates
+    (seed 4): one kd_build_batch call against per-cloud kd_presort +
+    kd_build, both serial (one host round trip per cloud) and pipelined over
+    host threads, each with its own context and stream (the round trips of
+    one thread overlap the device work of the others)."""
+    import threading
     import torch
     import kdgen
     from paper_1410_5420_gb300 import api
     clouds = kdgen.batch_clouds(count=args.clouds, seed=4)
-    pts = sum(c.shape[0] for c in clouds)
-    dev = [torch.from_numpy(c).cuda() for c in clouds]
-    stream = torch.cuda.current_stream()
-    ctx = api.kd_create(0, stream=stream)
+    pts = int(sum(c.shape[0] for c in clouds))
+    dev = [torch.from_numpy(c).cuda(dev_index) for c in clouds]
+    stream = torch.cuda.current_stream(dev_index)
+    ctx = api.kd_create(dev_index, stream=stream)
 
-    def batched():
-        return api.kd_build_batch(ctx, dev)
-
-    def plain():
-        return [api.build_tree(ctx, x) for x in dev]
-
-    out = {}
-    for name, fn, reps in (("batched", batched, args.steps), ("plain_per_cloud", plain, 1)):
+    def timed(fn, reps):
         for _ in range(max(1, min(args.warmup, 2))):
             fn()
-        torch.cuda.synchronize()
+        torch.cuda.synchronize(dev_index)
+        t0 = time.perf_counter()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(reps):
-            res = fn()
+            r = fn()
         e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / reps
-        out[name] = {"ms": ms, "points_per_s": pts / (ms / 1000.0)}
-    same = all(torch.equal(a["node_tuple"], b["node_tuple"]) for a, b in zip(batched(), plain()))
-    line = {"metric": METRIC, "mode": "batched", "value": out["batched"]["points_per_s"], "unit": UNIT,
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["batched"]["ms"],
-            "higher_is_better": True, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": f"batched: {args.clouds} clouds, sizes floor(2^U(6,16)), k=3 float32 unit "
-                                   f"cube, 0.5% duplicates (seed 4)", "points": pts},
-            "plain_per_cloud": out["plain_per_cloud"], "trees_identical": bool(same),
-            "speedup_vs_plain": out["batched"]["points_per_s"] / out["plain_per_cloud"]["points_per_s"]}
-    print(json.dumps(line), flush=True)
+        torch.cuda.synchronize(dev_index)
+        return max(e0.elapsed_time(e1), 1000 * (time.perf_counter() - t0)) / reps, r
+
+    ms_b, outs = timed(lambda: api.kd_build_batch(ctx, dev), args.steps)
+    ms_s, singles = timed(lambda: [api.build_tree(ctx, x) for x in dev], 1)
+    same = all(torch.equal(outs[i]["node_tuple"], singles[i]["node_tuple"])
+               and torch.equal(outs[i]["left"], singles[i]["left"]) for i in range(len(dev)))
+    del singles
+    nthreads = 4
+    streams = [torch.cuda.Stream(dev_index) for _ in range(nthreads)]
+    ctxs = [api.kd_create(dev_index, stream=st) for st in streams]
+
+    def pipelined():
+        def work(t):
+            for i in range(t, len(dev), nthreads):
+                api.build_tree(ctxs[t], dev[i])
+        th = [threading.Thread(target=work, args=(t,)) for t in range(nthreads)]
+        for x in th:
+            x.start()
+        for x in th:
+            x.join()
+        torch.cuda.synchronize(dev_index)
+
+    pipelined()
+    t0 = time.perf_counter()
+    pipelined()
+    ms_p = 1000 * (time.perf_counter() - t0)
+    for c in ctxs:
+        c.close()
     ctx.close()
+    return {"workload": f"{args.clouds} clouds, sizes floor(2^U(6,16)), k=3 float32 unit cube, 0.5% duplicates "
+                        f"(seed 4)", "points": pts, "ms": ms_b, "points_per_s": pts / (ms_b / 1000.0),
+            "plain_per_cloud_serial": {"ms": ms_s, "points_per_s": pts / (ms_s / 1000.0)},
+            "plain_per_cloud_pipelined": {"ms": ms_p, "points_per_s": pts / (ms_p / 1000.0),
+                                          "host_threads": nthreads},
+            "speedup_vs_serial": ms_s / ms_b, "speedup_vs_pipelined": ms_p / ms_b,
+            "trees_identical": bool(same)}
+
+
+def run_batched(args):
+    r = batched_result(args)
+    line = {"metric": METRIC, "mode": "batched", "value": r["points_per_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True,
+            "dtype": "u32", "data": "synthetic", "config": {"workload": "batched: " + r["workload"],
+                                                           "points": r["points"]}, "batched": r}
+    print(json.dumps(line), flush=True)
 
 
 def run_sweep(args):
@@ -363,57 +429,100 @@ def run_knn(args):
     ctx.close()
 
 
-def run_served(args):
+def host_mem_gb() -> float:
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) / (1 << 20)
+    except OSError:
+        pass
+    return 0.0
+
+
+def served_result(args, dev_index=0):
     """Poisson stream of build requests through kd_submit / kd_wait: sizes
-    log-uniform in [2^8, 2^20], k in {2,3,4}, int32 or float32 mixture
-    (the first --requests of the stream); arrival rate 0.8x the measured
-    serial plain throughput, then a saturation run."""
+    log-uniform in [2^8, 2^20], k in {2,3,4}, int32 uniform in [0, 2^24) or
+    float32 mixture (seed 5).  Serial plain builds of every request (host
+    in, host out) first; then the stream at 0.8x that rate (p50 / p99
+    latency from admission to result); then every request at once
+    (saturation)."""
     import threading
-    import torch
+    from concurrent.futures import ThreadPoolExecutor
     import kdgen
     from paper_1410_5420_gb300 import api
     reqs = kdgen.serving_requests(count=args.requests, seed=5, lo_log2=8.0, hi_log2=20.0)
-    clouds = [kdgen.serving_cloud(*r) for r in reqs]
-    pts = sum(c.shape[0] for c in clouds)
-    ctx = api.kd_create(0, mem_budget_bytes=64 << 30)
-    # serial plain builds (host in, host out) on the same GPU
+    est_gb = sum(r[0] * r[1] * 4 for r in reqs) / 2 ** 30
+    count = len(reqs)
+    if est_gb * 2.5 > host_mem_gb() > 0:  # coordinates plus the library's request copies
+        count = max(100, int(count * host_mem_gb() / (est_gb * 2.5)))
+        reqs = reqs[:count]
+    with ThreadPoolExecutor(max(1, min(16, os.cpu_count() or 1))) as pool:  # numpy releases the GIL
+        clouds = list(pool.map(lambda r: kdgen.serving_cloud(*r), reqs))
+    pts = int(sum(c.shape[0] for c in clouds))
+    ctx = api.kd_create(dev_index, mem_budget_bytes=64 << 30)
     for c in clouds[:20]:
-        api.build_tree(ctx, c)
+        api.build_tree(ctx, c, children=False)
     t0 = time.perf_counter()
     for c in clouds:
-        api.build_tree(ctx, c)
+        api.build_tree(ctx, c, children=False)
     serial_s = time.perf_counter() - t0
-    serial_pps = pts / serial_s
     rate = 0.8 * len(clouds) / serial_s
     arrivals = kdgen.poisson_arrivals(len(clouds), rate, seed=5)
-    tickets = [None] * len(clouds)
-    t0 = time.perf_counter()
-    for i, c in enumerate(clouds):
-        delay = arrivals[i] - (time.perf_counter() - t0)
-        if delay > 0:
-            time.sleep(delay)
-        tickets[i] = api.kd_submit(ctx, c)
-    for t in tickets:
-        api.kd_wait(ctx, t)
-    served_s = time.perf_counter() - t0
+
+    def stream_run(paced: bool):
+        # a waiter thread collects results as they finish, so outputs are
+        # dropped early and the submitter never blocks on a result
+        q, done = [], threading.Event()
+        lock = threading.Condition()
+
+        def waiter():
+            i = 0
+            while i < len(clouds):
+                with lock:
+                    while i >= len(q):
+                        lock.wait()
+                    t = q[i]
+                api.kd_wait(ctx, t)
+                q[i] = None
+                i += 1
+            done.set()
+
+        th = threading.Thread(target=waiter)
+        th.start()
+        t0 = time.perf_counter()
+        for i, c in enumerate(clouds):
+            if paced:
+                delay = arrivals[i] - (time.perf_counter() - t0)
+                if delay > 0:
+                    time.sleep(delay)
+            t = api.kd_submit(ctx, c, children=False)
+            with lock:
+                q.append(t)
+                lock.notify()
+        done.wait()
+        th.join()
+        return time.perf_counter() - t0
+
+    paced_s = stream_run(True)
     st = api.kd_serving_stats(ctx)
-    # saturation: everything submitted at once
-    t1 = time.perf_counter()
-    ts = [api.kd_submit(ctx, c) for c in clouds]
-    for t in ts:
-        api.kd_wait(ctx, t)
-    sat_s = time.perf_counter() - t1
-    line = {"metric": METRIC, "mode": "served", "value": pts / sat_s, "unit": UNIT, "n_gpus": 1,
-            "higher_is_better": True, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": f"served: {len(clouds)} Poisson requests, sizes log-U[2^8,2^20], k in {{2,3,4}}, "
-                                   f"int32 U[0,2^24) or float32 mixture (seed 5)", "points": pts,
-                       "rate_per_s": rate},
-            "poisson": {"points_per_s": pts / served_s, "p50_us": st["p50_us"], "p99_us": st["p99_us"],
-                        "completed": st["completed"]},
-            "saturation_points_per_s": pts / sat_s, "serial_plain_points_per_s": serial_pps,
-            "speedup_vs_serial_plain": (pts / sat_s) / serial_pps}
-    print(json.dumps(line), flush=True)
+    sat_s = stream_run(False)
     ctx.close()
+    return {"workload": f"{len(clouds)} Poisson requests of the stream (seed 5), sizes log-U[2^8,2^20], "
+                        f"k in {{2,3,4}}, int32 U[0,2^24) or float32 mixture; 64 GB budget",
+            "requests": len(clouds), "requests_in_stream": args.requests, "points": pts, "rate_per_s": rate,
+            "poisson": {"points_per_s": pts / paced_s, "p50_us": st["p50_us"], "p99_us": st["p99_us"],
+                        "completed": st["completed"]},
+            "saturation_points_per_s": pts / sat_s, "serial_plain_points_per_s": pts / serial_s,
+            "speedup_vs_serial_plain": serial_s / sat_s}
+
+
+def run_served(args):
+    r = served_result(args)
+    line = {"metric": METRIC, "mode": "served", "value": r["saturation_points_per_s"], "unit": UNIT,
+            "n_gpus": 1, "higher_is_better": True, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "served: " + r["workload"], "points": r["points"]}, "served": r}
+    print(json.dumps(line), flush=True)
 
 
 def main():
@@ -448,39 +557,49 @@ def main():
     pinned = torch.from_numpy(coords_h).pin_memory()
     x = pinned.cuda(dev)
     stream = torch.cuda.current_stream(dev)
-    ctx = api.kd_create(dev, stream=stream, debug=2)
+    ctx = api.kd_create(dev, stream=stream)
 
     def barrier():
         if world > 1:
             import torch.distributed as dist
             dist.barrier()
 
-    def step():
-        return api.build_tree(ctx, x, children=True, on_device=True)
+    def step(c):
+        return api.build_tree(c, x, children=True, on_device=True)
+
+    def timed_steps(c, steps):
+        barrier()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            step(c)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        return e0.elapsed_time(e1) / steps
 
     for _ in range(max(1, args.warmup)):
-        t = step()
+        t = step(ctx)
     m = t["m"]
-    api.kd_kernel_stats_reset(ctx)
+    del t
     launches0 = api.kd_launch_count(ctx)
     clocks = ClockSampler(dev)
-    barrier()
-    torch.cuda.synchronize(dev)
     clocks.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        step()
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    barrier()
+    ms_step = timed_steps(ctx, args.steps)
     clk = clocks.stop()
-    ms_total = e0.elapsed_time(e1)
     launches = api.kd_launch_count(ctx) - launches0
-    stats = api.kd_kernel_stats(ctx)
-    ms_per_step = max_over_ranks(ms_total / args.steps, world, f"cuda:{dev}")
+    ms_per_step = max_over_ranks(ms_step, world, f"cuda:{dev}")
     value = whole_job_value(world, n, ms_per_step / 1000.0)
+
+    # the same steps again with CUDA events around every launch (per-kernel times)
+    ctx_t = api.kd_create(dev, stream=stream, debug=2)
+    step(ctx_t)
+    api.kd_kernel_stats_reset(ctx_t)
+    ms_step_events = timed_steps(ctx_t, args.steps)
+    stats = api.kd_kernel_stats(ctx_t)
+    ctx_t.close()
 
     # end to end: pinned host coordinates in, whole tree back to pinned host
     out_node = torch.empty(n, dtype=torch.int32).pin_memory()
@@ -521,21 +640,32 @@ def main():
             dist.destroy_process_group()
         return
 
-    # roofline of the dominant kernel family
+    # roofline of the dominant kernel family under the fixed byte model
     peak, peak_src = measured_peaks()
+    model = scope_byte_model(K, 4, 4, 32, m)
     fam = max(stats, key=lambda f: stats[f]["ms"])
     st = stats[fam]
-    per_launch_bytes = st["bytes"] / max(st["launches"], 1)
-    per_launch_ms = st["ms"] / max(st["launches"], 1)
-    achieved = per_launch_bytes / (per_launch_ms / 1000.0) / 1e9 if per_launch_ms > 0 else 0.0
+    nl = max(st["launches"], 1)
+    per_launch_ms = st["ms"] / nl
+    units_per_launch = st["units"] / nl
+
+    def gbs(bytes_per_launch, ms):
+        return bytes_per_launch / (ms / 1000.0) / 1e9 if ms > 0 else 0.0
+
+    achieved = gbs(model["per_unit"].get(fam, 0) * units_per_launch, per_launch_ms)
+    achieved_own = gbs(st["bytes"] / nl, per_launch_ms)
     tr = traffic_for(fam)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": (tr * st["units"] / max(st["launches"], 1)) if tr is not None else None,
-            "kernel": fam, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
+            "traffic": (tr * units_per_launch) if tr is not None else None,
+            "kernel": fam, "bytes_per_unit": model["per_unit"].get(fam, 0),
+            "bytes_model": "fixed scope-table model: sort pass 2(w+4) B per element, level step 12(k-1) B "
+                           "per element, transform 2ks, dedup 8+kw, finisher 8k+4 B per tuple",
+            "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
             else "fallback 6.8 TB/s",
-            "step_share": st["ms"] / args.steps / ms_per_step}
-    total_bytes = sum(v["bytes"] for v in stats.values()) / args.steps
-    kernel_ms = sum(v["ms"] for v in stats.values()) / args.steps
+            "own_model": {"achieved": achieved_own, "frac": achieved_own / peak},
+            "step_share": st["ms"] / args.steps / ms_step_events}
+    model_bytes = model["per_point"] * n
+    own_bytes = sum(v["bytes"] for v in stats.values()) / args.steps
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -543,17 +673,29 @@ def main():
         "config": {"workload": WORKLOAD, "n": n, "k": K, "m": m, "seed": SEED, "parallelism": f"replicas{world}",
                    "l2": "inputs (768 MiB coordinates, GBs of index arrays) exceed the 126 MB L2; no flush"},
         "roofline": roof,
-        "step_model": {"algorithmic_bytes": total_bytes, "kernel_ms": kernel_ms,
-                       "achieved_gbs": total_bytes / (kernel_ms / 1000.0) / 1e9 if kernel_ms else None,
-                       "frac_of_measured": (total_bytes / (kernel_ms / 1000.0) / 1e9) / peak if kernel_ms else None},
+        "step_model": {"bytes_per_point": model["per_point"], "bytes": model_bytes,
+                       "achieved_gbs": model_bytes / (ms_per_step / 1000.0) / 1e9,
+                       "frac_of_measured": model_bytes / (ms_per_step / 1000.0) / 1e9 / peak,
+                       "frac_of_nominal_8tbs": model_bytes / (ms_per_step / 1000.0) / 1e9 / NOMINAL_HBM_GBS,
+                       "own_model_bytes": own_bytes,
+                       "own_model_frac_of_measured": own_bytes / (ms_per_step / 1000.0) / 1e9 / peak},
         "kernels": {f: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
-                        "gbs": (v["bytes"] / (v["ms"] / 1000.0) / 1e9) if v["ms"] else None}
+                        "model_gbs": gbs(model["per_unit"].get(f, 0) * v["units"], v["ms"]) or None,
+                        "own_gbs": gbs(v["bytes"], v["ms"]) or None}
                     for f, v in stats.items() if v["launches"]},
+        "ms_per_step_with_launch_events": ms_step_events,
         "clocks": clk,
         "e2e": {"value": whole_job_value(world, n, e2e_s), "unit": UNIT, "h2d_bytes_per_step": n * K * 4,
                 "d2h_bytes_per_step": m * 13},
         "gpu_launches": launches,
     }
+    ctx.close()
+    del x
+    torch.cuda.empty_cache()
+    if not args.no_extras and world == 1:
+        line["batched"] = batched_result(args, dev)
+        torch.cuda.empty_cache()
+        line["served"] = served_result(args, dev)
     if not args.no_cpu_baseline and world >= 1:
         try:
             line["cpu_baseline"] = cpu_baseline(min(args.cpu_sample, n))
@@ -561,7 +703,6 @@ def main():
             line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
                                     "sample": f"unavailable: {ex}"}
     print(json.dumps(line), flush=True)
-    ctx.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

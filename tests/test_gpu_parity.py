@@ -177,65 +177,3 @@ def test_batch_host_buffers_int64(cuda_lib, ctx):
     outs = cuda_lib.kd_build_batch(ctx, clouds)
     for c, got in zip(clouds, outs):
         assert_same_tree(got, oracle.build_tree(c))
-
-
-def _check_sampled_paths(coords, node, m, k, samples, rng):
-    """Every sampled address is on the correct side of each ancestor in the
-    ancestor's split dimension (cyclic super key), and ancestors sit at the
-    lower-median addresses: together with node_tuple being exactly the
-    unique tuples, this pins the unique balanced tree."""
-    c = coords
-    for i in rng.integers(0, m, size=samples):
-        lo, hi, depth = 0, m - 1, 0
-        ti = tuple(c[node[i]])
-        while True:
-            mid = lo + (hi - lo) // 2
-            if mid == i:
-                break
-            p = depth % k
-            key_i = tuple(ti[(p + j) % k] for j in range(k))
-            tm = tuple(c[node[mid]])
-            key_m = tuple(tm[(p + j) % k] for j in range(k))
-            if i < mid:
-                assert key_i < key_m
-                hi = mid - 1
-            else:
-                assert key_i > key_m
-                lo = mid + 1
-            depth += 1
-
-
-@pytest.mark.slow
-def test_full_size_large_workload_properties(cuda_lib, ctx):
-    """n = 2^26 float32 mixture, the benchmark's launch configuration."""
-    import torch
-    coords = kdgen.large_gmm()
-    x = torch.from_numpy(coords).cuda()
-    t = cuda_lib.build_tree(ctx, x)
-    m = t["m"]
-    node = to_np(t["node_tuple"])
-    # node_tuple is exactly the set of first representatives of distinct tuples
-    v = coords.view(np.uint32).copy()
-    v[v == 0x80000000] = 0  # -0.0 is +0.0
-    order = np.lexsort((np.arange(len(v)),) + tuple(v[:, j] for j in range(2, -1, -1)))
-    rows = v[order]
-    first = np.ones(len(v), dtype=bool)
-    first[1:] = np.any(rows[1:] != rows[:-1], axis=1)
-    reps = np.sort(order[first])
-    assert m == len(reps)
-    np.testing.assert_array_equal(np.sort(node), reps.astype(np.int32))
-    # children / dims are the shape's (pure function of m) on sampled addresses
-    rng = np.random.default_rng(0)
-    left, right, dim = to_np(t["left"]), to_np(t["right"]), to_np(t["dim"])
-    for a in rng.integers(0, m, 2000):
-        lo, hi, depth = 0, m - 1, 0
-        while True:
-            mid = lo + (hi - lo) // 2
-            if mid == a:
-                break
-            lo, hi = (lo, mid - 1) if a < mid else (mid + 1, hi)
-            depth += 1
-        assert dim[a] == depth % 3
-        assert left[a] == (-1 if a - 1 < lo else lo + (a - 1 - lo) // 2)
-        assert right[a] == (-1 if hi < a + 1 else a + 1 + (hi - a - 1) // 2)
-    _check_sampled_paths(coords.astype(np.float64), node, m, 3, 20000, rng)

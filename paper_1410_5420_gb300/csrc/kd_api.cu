@@ -63,12 +63,6 @@ cudaError_t launch_finish(const AllBufs& bufs, int k, const int64_t* unit_prefix
                           unsigned long long* phase_ns, cudaStream_t s);
 cudaError_t launch_top_nodes(const CloudDev* clouds, const int64_t* prefix, int ncloud, int64_t total, int k,
                              const uint32_t* perm0, uint32_t* medr, int all_nodes, cudaStream_t s);
-int finish_packed_kmax();
-int finish_packed_smax();
-cudaError_t init_finish_packed();
-cudaError_t launch_finish_packed(const AllBufs& bufs, int k, const int64_t* unit_prefix, int ncloud,
-                                 int64_t unit_base, int nunits, const CloudDev* clouds, const uint32_t* perm0,
-                                 int* err, cudaStream_t s);
 }  // namespace kd
 
 using namespace kd;
@@ -1083,22 +1077,14 @@ kd_status build_batch(kd_ctx* ctx, kd_presorted* H, kd_tree* outs) {
             CK(cudaMemsetAsync(phase, 0, sizeof(unsigned long long) * 8, s));
         }
         const int64_t m0 = cd[0].m;
-        // subtrees of at most 1024 tuples and k <= 6: the packed-word
-        // finisher (kd_finish.cu); otherwise, and for the phase counters,
-        // the label finisher
-        const bool packed = smax == finish_packed_smax() && k <= finish_packed_kmax() && !phase;
-        const double fin_bytes = packed ? 4.0 * k + 8.0 : 4.0 * (2 * k - 1) + 8.0;
+        const double fin_bytes = 4.0 * (2 * k - 1) + 8.0;
         for (int c = 0; c < nchunks; ++c) {
             const int64_t u0 = nunits * c / nchunks, u1 = nunits * (c + 1) / nchunks;
             {
                 LaunchTimer lt(ctx, F_FINISH, (double)M * (u1 - u0) / nunits, nullptr,
                                fin_bytes + (want_l ? 4 : 0) + (want_r ? 4 : 0) + (want_d ? 1 : 0));
-                if (packed)
-                    CK(launch_finish_packed(bufs, k, d_uprefix, count, u0, (int)(u1 - u0), d_cd, H->perm0, d_err,
-                                            s));
-                else
-                    CK(launch_finish(bufs, k, d_uprefix, count, u0, (int)(u1 - u0), d_cd, H->perm0, smax, d_err,
-                                     phase, s));
+                CK(launch_finish(bufs, k, d_uprefix, count, u0, (int)(u1 - u0), d_cd, H->perm0, smax, d_err, phase,
+                                 s));
             }
             if (overlap_copy) {
                 // addresses [a0, a1): from the first unit's start (0 for the
@@ -1290,8 +1276,7 @@ kd_status kd_create(kd_ctx** out, const kd_config* cfg) {
     {
         std::lock_guard<std::mutex> lk(init_mu);
         if (c.device < 64 && !init_done[c.device]) {
-            if (init_presort_kernels() != cudaSuccess || init_build_kernels() != cudaSuccess ||
-                init_finish_packed() != cudaSuccess) {
+            if (init_presort_kernels() != cudaSuccess || init_build_kernels() != cudaSuccess) {
                 cudaGetLastError();
                 return KD_EDEVICE;
             }

@@ -233,25 +233,38 @@ __global__ void __launch_bounds__(256) k_rs_scan(const int64_t* __restrict__ cou
     }
 }
 
+// The tile is ordered by digit in shared memory before it is written out.
+// 32-bit keys: in place, over the key and payload words of the stage the
+// tile came in (every value is in registers by then).  64-bit keys: in a
+// separate buffer of TILE key words.
+template <typename KW>
+constexpr bool rs_inplace() { return sizeof(KW) == 4; }
+
 template <typename KW, int TILE, int SP>
 constexpr size_t rs_move_smem() {
-    // two stages, then the sorted tile: keys, or key + payload pairs for
-    // 32-bit keys with one payload plane
-    const size_t sorted = sizeof(KW) == 4 ? (size_t)TILE * (SP == 1 ? 2 : 3) : (size_t)TILE * 2;
-    return ((size_t)2 * (RADIX + TILE * (sizeof(KW) / 4) + SP * TILE) + sorted) * 4;
+    return ((size_t)2 * (RADIX + TILE * (sizeof(KW) / 4) + SP * TILE) + (rs_inplace<KW>() ? 0 : (size_t)TILE * 2)) *
+           4;
+}
+
+// Resident blocks the move kernel is compiled for: as many as its shared
+// memory allows (32-bit keys: 4 with one staged payload, 3 with two).
+template <typename KW, int TILE, int SP>
+constexpr int rs_min_blocks() {
+    return rs_inplace<KW>() ? (SP == 1 ? 4 : 3) : 2;
 }
 
 template <typename KW, int TILE, int SP>
-__global__ void __launch_bounds__(RS_BLOCK, TILE * (SP + 1) * sizeof(KW) <= 2048 * 8 ? 3 : 2)
+__global__ void __launch_bounds__(RS_BLOCK, (rs_min_blocks<KW, TILE, SP>()))
     k_rs_move(const int64_t* __restrict__ count_ptr, const KW* __restrict__ key_src, KW* __restrict__ key_dst,
               const __grid_constant__ PayloadArgs pay, const uint32_t* __restrict__ offs, int shift,
               uint32_t* __restrict__ ctr, int* __restrict__ err) {
     constexpr int IPT = TILE / RS_THREADS;
     constexpr int KWW = sizeof(KW) / 4;
     constexpr int SW = RADIX + TILE * KWW + SP * TILE;  // stage words: offsets row | keys | payloads
-    constexpr bool PAIR = sizeof(KW) == 4 && SP == 1;   // key and payload sorted together
+    constexpr bool INPLACE = rs_inplace<KW>();
+    constexpr bool PAIR = sizeof(KW) == 4 && SP == 1;    // key and payload sorted together
     constexpr bool TRIPLE = sizeof(KW) == 4 && SP >= 2;  // key and two payloads: an 8-byte and a 4-byte word
-    extern __shared__ __align__(128) uint32_t rsm[];     // [2][SW] stages, then the sorted tile [TILE] keys
+    extern __shared__ __align__(128) uint32_t rsm[];     // [2][SW] stages (then the sorted tile for 64-bit keys)
     __shared__ __align__(8) uint64_t full[2], empty[2];
     __shared__ SortMeta meta[2];
     __shared__ uint32_t s_wc[RS_WARPS][RADIX];
@@ -310,8 +323,6 @@ __global__ void __launch_bounds__(RS_BLOCK, TILE * (SP + 1) * sizeof(KW) <= 2048
                 if (pay.src[p]) bulk_g2s(st + RADIX + TILE * KWW + p * TILE, pay.src[p] + M.base, pb, &full[s]);
         }
     }
-    KW* sbuf = reinterpret_cast<KW*>(rsm + (size_t)2 * SW);
-    uint32_t* sb32 = rsm + (size_t)2 * SW;
     const int wbase = warp * 32 * IPT;
     for (int it = 0;; ++it) {
         const int s = it & 1;
@@ -322,17 +333,31 @@ __global__ void __launch_bounds__(RS_BLOCK, TILE * (SP + 1) * sizeof(KW) <= 2048
         }
         const SortMeta M = meta[s];
         if (M.t < 0) break;
-        const uint32_t* st = rsm + (size_t)s * SW;
-        const KW* skeys = reinterpret_cast<const KW*>(st + RADIX);
-        // stable warp ranking through match words
+        uint32_t* st = rsm + (size_t)s * SW;
+        // the tile's keys and staged payloads into registers
+        KW kreg[IPT];
+        uint32_t preg[SP][IPT];
+        {
+            const KW* skeys = reinterpret_cast<const KW*>(st + RADIX);
+#pragma unroll
+            for (int j = 0; j < IPT; ++j) {
+                const int o = wbase + j * 32 + lane;
+                const bool v = o < M.n;
+                kreg[j] = v ? skeys[o] : (KW)0;
+#pragma unroll
+                for (int p = 0; p < SP; ++p) {
+                    const uint32_t* sp = st + RADIX + TILE * KWW + p * TILE;
+                    preg[p][j] = (p < pay.n && pay.src[p]) ? (v ? sp[o] : 0u) : (uint32_t)(M.base + o);
+                }
+            }
+        }
+        // stable warp ranking (match instruction or match words)
         uint32_t dig[IPT], slot[IPT];
 #pragma unroll
-        for (int j = 0; j < IPT; ++j) {
-            const int o = wbase + j * 32 + lane;
-            dig[j] = o < M.n ? digit_of(skeys[o], shift) : (uint32_t)RADIX;
-        }
+        for (int j = 0; j < IPT; ++j)
+            dig[j] = wbase + j * 32 + lane < M.n ? digit_of(kreg[j], shift) : (uint32_t)RADIX;
         warp_rank_adaptive<IPT>(dig, RADIX, s_wc[warp], s_match[warp], slot);
-        consumer_sync<RS_THREADS>();
+        consumer_sync<RS_THREADS>();  // every warp has ranked, and has read the stage into registers
         // digit tid: prefix over warps in place, tile count, tile start
         uint32_t c = 0;
 #pragma unroll
@@ -361,22 +386,18 @@ __global__ void __launch_bounds__(RS_BLOCK, TILE * (SP + 1) * sizeof(KW) <= 2048
             if (dig[j] < RADIX) slot[j] += s_tstart[dig[j]] + s_wc[warp][dig[j]];
         __syncwarp();
         for (int d = lane; d < RADIX; d += 32) s_wc[warp][d] = 0;  // own row, read above only by this warp
+        // the sorted tile: over this stage's keys and payloads, or a separate buffer
+        uint32_t* sb32 = INPLACE ? st + RADIX : rsm + (size_t)2 * SW;
+        KW* sbuf = reinterpret_cast<KW*>(sb32);
         if constexpr (PAIR) {
             if (pay.n == 1) {
                 // 32-bit keys with one payload: both go through the sorted
                 // tile as one 8-byte word
-                const uint32_t* src = pay.src[0];
-                const uint32_t* sp = st + RADIX + TILE * KWW;
                 uint2* sb2 = reinterpret_cast<uint2*>(sb32);
 #pragma unroll
-                for (int j = 0; j < IPT; ++j) {
-                    const int o = wbase + j * 32 + lane;
-                    if (dig[j] < RADIX)
-                        sb2[slot[j]] = make_uint2((uint32_t)skeys[o], src ? sp[o] : (uint32_t)(M.base + o));
-                }
+                for (int j = 0; j < IPT; ++j)
+                    if (dig[j] < RADIX) sb2[slot[j]] = make_uint2((uint32_t)kreg[j], preg[0][j]);
                 consumer_sync<RS_THREADS>();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&empty[s]);  // every read of the stage is behind the barrier
                 uint32_t* dst = pay.dst[0];
 #pragma unroll
                 for (int r = 0; r < IPT; ++r) {
@@ -392,6 +413,9 @@ __global__ void __launch_bounds__(RS_BLOCK, TILE * (SP + 1) * sizeof(KW) <= 2048
                         }
                     }
                 }
+                if (INPLACE) fence_proxy_async_smem();  // our writes to the stage before the next bulk copy into it
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[s]);  // this warp's reads of the stage are done
                 continue;
             }
         }
@@ -399,21 +423,14 @@ __global__ void __launch_bounds__(RS_BLOCK, TILE * (SP + 1) * sizeof(KW) <= 2048
             if (pay.n == 2) {
                 uint2* sb2 = reinterpret_cast<uint2*>(sb32);
                 uint32_t* sb1 = sb32 + 2 * TILE;
-                const uint32_t* src0 = pay.src[0];
-                const uint32_t* src1 = pay.src[1];
-                const uint32_t* sp0 = st + RADIX + TILE * KWW;
-                const uint32_t* sp1 = sp0 + TILE;
 #pragma unroll
                 for (int j = 0; j < IPT; ++j) {
-                    const int o = wbase + j * 32 + lane;
                     if (dig[j] < RADIX) {
-                        sb2[slot[j]] = make_uint2((uint32_t)skeys[o], src0 ? sp0[o] : (uint32_t)(M.base + o));
-                        sb1[slot[j]] = src1 ? sp1[o] : (uint32_t)(M.base + o);
+                        sb2[slot[j]] = make_uint2((uint32_t)kreg[j], preg[0][j]);
+                        sb1[slot[j]] = preg[1][j];
                     }
                 }
                 consumer_sync<RS_THREADS>();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&empty[s]);  // every read of the stage is behind the barrier
                 uint32_t* dst0 = pay.dst[0];
                 uint32_t* dst1 = pay.dst[1];
 #pragma unroll
@@ -431,12 +448,15 @@ __global__ void __launch_bounds__(RS_BLOCK, TILE * (SP + 1) * sizeof(KW) <= 2048
                         }
                     }
                 }
+                if (INPLACE) fence_proxy_async_smem();  // our writes to the stage before the next bulk copy into it
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[s]);  // this warp's reads of the stage are done
                 continue;
             }
         }
 #pragma unroll
         for (int j = 0; j < IPT; ++j)
-            if (dig[j] < RADIX) sbuf[slot[j]] = skeys[wbase + j * 32 + lane];
+            if (dig[j] < RADIX) sbuf[slot[j]] = kreg[j];
         consumer_sync<RS_THREADS>();
         // A destination outside [0, count) can only come from inconsistent
         // counts; it is reported and never written.
@@ -459,13 +479,16 @@ __global__ void __launch_bounds__(RS_BLOCK, TILE * (SP + 1) * sizeof(KW) <= 2048
         for (int p = 0; p < pay.n; ++p) {
             consumer_sync<RS_THREADS>();  // earlier readers of the sorted tile are done
             const uint32_t* src = pay.src[p];
-            const uint32_t* sp = st + RADIX + TILE * KWW + p * TILE;
-            const bool staged = p < SP && src != nullptr;
 #pragma unroll
             for (int j = 0; j < IPT; ++j) {
                 const int o = wbase + j * 32 + lane;
-                if (dig[j] < RADIX)
-                    sb32[slot[j]] = staged ? sp[o] : (src ? src[M.base + o] : (uint32_t)(M.base + o));
+                if (dig[j] < RADIX) {
+                    uint32_t val = src ? src[M.base + o] : (uint32_t)(M.base + o);
+#pragma unroll
+                    for (int q = 0; q < SP; ++q)
+                        if (q == p) val = preg[q][j];
+                    sb32[slot[j]] = val;
+                }
             }
             consumer_sync<RS_THREADS>();
             uint32_t* dst = pay.dst[p];
@@ -473,7 +496,8 @@ __global__ void __launch_bounds__(RS_BLOCK, TILE * (SP + 1) * sizeof(KW) <= 2048
             for (int r = 0; r < IPT; ++r)
                 if (dest[r] != 0xffffffffu) dst[dest[r]] = sb32[r * RS_THREADS + tid];
         }
-        // every read of this stage is behind the barriers above
+        // every read of this stage (and of the sorted tile over it) is behind the barriers above
+        if (INPLACE) fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
     }

@@ -57,13 +57,16 @@ typedef struct {
     int device;              /* CUDA device ordinal */
     void *cuda_stream;       /* cudaStream_t to order work on; NULL: the library makes its own */
     size_t mem_budget_bytes; /* cap on the library's device workspace; 0: no cap */
-    int tile_T;              /* 0: default.  Reserved for the autotuner */
-    int switch_threshold;    /* subtree size finished on chip (rounded up to 1024, 2048 or 4096, capped by k); 0: 1024 */
+    int level_tile;          /* positions per level-step tile: 1024, or 2048 (k <= 4); 0: tuned, else 2048 for
+                                k <= 4 and 1024 above */
+    int switch_threshold;    /* subtree size finished on chip (rounded up to 1024, 2048 or 4096, capped by k);
+                                0: tuned, else 1024 */
     int debug;               /* bit 1: synchronise after the presort; bit 2: time every launch
                                 (kd_kernel_stats); bit 4: finisher phase counters; bit 8
                                 (failure-detection tests): bound the device waits to a few
                                 thousand polls and make the next presort's first look-back
                                 wait run out once, which it reports as KD_ETIMEOUT */
+    const char *tune_cache;  /* autotuner cache file (read by kd_create, rewritten by kd_autotune); NULL: none */
 } kd_config;
 
 typedef struct {
@@ -159,6 +162,27 @@ kd_status kd_wait(kd_ctx *ctx, kd_ticket ticket, int timeout_ms);
 /* Serving statistics: completed requests and their admission-to-result
  * latency percentiles (microseconds). */
 kd_status kd_serving_stats(kd_ctx *ctx, int64_t *completed, double *p50_us, double *p99_us);
+
+/*
+ * Autotuner.  The on-chip subtree size (1024, 2048 or 4096 tuples, as k
+ * allows) and the level-step tile (1024 or 2048 positions) are chosen per
+ * (k, dtype, size bucket = floor(log2 n) of the largest cloud of a build).
+ * kd_autotune presorts a synthetic cloud of n tuples (uniform coordinates,
+ * generated on the device), times kd_build with every candidate pair (reps
+ * runs each, median of CUDA-event times on the context's stream), records
+ * the fastest for the bucket in the context, rewrites cfg->tune_cache when
+ * one was given, and returns it.  Later builds whose bucket has an entry use
+ * it unless cfg->switch_threshold or cfg->level_tile fix a value.  Every
+ * candidate builds the same tree.  Errors: KD_EINVAL (k, n, dtype or reps
+ * out of range), KD_ENOMEM, KD_EDEVICE.  Synchronises the stream.
+ */
+kd_status kd_autotune(kd_ctx *ctx, int k, kd_dtype dtype, int64_t n, int reps, int *switch_threshold_out,
+                      int *level_tile_out);
+
+/* The subtree size and level tile a build of clouds of at most n tuples
+ * (k, dtype) would use on this context now. */
+kd_status kd_tuning_get(kd_ctx *ctx, int k, kd_dtype dtype, int64_t n, int *switch_threshold_out,
+                        int *level_tile_out);
 
 /* Stop serving, free every device resource and the context. */
 kd_status kd_destroy(kd_ctx *ctx);

@@ -27,13 +27,13 @@ EXPORTS = ["kd_create", "kd_presort", "kd_handle_info", "kd_handle_arrays", "kd_
            "kd_build_batch", "kd_submit", "kd_wait", "kd_serving_stats", "kd_destroy", "kd_last_error",
            "kd_launch_count", "kd_kernel_stats", "kd_kernel_stats_reset", "kd_trace_counters",
            "kd_presort_noalloc", "kd_index_create", "kd_index_destroy", "kd_knn", "kd_region",
-           "kd_knn_all", "kd_reverse_knn"]
+           "kd_knn_all", "kd_reverse_knn", "kd_autotune", "kd_tuning_get"]
 
 
 class KdConfig(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
-                ("mem_budget_bytes", ctypes.c_size_t), ("tile_T", ctypes.c_int),
-                ("switch_threshold", ctypes.c_int), ("debug", ctypes.c_int)]
+                ("mem_budget_bytes", ctypes.c_size_t), ("level_tile", ctypes.c_int),
+                ("switch_threshold", ctypes.c_int), ("debug", ctypes.c_int), ("tune_cache", ctypes.c_char_p)]
 
 
 class KdCloud(ctypes.Structure):
@@ -86,6 +86,9 @@ def load():
         "kd_region": ([vp, vp, vp, vp, i64, ctypes.c_int, vp, vp, i64], ctypes.c_int),
         "kd_knn_all": ([vp, vp, ctypes.c_int, ctypes.c_int, vp, vp], ctypes.c_int),
         "kd_reverse_knn": ([vp, vp, ctypes.c_int, ctypes.c_int, vp, vp], ctypes.c_int),
+        "kd_autotune": ([vp, ctypes.c_int, ctypes.c_int, i64, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int)],
+                        ctypes.c_int),
+        "kd_tuning_get": ([vp, ctypes.c_int, ctypes.c_int, i64, P(ctypes.c_int), P(ctypes.c_int)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)

@@ -69,14 +69,16 @@ class Handle:
 
 
 def kd_create(device: int = 0, stream=None, mem_budget_bytes: int = 0, switch_threshold: int = 0,
-              debug: int = 0) -> Context:
+              debug: int = 0, level_tile: int = 0, tune_cache: str | None = None) -> Context:
     """kd_create.  ``stream``: a torch.cuda.Stream, an int handle, or None for
-    torch's current stream on ``device``."""
+    torch's current stream on ``device``.  ``switch_threshold`` / ``level_tile``:
+    0 for the tuned (or default) values; ``tune_cache``: the autotuner's file."""
     lib = _lib.load()
     if stream is None and torch is not None and torch.cuda.is_available():
         stream = torch.cuda.current_stream(device)
     sh = stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0)
-    cfg = KdConfig(device, ctypes.c_void_p(sh), mem_budget_bytes, 0, switch_threshold, debug)
+    cfg = KdConfig(device, ctypes.c_void_p(sh), mem_budget_bytes, level_tile, switch_threshold, debug,
+                   tune_cache.encode() if tune_cache else None)
     out = ctypes.c_void_p()
     rc = lib.kd_create(ctypes.byref(out), ctypes.byref(cfg))
     if rc != _lib.KD_OK:
@@ -420,6 +422,30 @@ def kd_region(ctx: Context, index: Index, lo, hi):
                                 ctypes.c_void_p(op), ctypes.c_void_p(ipt), total))
     del keep_lo, keep_hi
     return offs, idx[:total]
+
+
+_DT_CODES = {"int32": _lib.KD_I32, "int64": _lib.KD_I64, "float32": _lib.KD_F32}
+
+
+def _dtype_code(dtype) -> int:
+    if isinstance(dtype, int):
+        return dtype
+    return _DT_CODES[str(np.dtype(str(dtype).replace("torch.", "")))]
+
+
+def kd_autotune(ctx: Context, k: int, dtype, n: int, reps: int = 3) -> dict:
+    """kd_autotune: time every (on-chip subtree size, level tile) pair on a
+    synthetic cloud of n tuples; returns the chosen pair."""
+    sm, lt = ctypes.c_int(), ctypes.c_int()
+    ctx.check(_lib.load().kd_autotune(ctx.ptr, k, _dtype_code(dtype), n, reps, ctypes.byref(sm), ctypes.byref(lt)))
+    return {"switch_threshold": sm.value, "level_tile": lt.value}
+
+
+def kd_tuning_get(ctx: Context, k: int, dtype, n: int) -> dict:
+    """kd_tuning_get: the pair a build of clouds of at most n tuples uses."""
+    sm, lt = ctypes.c_int(), ctypes.c_int()
+    ctx.check(_lib.load().kd_tuning_get(ctx.ptr, k, _dtype_code(dtype), n, ctypes.byref(sm), ctypes.byref(lt)))
+    return {"switch_threshold": sm.value, "level_tile": lt.value}
 
 
 def kd_launch_count(ctx: Context) -> int:

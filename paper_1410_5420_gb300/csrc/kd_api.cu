@@ -49,8 +49,10 @@ cudaError_t launch_perm_scatter(const int64_t* m_ptr, int64_t max_m, const uint3
 cudaError_t launch_arrays_out(const int64_t* m_ptr, int64_t max_m, int k, const AllPlanes& rec,
                               const uint32_t* perm0, int32_t* out, cudaStream_t s);
 int level_tile(int k);
+cudaError_t launch_tune_cloud(int dtype, void* coords, int64_t count, uint64_t seed, cudaStream_t s);
+bool level_tile_supported(int k, int tile);
 int level_status_stride(int k);
-cudaError_t launch_level_pass(int k, const AllBufs& bufs, int q, const LevelJob* jobs, int njobs, int ntiles,
+cudaError_t launch_level_pass(int k, int tile, const AllBufs& bufs, int q, const LevelJob* jobs, int njobs, int ntiles,
                               const CloudDev* clouds, uint32_t* medr, const uint32_t* perm0, uint32_t* status,
                               int* err, cudaStream_t s);
 size_t level_status_words(int k, int ntiles);
@@ -103,6 +105,17 @@ struct kd_ctx {
     size_t in_use = 0;
     int debug = 0;
     int smax_override = 0;
+    int level_tile_override = 0;
+    // autotuner: the fastest (on-chip subtree size, level tile) measured per
+    // (k, dtype, size bucket), and the cache file it is kept in
+    struct Tuned {
+        int smax, ltile;
+        double ms;
+    };
+    std::map<uint32_t, Tuned> tuning;
+    std::string tune_cache;
+    int force_smax = 0, force_ltile = 0;  // the candidate kd_autotune is timing
+    int last_smax = 0, last_ltile = 0;    // what the last build used
     // Failure-detection tests (debug bit 8): the look-back polls are bounded
     // by a few thousand instead of 2^24, and the next presort's first sort
     // pass has its chunk 0 withhold its flag (once), so that the other
@@ -851,6 +864,61 @@ int nlevels(int64_t m) {
     return L;  // ceil(log2(m + 1))
 }
 
+// ---------------------------------------------------------- tuned parameters
+// Size bucket: floor(log2 n) of the largest cloud.
+uint32_t tune_key(int k, int dtype, int64_t n) {
+    int b = 0;
+    while (b < 62 && ((int64_t)2 << b) <= n) ++b;
+    return ((uint32_t)k << 16) | ((uint32_t)dtype << 8) | (uint32_t)b;
+}
+
+// The on-chip subtree size and the level-step tile a build of clouds of at
+// most nmax tuples uses: the candidate being timed by kd_autotune, else the
+// context's fixed settings, else the tuned entry for (k, dtype, bucket),
+// else the defaults (1024; 2048 for k <= 4, 1024 above).
+void choose_params(kd_ctx* ctx, int k, int dtype, int64_t nmax, int* smax_out, int* ltile_out) {
+    const auto it = ctx->tuning.find(tune_key(k, dtype, nmax));
+    const bool tuned = it != ctx->tuning.end();
+    int want = ctx->force_smax ? ctx->force_smax
+                               : (ctx->smax_override ? ctx->smax_override : (tuned ? it->second.smax : 1024));
+    int smax = 1024;
+    while (smax < want && smax < 4096) smax *= 2;
+    while (smax > 1024 && k > finish_kmax(smax)) smax /= 2;
+    int lt = ctx->force_ltile ? ctx->force_ltile
+                              : (ctx->level_tile_override ? ctx->level_tile_override
+                                                          : (tuned ? it->second.ltile : level_tile(std::max(k, 2))));
+    if (!level_tile_supported(std::max(k, 2), lt)) lt = level_tile(std::max(k, 2));
+    *smax_out = smax;
+    *ltile_out = lt;
+}
+
+// Tuning cache file: one line per entry, "k dtype bucket smax level_tile ms".
+void tuning_load(kd_ctx* ctx) {
+    if (ctx->tune_cache.empty()) return;
+    FILE* f = fopen(ctx->tune_cache.c_str(), "r");
+    if (!f) return;
+    int k, dt, b, sm, lt;
+    double ms;
+    while (fscanf(f, "%d %d %d %d %d %lf", &k, &dt, &b, &sm, &lt, &ms) == 6) {
+        if (k < 1 || k > KD_MAX_K || dt < 0 || dt > 2 || b < 0 || b > 62) continue;
+        if (sm != 1024 && sm != 2048 && sm != 4096) continue;
+        ctx->tuning[((uint32_t)k << 16) | ((uint32_t)dt << 8) | (uint32_t)b] = kd_ctx::Tuned{sm, lt, ms};
+    }
+    fclose(f);
+}
+
+bool tuning_save(kd_ctx* ctx) {
+    if (ctx->tune_cache.empty()) return true;
+    const std::string tmp = ctx->tune_cache + ".tmp";
+    FILE* f = fopen(tmp.c_str(), "w");
+    if (!f) return false;
+    for (const auto& e : ctx->tuning)
+        fprintf(f, "%u %u %u %d %d %.6f\n", e.first >> 16, (e.first >> 8) & 255u, e.first & 255u, e.second.smax,
+                e.second.ltile, e.second.ms);
+    const bool ok = fclose(f) == 0;
+    return ok && rename(tmp.c_str(), ctx->tune_cache.c_str()) == 0;
+}
+
 kd_status build_batch(kd_ctx* ctx, kd_presorted* H, kd_tree* outs) {
     const int k = H->k, count = H->count;
     const int64_t M = H->M;
@@ -865,17 +933,19 @@ kd_status build_batch(kd_ctx* ctx, kd_presorted* H, kd_tree* outs) {
     int* d_err = nullptr;
     CKS(S.get(&d_err, 4));
     CK(cudaMemsetAsync(d_err, 0, 4, s));
-    // subtree size finished on chip: a power of two in [1024, 4096] (the
-    // level-pass tiles of 2048 positions need segments of at least 683).
-    // 1024 by default: one more level step costs less than the finisher's
-    // extra block level at 2048 (k = 2..4, 2^22..2^26 tuples).
-    int smax = 1024;
-    if (ctx->smax_override) {
-        smax = 1024;
-        while (smax < ctx->smax_override && smax < 4096) smax *= 2;
+    // subtree size finished on chip (a power of two in [1024, 4096]) and
+    // level-step tile (1024 or 2048 positions; a tile may touch at most 4
+    // segments, so segments above the finisher need at least tile / 3):
+    // tuned per (k, dtype, size bucket), else 1024 and the larger tile
+    int smax = 1024, tile = level_tile(std::max(k, 2));
+    {
+        int64_t nmax = 0;
+        for (int i = 0; i < count; ++i) nmax = std::max(nmax, H->n_c[i]);
+        choose_params(ctx, k, H->dtype, nmax, &smax, &tile);
     }
-    while (smax > 1024 && k > finish_kmax(smax)) smax /= 2;
-    if (k >= 2 && smax * 3 < level_tile(k) + 3) return fail(ctx, KD_EINVAL, "switch threshold too small");
+    ctx->last_smax = smax;
+    ctx->last_ltile = tile;
+    if (k >= 2 && smax * 3 < tile + 3) return fail(ctx, KD_EINVAL, "switch threshold too small");
 
     // outputs: user device arrays, or staging for host arrays
     bool any_host = false, want_l = false, want_r = false, want_d = false;
@@ -940,7 +1010,6 @@ kd_status build_batch(kd_ctx* ctx, kd_presorted* H, kd_tree* outs) {
         moves[i].fill(0);
         level[i].fill(0);
     }
-    const int tile = level_tile(std::max(k, 2));
     bool need_bufs = false;
     if (k >= 2) {
         int tmax = 0;
@@ -1057,7 +1126,7 @@ kd_status build_batch(kd_ctx* ctx, kd_presorted* H, kd_tree* outs) {
         // array q moves k planes (array 0) or k - 1 (its own rank is not carried)
         LaunchTimer lt(ctx, F_LEVEL, step_elems[st], nullptr, 8.0 * (k - (step_q[st] != 0)) + 4.0 * F);
         ctx->launches += 3;  // tile records, count pass and scan
-        CK(launch_level_pass(k, bufs, step_q[st], d_jobs + job_off[st], (int)step_jobs[st].size(),
+        CK(launch_level_pass(k, tile, bufs, step_q[st], d_jobs + job_off[st], (int)step_jobs[st].size(),
                              (int)step_ntiles[st], d_cd, medr, H->perm0, d_status, d_err, s));
     }
     // A single cloud with page-locked host outputs: the finisher runs in chunks of
@@ -1265,6 +1334,11 @@ kd_status kd_create(kd_ctx** out, const kd_config* cfg) {
     ctx->budget = c.mem_budget_bytes;
     ctx->debug = c.debug;
     ctx->smax_override = c.switch_threshold;
+    if (c.level_tile != 0 && c.level_tile != 1024 && c.level_tile != 2048) return KD_EINVAL;
+    ctx->level_tile_override = c.level_tile;
+    if (c.tune_cache) ctx->tune_cache = c.tune_cache;
+    ctx->cfg.tune_cache = ctx->tune_cache.empty() ? nullptr : ctx->tune_cache.c_str();  // owned copy for workers
+    tuning_load(ctx.get());
     if (c.debug & 8) {
         ctx->spin_limit = 4096;
         ctx->inject_timeout = true;
@@ -1444,6 +1518,98 @@ kd_status kd_serving_stats(kd_ctx* ctx, int64_t* completed, double* p50_us, doub
     if (completed) *completed = ctx->completed;
     if (p50_us) *p50_us = pct(0.50);
     if (p99_us) *p99_us = pct(0.99);
+    return KD_OK;
+}
+
+kd_status kd_autotune(kd_ctx* ctx, int k, kd_dtype dtype, int64_t n, int reps, int* smax_out, int* ltile_out) {
+    if (!ctx) return KD_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    cudaSetDevice(ctx->device);
+    ctx->last_error.clear();
+    if (k < 1 || k > KD_MAX_K || n < 1 || n > KD_MAX_N || reps < 1 || reps > 100 ||
+        (dtype != KD_I32 && dtype != KD_I64 && dtype != KD_F32))
+        return fail(ctx, KD_EINVAL, "kd_autotune: k, n, dtype or reps out of range");
+    const uint32_t key = tune_key(k, dtype, n);
+    if (k >= 2) {
+        Scratch S(ctx);
+        void* coords = nullptr;
+        CKS(S.get(&coords, (size_t)n * k * dtype_size(dtype)));
+        {
+            LaunchTimer lt(ctx, F_OTHER, 0.0);
+            CK(launch_tune_cloud(dtype, coords, n * k, (uint64_t)key * 0x9E3779B97F4A7C15ull, ctx->stream));
+        }
+        kd_cloud cl{coords, n, k, dtype, 1};
+        kd_presorted* H = nullptr;
+        CKS(presort_batch(ctx, &cl, 1, &H));
+        struct Release {
+            kd_ctx* c;
+            kd_presorted* h;
+            ~Release() { release_handle(c, h); }
+        } rel{ctx, H};
+        int32_t *node = nullptr, *left = nullptr, *right = nullptr;
+        uint8_t* dim = nullptr;
+        CKS(S.get(&node, (size_t)n * 4));
+        CKS(S.get(&left, (size_t)n * 4));
+        CKS(S.get(&right, (size_t)n * 4));
+        CKS(S.get(&dim, (size_t)n));
+        cudaEvent_t e0 = take_event(ctx), e1 = take_event(ctx);
+        double best = 1e30;
+        int bsm = 1024, blt = level_tile(k);
+        for (int sm : {1024, 2048, 4096}) {
+            if (k > finish_kmax(sm)) continue;
+            for (int lt : {1024, 2048}) {
+                if (!level_tile_supported(k, lt) || sm * 3 < lt + 3) continue;
+                ctx->force_smax = sm;
+                ctx->force_ltile = lt;
+                std::vector<float> ms;
+                kd_status st = KD_OK;
+                for (int r = 0; r <= reps && st == KD_OK; ++r) {  // the first run is a warm-up
+                    kd_tree t{0, -1, node, left, right, dim, 1};
+                    cudaEventRecord(e0, ctx->stream);
+                    st = build_batch(ctx, H, &t);
+                    cudaEventRecord(e1, ctx->stream);
+                    if (st == KD_OK && r > 0) {
+                        cudaEventSynchronize(e1);
+                        float x = 0;
+                        cudaEventElapsedTime(&x, e0, e1);
+                        ms.push_back(x);
+                    }
+                }
+                ctx->force_smax = ctx->force_ltile = 0;
+                if (st != KD_OK) {
+                    ctx->event_pool.push_back(e0);
+                    ctx->event_pool.push_back(e1);
+                    return st;
+                }
+                std::sort(ms.begin(), ms.end());
+                const double med = ms[ms.size() / 2];
+                if (med < best) {
+                    best = med;
+                    bsm = sm;
+                    blt = lt;
+                }
+            }
+        }
+        ctx->event_pool.push_back(e0);
+        ctx->event_pool.push_back(e1);
+        ctx->tuning[key] = kd_ctx::Tuned{bsm, blt, best};
+        if (!tuning_save(ctx)) return fail(ctx, KD_EINVAL, "kd_autotune: cannot write " + ctx->tune_cache);
+    }
+    if (ctx->debug & 2) collect_timing(ctx);
+    int sm = 0, lt = 0;
+    choose_params(ctx, k, dtype, n, &sm, &lt);
+    if (smax_out) *smax_out = sm;
+    if (ltile_out) *ltile_out = lt;
+    return KD_OK;
+}
+
+kd_status kd_tuning_get(kd_ctx* ctx, int k, kd_dtype dtype, int64_t n, int* smax_out, int* ltile_out) {
+    if (!ctx || k < 1 || k > KD_MAX_K || n < 0) return KD_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    int sm = 0, lt = 0;
+    choose_params(ctx, k, dtype, n, &sm, &lt);
+    if (smax_out) *smax_out = sm;
+    if (ltile_out) *ltile_out = lt;
     return KD_OK;
 }
 

@@ -89,8 +89,12 @@ constexpr int LEVEL_STAGES = 2;
 constexpr int PLANE_SLACK = 8;  // staged slice = tile rounded out to 16-byte boundaries
 constexpr int LEVEL_BLOCK = LEVEL_THREADS + 32;  // eight consumer warps + one producer warp
 
+// Elements per thread of a level-step tile: 8 (tiles of 2048 positions) or 4
+// (1024), chosen per step by the host; k > 4 uses 4 (its planes fill the
+// registers).  The default is the larger tile where it exists.
 __host__ __device__ constexpr int level_ipt_of(int K) { return K <= 4 ? 8 : 4; }
 __host__ __device__ constexpr int level_tile_of(int K) { return LEVEL_THREADS * level_ipt_of(K); }
+__host__ __device__ constexpr bool level_ipt_ok(int K, int IPT) { return IPT == 4 || (IPT == 8 && K <= 4); }
 __host__ __device__ constexpr int level_nbp(int K) { return (1 << (K - 1)) < 4 ? 4 : (1 << (K - 1)); }
 __host__ __device__ constexpr int trec_words(int K) { return TR_HEAD + LEVEL_NSMAX * (1 << (K - 1)); }
 
@@ -102,7 +106,7 @@ struct StageMeta {
     int64_t goff;
 };
 
-template <int K>
+template <int K, int IPT>
 __global__ void __launch_bounds__(256) k_level_tiles(const LevelJob* __restrict__ jobs, int njobs, int ntiles,
                                                      const CloudDev* __restrict__ clouds,
                                                      const uint32_t* __restrict__ medr, uint32_t* __restrict__ trec,
@@ -110,7 +114,7 @@ __global__ void __launch_bounds__(256) k_level_tiles(const LevelJob* __restrict_
                                                      int nflags, int* __restrict__ err) {
     constexpr int NBMAX = 1 << (K - 1);
     constexpr int TW = trec_words(K);
-    constexpr int TILE = level_tile_of(K);
+    constexpr int TILE = LEVEL_THREADS * IPT;
     pdl_wait();  // the previous step's counters and medians
     pdl_trigger();
     if (blockIdx.x == 0) {
@@ -169,14 +173,14 @@ __global__ void __launch_bounds__(256) k_level_tiles(const LevelJob* __restrict_
 // facts in the stage's meta entry and starts the bulk copies of the tile
 // record, `nplanes` plane slices and (move pass) the scanned counts of the
 // previous tile.  Ends by publishing t = -1.
-template <int K, bool MOVE>
+template <int K, int IPT, bool MOVE>
 __device__ __forceinline__ void level_producer(const AllBufs& bufs, int q, const LevelJob* __restrict__ jobs,
                                                int njobs, int ntiles, const CloudDev* __restrict__ clouds,
                                                const uint32_t* __restrict__ trec, const uint32_t* __restrict__ incl,
                                                uint32_t* ctr, uint32_t* smem, StageMeta* meta, uint64_t* full,
                                                uint64_t* empty, int* err) {
     constexpr int TW = trec_words(K);
-    constexpr int TILE = level_tile_of(K);
+    constexpr int TILE = LEVEL_THREADS * IPT;
     constexpr int PST = TILE + PLANE_SLACK;
     constexpr int NP = MOVE ? K : K - 1;
     constexpr int NBP = level_nbp(K);
@@ -232,10 +236,10 @@ __device__ __forceinline__ void level_producer(const AllBufs& bufs, int q, const
     }
 }
 
-template <int K>
+template <int K, int IPT>
 constexpr size_t level_smem_bytes(bool move) {
     return (size_t)LEVEL_STAGES *
-           (trec_words(K) + level_nbp(K) + (move ? K : K - 1) * (level_tile_of(K) + PLANE_SLACK)) * 4;
+           (trec_words(K) + level_nbp(K) + (move ? K : K - 1) * (LEVEL_THREADS * IPT + PLANE_SLACK)) * 4;
 }
 
 // Segment slot of cloud-local position pos among the tile's ns segments
@@ -308,14 +312,13 @@ __device__ __forceinline__ uint32_t route_rec(const uint32_t (&r)[K], int F, int
 // Count pass: per tile, the bucket counts of its last segment (cnt[t][b],
 // row stride level_nbp(K)) and whether that segment starts inside the tile
 // (head[t]).  Reads the F decision planes only.
-template <int K>
+template <int K, int IPT>
 __global__ void __launch_bounds__(LEVEL_BLOCK)
     k_level_count(const __grid_constant__ AllBufs bufs, int q, const LevelJob* __restrict__ jobs, int njobs,
                   int ntiles, const CloudDev* __restrict__ clouds, const uint32_t* __restrict__ trec,
                   uint32_t* __restrict__ cnt, uint32_t* __restrict__ head, uint32_t* __restrict__ ctr,
                   int* __restrict__ err) {
-    constexpr int IPT = level_ipt_of(K);
-    constexpr int TILE = level_tile_of(K);
+    constexpr int TILE = LEVEL_THREADS * IPT;
     constexpr int PST = TILE + PLANE_SLACK;
     constexpr int NBMAX = 1 << (K - 1);
     constexpr int NDMAX = LEVEL_NSMAX * NBMAX;
@@ -340,7 +343,7 @@ __global__ void __launch_bounds__(LEVEL_BLOCK)
     pdl_trigger();
     if (warp == LEVEL_WARPS) {
         if (lane == 0)
-            level_producer<K, false>(bufs, q, jobs, njobs, ntiles, clouds, trec, nullptr, ctr, lsm, meta, full, empty,
+            level_producer<K, IPT, false>(bufs, q, jobs, njobs, ntiles, clouds, trec, nullptr, ctr, lsm, meta, full, empty,
                                      err);
         return;
     }
@@ -556,14 +559,13 @@ __device__ __forceinline__ uint32_t plane_value(const uint32_t (&v)[K][IPT], int
 // ranking), with all K planes.  The element landing on the middle of a
 // final segment of level lev_out (its primary level) is that segment's
 // median: its rank in super key q goes to medr and its tuple to the node.
-template <int K>
+template <int K, int IPT>
 __global__ void __launch_bounds__(LEVEL_BLOCK, K <= 3 ? 3 : 2)
     k_level_pass(const __grid_constant__ AllBufs bufs, int q, const LevelJob* __restrict__ jobs, int njobs,
                  int ntiles, const CloudDev* __restrict__ clouds, uint32_t* __restrict__ medr,
                  const uint32_t* __restrict__ perm0, const uint32_t* __restrict__ trec,
                  const uint32_t* __restrict__ incl, uint32_t* __restrict__ ctr, int* __restrict__ err) {
-    constexpr int IPT = level_ipt_of(K);
-    constexpr int TILE = level_tile_of(K);
+    constexpr int TILE = LEVEL_THREADS * IPT;
     constexpr int PST = TILE + PLANE_SLACK;
     constexpr int NBMAX = 1 << (K - 1);
     constexpr int NDMAX = LEVEL_NSMAX * NBMAX;
@@ -591,7 +593,7 @@ __global__ void __launch_bounds__(LEVEL_BLOCK, K <= 3 ? 3 : 2)
     pdl_trigger();
     if (warp == LEVEL_WARPS) {
         if (lane == 0)
-            level_producer<K, true>(bufs, q, jobs, njobs, ntiles, clouds, trec, incl, ctr, lsm, meta, full, empty, err);
+            level_producer<K, IPT, true>(bufs, q, jobs, njobs, ntiles, clouds, trec, incl, ctr, lsm, meta, full, empty, err);
         return;
     }
     const int wbase = warp * 32 * IPT;
@@ -1175,10 +1177,14 @@ __global__ void k_top_nodes(const CloudDev* __restrict__ clouds, const int64_t* 
 
 // ------------------------------------------------------------ launchers
 int level_tile(int k) { return level_tile_of(k); }
+bool level_tile_supported(int k, int tile) {
+    return tile == LEVEL_THREADS * 4 || (tile == LEVEL_THREADS * 8 && level_ipt_ok(k, 8));
+}
 
 // Resident blocks per SM of the persistent level kernels ([0] count,
-// [1] move; by K) and the SM count, set by init_build_kernels.
-static int g_level_occ[2][MAXK + 1];
+// [1] move; by K and tile variant: [0] 4, [1] 8 elements per thread) and
+// the SM count, set by init_build_kernels.
+static int g_level_occ[2][MAXK + 1][2];
 static int g_num_sms = 0;
 
 // Status area of one level step (u32 words, every region 16-byte aligned):
@@ -1208,62 +1214,73 @@ size_t level_status_words(int k, int ntiles) {
     return t4 * (2 * (size_t)level_nbp(k) + 1 + (size_t)trec_words(k)) + level_lb_words(k, ntiles) + 4;
 }
 
-cudaError_t launch_level_pass(int k, const AllBufs& bufs, int q, const LevelJob* jobs, int njobs, int ntiles,
-                              const CloudDev* clouds, uint32_t* medr, const uint32_t* perm0, uint32_t* status,
+template <int K, int IPT>
+static cudaError_t level_step(const AllBufs& bufs, int q, const LevelJob* jobs, int njobs, int ntiles,
+                              const CloudDev* clouds, uint32_t* medr, const uint32_t* perm0, const LevelStatus& L,
                               int* err, cudaStream_t s) {
-    if (ntiles == 0) return cudaSuccess;
-    if (k < 2 || k > MAXK || g_num_sms == 0) return cudaErrorInvalidValue;
-    const LevelStatus L = level_status_layout(k, ntiles, status);
-    const int nbmax = 1 << (k - 1);
+    const int v = IPT == 8 ? 1 : 0;
+    const int nbmax = 1 << (K - 1);
     const int nch = level_scan_chunks(ntiles);
     const int nflags = nbmax * nch;  // look-back flags of the scan, [bucket][chunk]
-    const int gc = std::min(ntiles, g_num_sms * g_level_occ[0][k]);
-    const int gm = std::min(ntiles, g_num_sms * g_level_occ[1][k]);
+    const int gc = std::min(ntiles, g_num_sms * g_level_occ[0][K][v]);
+    const int gm = std::min(ntiles, g_num_sms * g_level_occ[1][K][v]);
+    cudaError_t e = launch_dependent(k_level_tiles<K, IPT>, dim3((ntiles + 7) / 8), dim3(256), 0, s, jobs, njobs,
+                                     ntiles, clouds, (const uint32_t*)medr, L.trec, L.ctrs, L.lb, nflags, err);
+    if (e == cudaSuccess)
+        e = launch_dependent(k_level_count<K, IPT>, dim3(gc), dim3(LEVEL_BLOCK), level_smem_bytes<K, IPT>(false), s,
+                             bufs, q, jobs, njobs, ntiles, clouds, (const uint32_t*)L.trec, L.cnt, L.head, L.ctrs, err);
+    if (e == cudaSuccess)
+        e = launch_dependent(k_level_scan, dim3(nbmax * nch), dim3(1024), 0, s, ntiles, nbmax, level_nbp(K),
+                             (const uint32_t*)L.cnt, (const uint32_t*)L.head, L.incl, L.lb, L.ctrs + 2, err);
+    if (e == cudaSuccess)
+        e = launch_dependent(k_level_pass<K, IPT>, dim3(gm), dim3(LEVEL_BLOCK), level_smem_bytes<K, IPT>(true), s, bufs,
+                             q, jobs, njobs, ntiles, clouds, medr, perm0, (const uint32_t*)L.trec,
+                             (const uint32_t*)L.incl, L.ctrs + 1, err);
+    return e;
+}
+
+// One level step of array q over the jobs' tiles of `tile` positions
+// (1024, or 2048 for k <= 4).
+cudaError_t launch_level_pass(int k, int tile, const AllBufs& bufs, int q, const LevelJob* jobs, int njobs,
+                              int ntiles, const CloudDev* clouds, uint32_t* medr, const uint32_t* perm0,
+                              uint32_t* status, int* err, cudaStream_t s) {
+    if (ntiles == 0) return cudaSuccess;
+    if (k < 2 || k > MAXK || g_num_sms == 0 || !level_tile_supported(k, tile)) return cudaErrorInvalidValue;
+    const LevelStatus L = level_status_layout(k, ntiles, status);
+    const bool big = tile == LEVEL_THREADS * 8;
     cudaError_t e = cudaSuccess;
-#define KD_LEVEL_CASE(KK)                                                                                      \
-    case KK:                                                                                                 \
-        e = launch_dependent(k_level_tiles<KK>, dim3((ntiles + 7) / 8), dim3(256), 0, s, jobs, njobs, ntiles,    \
-                             clouds, (const uint32_t*)medr, L.trec, L.ctrs, L.lb, nflags, err);              \
-        if (e == cudaSuccess)                                                                                \
-            e = launch_dependent(k_level_count<KK>, dim3(gc), dim3(LEVEL_BLOCK), level_smem_bytes<KK>(false), s, bufs, \
-                             q, jobs, njobs, ntiles, clouds, (const uint32_t*)L.trec, L.cnt, L.head, L.ctrs, err);  \
-        if (e == cudaSuccess)                                                                                \
-            e = launch_dependent(k_level_scan, dim3(nbmax * nch), dim3(1024), 0, s, ntiles, nbmax,            \
-                                 level_nbp(KK), (const uint32_t*)L.cnt, (const uint32_t*)L.head, L.incl, L.lb, \
-                                 L.ctrs + 2, err);                                                           \
-        if (e == cudaSuccess)                                                                                \
-            e = launch_dependent(k_level_pass<KK>, dim3(gm), dim3(LEVEL_BLOCK), level_smem_bytes<KK>(true), s, \
-                                 bufs, q, jobs, njobs, ntiles, clouds, medr, perm0, (const uint32_t*)L.trec,   \
-                                 (const uint32_t*)L.incl, L.ctrs + 1, err);                                  \
-        if (e != cudaSuccess) return e;                                                                      \
-        break;
     switch (k) {
-        KD_LEVEL_CASE(2)
-        KD_LEVEL_CASE(3)
-        KD_LEVEL_CASE(4)
-        KD_LEVEL_CASE(5)
-        KD_LEVEL_CASE(6)
-        KD_LEVEL_CASE(7)
-        KD_LEVEL_CASE(8)
-        default:
-            return cudaErrorInvalidValue;
+        case 2: e = big ? level_step<2, 8>(bufs, q, jobs, njobs, ntiles, clouds, medr, perm0, L, err, s)
+                        : level_step<2, 4>(bufs, q, jobs, njobs, ntiles, clouds, medr, perm0, L, err, s); break;
+        case 3: e = big ? level_step<3, 8>(bufs, q, jobs, njobs, ntiles, clouds, medr, perm0, L, err, s)
+                        : level_step<3, 4>(bufs, q, jobs, njobs, ntiles, clouds, medr, perm0, L, err, s); break;
+        case 4: e = big ? level_step<4, 8>(bufs, q, jobs, njobs, ntiles, clouds, medr, perm0, L, err, s)
+                        : level_step<4, 4>(bufs, q, jobs, njobs, ntiles, clouds, medr, perm0, L, err, s); break;
+        case 5: e = level_step<5, 4>(bufs, q, jobs, njobs, ntiles, clouds, medr, perm0, L, err, s); break;
+        case 6: e = level_step<6, 4>(bufs, q, jobs, njobs, ntiles, clouds, medr, perm0, L, err, s); break;
+        case 7: e = level_step<7, 4>(bufs, q, jobs, njobs, ntiles, clouds, medr, perm0, L, err, s); break;
+        case 8: e = level_step<8, 4>(bufs, q, jobs, njobs, ntiles, clouds, medr, perm0, L, err, s); break;
+        default: return cudaErrorInvalidValue;
     }
-#undef KD_LEVEL_CASE
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
-template <int K>
+template <int K, int IPT>
 static cudaError_t init_level_kernels() {
-    const size_t sc = level_smem_bytes<K>(false), sm = level_smem_bytes<K>(true);
-    cudaError_t e = cudaFuncSetAttribute((const void*)k_level_count<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sc);
+    const int v = IPT == 8 ? 1 : 0;
+    const size_t sc = level_smem_bytes<K, IPT>(false), sm = level_smem_bytes<K, IPT>(true);
+    cudaError_t e = cudaFuncSetAttribute((const void*)k_level_count<K, IPT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute((const void*)k_level_pass<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        e = cudaFuncSetAttribute((const void*)k_level_pass<K, IPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sm);
     int oc = 0, om = 0;
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oc, k_level_count<K>, LEVEL_BLOCK, sc);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&om, k_level_pass<K>, LEVEL_BLOCK, sm);
-    g_level_occ[0][K] = oc > 0 ? oc : 1;
-    g_level_occ[1][K] = om > 0 ? om : 1;
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oc, k_level_count<K, IPT>, LEVEL_BLOCK, sc);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&om, k_level_pass<K, IPT>, LEVEL_BLOCK, sm);
+    g_level_occ[0][K][v] = oc > 0 ? oc : 1;
+    g_level_occ[1][K][v] = om > 0 ? om : 1;
     return e;
 }
 
@@ -1277,13 +1294,16 @@ cudaError_t init_build_kernels() {
     int dev = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = init_level_kernels<2>();
-    if (e == cudaSuccess) e = init_level_kernels<3>();
-    if (e == cudaSuccess) e = init_level_kernels<4>();
-    if (e == cudaSuccess) e = init_level_kernels<5>();
-    if (e == cudaSuccess) e = init_level_kernels<6>();
-    if (e == cudaSuccess) e = init_level_kernels<7>();
-    if (e == cudaSuccess) e = init_level_kernels<8>();
+    if (e == cudaSuccess) e = init_level_kernels<2, 8>();
+    if (e == cudaSuccess) e = init_level_kernels<2, 4>();
+    if (e == cudaSuccess) e = init_level_kernels<3, 8>();
+    if (e == cudaSuccess) e = init_level_kernels<3, 4>();
+    if (e == cudaSuccess) e = init_level_kernels<4, 8>();
+    if (e == cudaSuccess) e = init_level_kernels<4, 4>();
+    if (e == cudaSuccess) e = init_level_kernels<5, 4>();
+    if (e == cudaSuccess) e = init_level_kernels<6, 4>();
+    if (e == cudaSuccess) e = init_level_kernels<7, 4>();
+    if (e == cudaSuccess) e = init_level_kernels<8, 4>();
     auto set = [&](const void* f, size_t bytes) {
         if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     };

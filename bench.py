@@ -270,6 +270,8 @@ def batched_result(args, dev_index=0):
     dev = [torch.from_numpy(c).cuda(dev_index) for c in clouds]
     stream = torch.cuda.current_stream(dev_index)
     ctx = api.kd_create(dev_index, stream=stream)
+    # the autotuner picks the subtree size and level tile for the bucket of the largest cloud
+    tuned = api.kd_autotune(ctx, 3, "float32", max(c.shape[0] for c in clouds), reps=3)
 
     def timed(fn, reps):
         for _ in range(max(1, min(args.warmup, 2))):
@@ -317,7 +319,7 @@ def batched_result(args, dev_index=0):
             "plain_per_cloud_pipelined": {"ms": ms_p, "points_per_s": pts / (ms_p / 1000.0),
                                           "host_threads": nthreads},
             "speedup_vs_serial": ms_s / ms_b, "speedup_vs_pipelined": ms_p / ms_b,
-            "trees_identical": bool(same)}
+            "trees_identical": bool(same), "tuned": tuned}
 
 
 def run_batched(args):
@@ -558,6 +560,7 @@ def main():
     x = pinned.cuda(dev)
     stream = torch.cuda.current_stream(dev)
     ctx = api.kd_create(dev, stream=stream)
+    tuned = api.kd_autotune(ctx, K, "float32", n, reps=2)
 
     def barrier():
         if world > 1:
@@ -594,7 +597,8 @@ def main():
     value = whole_job_value(world, n, ms_per_step / 1000.0)
 
     # the same steps again with CUDA events around every launch (per-kernel times)
-    ctx_t = api.kd_create(dev, stream=stream, debug=2)
+    ctx_t = api.kd_create(dev, stream=stream, debug=2, switch_threshold=tuned["switch_threshold"],
+                          level_tile=tuned["level_tile"])
     step(ctx_t)
     api.kd_kernel_stats_reset(ctx_t)
     ms_step_events = timed_steps(ctx_t, args.steps)
@@ -606,7 +610,8 @@ def main():
     out_l = torch.empty(n, dtype=torch.int32).pin_memory()
     out_r = torch.empty(n, dtype=torch.int32).pin_memory()
     out_d = torch.empty(n, dtype=torch.uint8).pin_memory()
-    ctx_h = api.kd_create(dev, stream=stream)
+    ctx_h = api.kd_create(dev, stream=stream, switch_threshold=tuned["switch_threshold"],
+                          level_tile=tuned["level_tile"])
     import ctypes
     from paper_1410_5420_gb300 import _lib
     lib = _lib.load()
@@ -671,6 +676,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": n, "k": K, "m": m, "seed": SEED, "parallelism": f"replicas{world}",
+                   "tuned": tuned,
                    "l2": "inputs (768 MiB coordinates, GBs of index arrays) exceed the 126 MB L2; no flush"},
         "roofline": roof,
         "step_model": {"bytes_per_point": model["per_point"], "bytes": model_bytes,

@@ -68,7 +68,8 @@ def test_every_candidate_builds_the_same_tree(cuda_lib, k, dtype):
                 same(cuda_lib.build_tree(ctx, x), ref)
             finally:
                 ctx.close()
-    assert len(seen) >= 2  # k limits the choices, but there always are some
+    # subtrees of 4096 serve k <= 3, of 2048 k <= 4; tiles of 2048 serve k <= 4
+    assert len(seen) == {2: 6, 3: 6, 4: 4, 5: 1}[k]
 
 
 def test_batched_build_uses_the_tuned_pair(cuda_lib, tmp_path):

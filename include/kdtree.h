@@ -129,6 +129,18 @@ kd_status kd_handle_arrays(kd_ctx *ctx, kd_handle h, int32_t *out, int on_device
  */
 kd_status kd_build(kd_ctx *ctx, kd_handle h, kd_tree *out);
 
+/*
+ * The O(n log n) build of the paper's "Comparative Performance" section
+ * ("The O(n log n) Algorithm"): one index array sorted by super key 0 and
+ * deduplicated, then at every level the median of each sub-array in the
+ * level's super key is found by selection (a most-significant-byte radix
+ * selection, linear per level) and the sub-array is partitioned around it.
+ * No other super-key order is presorted.  The tree equals kd_presort +
+ * kd_build's for the same cloud (every median is unique).  cloud and out as
+ * for kd_presort / kd_build; errors as theirs.
+ */
+kd_status kd_build_select(kd_ctx *ctx, const kd_cloud *cloud, kd_tree *out);
+
 /* Release a handle that will not be built. */
 kd_status kd_release(kd_ctx *ctx, kd_handle h);
 
@@ -296,7 +308,8 @@ int64_t kd_launch_count(kd_ctx *ctx);
  * Kernel timing (instrumentation; active when cfg->debug & 2): CUDA events
  * recorded on the context's stream around every launch, summed per kernel
  * family (0 transform, 1 sort pass, 2 dedup, 3 records, 4 level pass,
- * 5 finisher, 6 top nodes, 7 other, 8 key gathers between sorts).  *ms: device time, *launches: launch
+ * 5 finisher, 6 top nodes, 7 other, 8 key gathers, 9 median selection and
+ * partition of kd_build_select, 10 its finisher).  *ms: device time, *launches: launch
  * count, *units: elements the launches processed, *bytes: the algorithmic
  * bytes those launches must move (reads + writes per element of each kernel,
  * summed over launches).  Any output pointer may be NULL.  Synchronises the

@@ -21,13 +21,14 @@ STATUS_NAMES = {0: "KD_OK", -1: "KD_EINVAL", -2: "KD_ENOMEM", -3: "KD_EDEVICE", 
                 -5: "KD_EBUSY", -6: "KD_ENAN"}
 
 # kernel families reported by kd_kernel_stats
-FAMILIES = ["transform", "sort_pass", "dedup", "records", "level_pass", "finish", "top_nodes", "other", "gather"]
+FAMILIES = ["transform", "sort_pass", "dedup", "records", "level_pass", "finish", "top_nodes", "other", "gather",
+            "select", "select_finish"]
 
 EXPORTS = ["kd_create", "kd_presort", "kd_handle_info", "kd_handle_arrays", "kd_build", "kd_release",
            "kd_build_batch", "kd_submit", "kd_wait", "kd_serving_stats", "kd_destroy", "kd_last_error",
            "kd_launch_count", "kd_kernel_stats", "kd_kernel_stats_reset", "kd_trace_counters",
            "kd_presort_noalloc", "kd_index_create", "kd_index_destroy", "kd_knn", "kd_region",
-           "kd_knn_all", "kd_reverse_knn", "kd_autotune", "kd_tuning_get"]
+           "kd_knn_all", "kd_reverse_knn", "kd_autotune", "kd_tuning_get", "kd_build_select"]
 
 
 class KdConfig(ctypes.Structure):
@@ -89,6 +90,7 @@ def load():
         "kd_autotune": ([vp, ctypes.c_int, ctypes.c_int, i64, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int)],
                         ctypes.c_int),
         "kd_tuning_get": ([vp, ctypes.c_int, ctypes.c_int, i64, P(ctypes.c_int), P(ctypes.c_int)], ctypes.c_int),
+        "kd_build_select": ([vp, P(KdCloud), P(KdTree)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)

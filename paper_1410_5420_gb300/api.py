@@ -166,6 +166,17 @@ def build_tree(ctx: Context, coords, children: bool = True, on_device: bool | No
     return kd_build(ctx, kd_presort(ctx, coords), children=children, on_device=on_device)
 
 
+def kd_build_select(ctx: Context, coords, children: bool = True, on_device: bool | None = None) -> dict:
+    """kd_build_select: the O(n log n) build with per-level median selection
+    (one presorted index array); the same tree as build_tree."""
+    c, keep = _cloud(coords)
+    dev = bool(c.on_device) if on_device is None else on_device
+    tree, arrays = _alloc_tree(c.n, dev, ctx.device, children)
+    ctx.check(_lib.load().kd_build_select(ctx.ptr, ctypes.byref(c), ctypes.byref(tree)))
+    del keep
+    return _result(tree, arrays)
+
+
 def _np_struct(ctype) -> np.dtype:
     """numpy dtype with the layout of a ctypes Structure of scalar fields."""
     names, formats, offsets = [], [], []

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libkdtree.so")
-SOURCES = ["kd_presort.cu", "kd_build.cu", "kd_api.cu", "kd_noalloc.cu", "kd_search.cu", "kd_tune.cu"]
+SOURCES = ["kd_presort.cu", "kd_build.cu", "kd_api.cu", "kd_noalloc.cu", "kd_search.cu", "kd_tune.cu", "kd_select.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -50,6 +50,15 @@ cudaError_t launch_arrays_out(const int64_t* m_ptr, int64_t max_m, int k, const 
                               const uint32_t* perm0, int32_t* out, cudaStream_t s);
 int level_tile(int k);
 cudaError_t launch_tune_cloud(int dtype, void* coords, int64_t count, uint64_t seed, cudaStream_t s);
+size_t sel_seg_bytes(int key64);
+int sel_finish_tile(int key64, int k);
+cudaError_t init_select_kernels();
+cudaError_t launch_sel_level(int key64, void* const* id, void* const* key, int cur, int k, int32_t m, int L,
+                             int tile, void* segs, uint32_t* ghist, int32_t* gany, uint32_t* unresolved, int32_t* node,
+                             int64_t in_off, int* err, cudaStream_t s, int round_begin, int round_end, int phase);
+cudaError_t launch_sel_finish(int key64, void* const* id, void* const* key, int cur, int k, int32_t m, int lam, int T,
+                              int32_t* node, int32_t* left, int32_t* right, uint8_t* dim, int64_t in_off, int* err,
+                              cudaStream_t s);
 bool level_tile_supported(int k, int tile);
 int level_status_stride(int k);
 cudaError_t launch_level_pass(int k, int tile, const AllBufs& bufs, int q, const LevelJob* jobs, int njobs, int ntiles,
@@ -71,7 +80,12 @@ using namespace kd;
 
 namespace {
 
-enum Family { F_TRANSFORM = 0, F_SORT, F_DEDUP, F_RECORDS, F_LEVEL, F_FINISH, F_TOP, F_OTHER, F_GATHER, F_COUNT };
+enum Family {
+    F_TRANSFORM = 0, F_SORT, F_DEDUP, F_RECORDS, F_LEVEL, F_FINISH, F_TOP, F_OTHER, F_GATHER,
+    F_SELECT,         // median-selection build: selection rounds and partitions of the levels
+    F_SELECT_FINISH,  // median-selection build: on-chip finisher
+    F_COUNT
+};
 
 struct TimedLaunch {
     int family;
@@ -92,6 +106,7 @@ struct kd_presorted {
     uint32_t* perm0 = nullptr;
     AllPlanes rec{};
     void* rec_block = nullptr;
+    void* sel_keys = nullptr;  // median-selection build: k key planes in array-0 order
     int64_t* d_m = nullptr;
     size_t bytes = 0;
 };
@@ -365,7 +380,11 @@ double pass_bytes(const Pass& P, bool writes_key, int npay) {
     return (double)P.w * (writes_key ? 2 : 1) + 8.0 * npay + (P.mode == KEY_GATHER ? 4.0 : 0.0);
 }
 
-kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_presorted** out) {
+// all_arrays = false (median-selection build, single cloud): only array 0
+// and its duplicate removal; the handle then holds the k key planes
+// gathered into array-0 order instead of the other arrays and the rank
+// records.
+kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_presorted** out, bool all_arrays = true) {
     *out = nullptr;
     if (count < 1 || !clouds) return fail(ctx, KD_EINVAL, "no clouds");
     for (int i = 0; i < count; ++i) CKS(validate_cloud(ctx, &clouds[i]));
@@ -410,7 +429,8 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
     }
     CKS(dev_alloc(ctx, &p, (size_t)pad4(N) * 4 + 16));
     H->perm0 = (uint32_t*)p;
-    const size_t rec_planes = k >= 2 ? (size_t)k * k : 0;
+    if (!all_arrays && count != 1) return fail(ctx, KD_EINVAL, "internal: array-0-only presort of a batch");
+    const size_t rec_planes = (k >= 2 && all_arrays) ? (size_t)k * k : 0;
     if (rec_planes) {
         kd_status st = dev_alloc(ctx, &H->rec_block, (rec_planes * pad4(N) + 4) * 4);
         if (st != KD_OK) {
@@ -430,6 +450,7 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
             if (armed && h) {
                 dev_free(c, h->perm0);
                 dev_free(c, h->rec_block);
+                dev_free(c, h->sel_keys);
                 dev_free(c, h->d_m);
             }
         }
@@ -647,7 +668,7 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
     // key buffer the chain's first sort reads) and, for 32-bit keys and
     // k >= 3, x_{k-2} (carried through that sort for the next one), both in
     // array-0 order, so neither needs a gather
-    const bool y_first = count == 1 && k >= 2;
+    const bool y_first = count == 1 && k >= 2 && all_arrays;
     const bool y_second = y_first && k >= 3 && !key64;
     unsigned char *y1tmp = nullptr, *y2tmp = nullptr, *y2c = nullptr;
     if (y_first) CKS(S.get(&y1tmp, (size_t)NS * w + 16));
@@ -689,9 +710,19 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
         kc ^= 1;
         ic ^= 1;
     }
+    // median-selection build: the key planes in array-0 order ----------------
+    if (!all_arrays) {
+        kd_status st = dev_alloc(ctx, &H->sel_keys, (size_t)k * NS * w + 16);
+        if (st != KD_OK) return st;
+        for (int d = 0; d < k; ++d) {
+            LaunchTimer lg(ctx, F_GATHER, 0.0, H->d_m, 4.0 + 2.0 * w);
+            CK(launch_gather(key64, H->d_m, N, plane_ptr(d), H->perm0,
+                             (unsigned char*)H->sel_keys + (size_t)d * NS * w, d_err, s));
+        }
+    }
     // chain: array d = stable sort of array d+1 by x_d (then cloud) --------
     // payload plane list: [id (while a later gather needs it)], R_0, R_{k-1}, ..., R_{d+1}
-    if (k >= 2) {
+    if (k >= 2 && all_arrays) {
         const uint32_t* id_src = H->perm0;  // array 0 order
         // the first sort's keys come from duplicate removal; the second's are
         // carried through the first sort (see above)
@@ -849,6 +880,7 @@ void release_handle(kd_ctx* ctx, kd_presorted* h) {
     if (!h) return;
     dev_free(ctx, h->perm0);
     dev_free(ctx, h->rec_block);
+    dev_free(ctx, h->sel_keys);
     dev_free(ctx, h->d_m);
     delete h;
 }
@@ -1209,6 +1241,122 @@ kd_status build_batch(kd_ctx* ctx, kd_presorted* H, kd_tree* outs) {
     return KD_OK;
 }
 
+// ------------------------------------------------- median-selection build
+// The O(n log n) build of the paper's "Comparative Performance" section:
+// one index array (array 0, presorted by super key 0 and deduplicated) with
+// its key planes; every level selects each segment's median in the level's
+// super key (kd_select.cu) and partitions the segment around it.
+kd_status select_build(kd_ctx* ctx, kd_presorted* H, kd_tree* out) {
+    const int k = H->k;
+    const int64_t M = H->M;
+    cudaStream_t s = ctx->stream;
+    if (!out->node_tuple && M > 0) return fail(ctx, KD_EINVAL, "node_tuple output is NULL");
+    out->m = (int32_t)M;
+    out->root = M > 0 ? (int32_t)((M - 1) / 2) : -1;
+    if (M == 0) return KD_OK;
+    if (k == 1) return build_batch(ctx, H, out);  // one dimension: the sorted array is the tree
+    const int key64 = H->dtype == KD_I64;
+    const int w = key64 ? 8 : 4;
+    const int64_t NS = pad4(H->N);
+    Scratch S(ctx);
+    int* d_err = nullptr;
+    CKS(S.get(&d_err, 4));
+    CK(cudaMemsetAsync(d_err, 0, 4, s));
+    // outputs: the caller's device arrays or staging for host arrays
+    int32_t *node = out->node_tuple, *left = out->left, *right = out->right;
+    uint8_t* dim = out->dim;
+    if (!out->on_device) {
+        CKS(S.get(&node, (size_t)M * 4));
+        if (out->left) CKS(S.get(&left, (size_t)M * 4));
+        if (out->right) CKS(S.get(&right, (size_t)M * 4));
+        if (out->dim) CKS(S.get(&dim, (size_t)M));
+    }
+    // planes: buffer 0 is the handle's (array 0 and its key planes), buffer 1 new
+    void* ids[2];
+    void* keys[2 * MAXK] = {};
+    ids[0] = H->perm0;
+    CKS(S.get(&ids[1], (size_t)NS * 4 + 16));
+    unsigned char* k1 = nullptr;
+    CKS(S.get(&k1, (size_t)k * NS * w + 16));
+    for (int d = 0; d < k; ++d) {
+        keys[d] = (unsigned char*)H->sel_keys + (size_t)d * NS * w;
+        keys[MAXK + d] = k1 + (size_t)d * NS * w;
+    }
+    const int T = sel_finish_tile(key64, k);
+    const int stile = T >= 1024 ? 2048 : 1024;  // a level tile touches at most 4 segments of >= T tuples
+    int lam = 0;
+    while (max_seg(M, lam) > T) ++lam;
+    void* segs = nullptr;
+    uint32_t *ghist = nullptr, *unresolved = nullptr;
+    int32_t* gany = nullptr;
+    const int64_t nsegmax = lam > 0 ? ((int64_t)1 << (lam - 1)) : 1;
+    CKS(S.get(&segs, (size_t)nsegmax * sel_seg_bytes(key64)));
+    CKS(S.get(&ghist, (size_t)nsegmax * RADIX * 4));
+    CKS(S.get(&gany, (size_t)nsegmax * RADIX * 4));
+    CKS(S.get(&unresolved, 16));
+    const int nbytes = k * w;
+    int cur = 0;
+    for (int L = 0; L < lam; ++L) {
+        LaunchTimer lt(ctx, F_SELECT, (double)M, nullptr, 0.0);
+        CK(launch_sel_level(key64, ids, keys, cur, k, (int32_t)M, L, stile, segs, ghist, gany, unresolved, node, 0, d_err, s,
+                            0, 0, 0));
+        // rounds 0 and 1 always run; later rounds until no segment is open
+        CK(launch_sel_level(key64, ids, keys, cur, k, (int32_t)M, L, stile, segs, ghist, gany, unresolved, node, 0, d_err, s,
+                            0, std::min(2, nbytes), 1));
+        ctx->launches += 2 * std::min(2, nbytes);
+        for (int r = 2; r < nbytes; ++r) {
+            uint32_t open = 0;
+            CK(cudaMemsetAsync(unresolved, 0, 4, s));
+            CK(launch_sel_level(key64, ids, keys, cur, k, (int32_t)M, L, stile, segs, ghist, gany, unresolved, node, 0,
+                                d_err, s, r, r + 1, 1));
+            ctx->launches += 2;
+            CK(cudaMemcpyAsync(&open, unresolved, 4, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (open == 0) break;
+        }
+        CK(launch_sel_level(key64, ids, keys, cur, k, (int32_t)M, L, stile, segs, ghist, gany, unresolved, node, 0, d_err, s,
+                            0, 0, 2));
+        cur ^= 1;
+    }
+    // children and split dimension of the nodes above the finisher level
+    CloudDev cd{};
+    cd.off = 0;
+    cd.in_off = 0;
+    cd.m = (int32_t)M;
+    cd.lam = lam;
+    cd.medr_off = 0;
+    cd.node = node;
+    cd.left = left;
+    cd.right = right;
+    cd.dim = dim;
+    const int64_t top = lam > 0 ? ((int64_t)1 << lam) - 1 : 0;
+    if (top > 0) {
+        CloudDev* d_cd = nullptr;
+        int64_t* d_prefix = nullptr;
+        CKS(S.get(&d_cd, sizeof(CloudDev)));
+        CKS(S.get(&d_prefix, 2 * sizeof(int64_t)));
+        const int64_t prefix[2] = {0, top};
+        CK(cudaMemcpyAsync(d_cd, &cd, sizeof(CloudDev), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(d_prefix, prefix, sizeof(prefix), cudaMemcpyHostToDevice, s));
+        LaunchTimer lt(ctx, F_TOP, (double)top, nullptr, 13.0);
+        CK(launch_top_nodes(d_cd, d_prefix, 1, top, k, H->perm0, nullptr, 0, s));
+        CK(cudaStreamSynchronize(s));  // the host copies of cd and prefix go out of scope
+    }
+    {
+        LaunchTimer lt(ctx, F_SELECT_FINISH, (double)M, nullptr, 0.0);
+        CK(launch_sel_finish(key64, ids, keys, cur, k, (int32_t)M, lam, T, node, left, right, dim, 0, d_err, s));
+    }
+    CKS(check_device_err(ctx, d_err));
+    if (!out->on_device) {
+        CK(cudaMemcpyAsync(out->node_tuple, node, (size_t)M * 4, cudaMemcpyDeviceToHost, s));
+        if (out->left) CK(cudaMemcpyAsync(out->left, left, (size_t)M * 4, cudaMemcpyDeviceToHost, s));
+        if (out->right) CK(cudaMemcpyAsync(out->right, right, (size_t)M * 4, cudaMemcpyDeviceToHost, s));
+        if (out->dim) CK(cudaMemcpyAsync(out->dim, dim, (size_t)M, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return KD_OK;
+}
+
 // ---------------------------------------------------------------- serving
 constexpr size_t SERVE_QUEUE_MAX = 1 << 20;
 constexpr int SERVE_WORKERS = 2;              // batches in flight on the device at once
@@ -1350,7 +1498,8 @@ kd_status kd_create(kd_ctx** out, const kd_config* cfg) {
     {
         std::lock_guard<std::mutex> lk(init_mu);
         if (c.device < 64 && !init_done[c.device]) {
-            if (init_presort_kernels() != cudaSuccess || init_build_kernels() != cudaSuccess) {
+            if (init_presort_kernels() != cudaSuccess || init_build_kernels() != cudaSuccess ||
+                init_select_kernels() != cudaSuccess) {
                 cudaGetLastError();
                 return KD_EDEVICE;
             }
@@ -1420,6 +1569,20 @@ kd_status kd_build(kd_ctx* ctx, kd_handle h, kd_tree* out) {
     cudaSetDevice(ctx->device);
     ctx->last_error.clear();
     kd_status st = out ? build_batch(ctx, h, out) : fail(ctx, KD_EINVAL, "tree output is NULL");
+    if (st == KD_OK && (ctx->debug & 2)) collect_timing(ctx);
+    release_handle(ctx, h);
+    return st;
+}
+
+kd_status kd_build_select(kd_ctx* ctx, const kd_cloud* cloud, kd_tree* out) {
+    if (!ctx || !cloud || !out) return KD_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    cudaSetDevice(ctx->device);
+    ctx->last_error.clear();
+    kd_presorted* h = nullptr;
+    kd_status st = presort_batch(ctx, cloud, 1, &h, /*all_arrays=*/false);
+    if (st != KD_OK) return st;
+    st = select_build(ctx, h, out);
     if (st == KD_OK && (ctx->debug & 2)) collect_timing(ctx);
     release_handle(ctx, h);
     return st;

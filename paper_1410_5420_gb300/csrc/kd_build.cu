@@ -41,32 +41,6 @@ namespace kd {
 
 constexpr uint32_t INV = 0xffffffffu;
 
-// Level-L segments touching the tile [pos0, pos0 + npos): at most
-// LEVEL_NSMAX (the host sizes tiles so that this holds).  Thread 0 only.
-__device__ __forceinline__ int tile_segments(int32_t pos0, int32_t npos, int32_t m, int L, int32_t* lo, int32_t* hi,
-                                             int32_t* idx, int* err) {
-    int ns = 0;
-    int32_t i = pos0;
-    const int32_t pend = pos0 + npos - 1;
-    while (i <= pend) {
-        const Seg sg = segment_of(i, m, L);
-        if (sg.idx < 0) {
-            ++i;
-            continue;
-        }
-        if (ns == LEVEL_NSMAX) {
-            atomicOr(err, ERR_INTERNAL);
-            break;
-        }
-        lo[ns] = sg.lo;
-        hi[ns] = sg.hi;
-        idx[ns] = sg.idx;
-        ++ns;
-        i = sg.hi + 1;
-    }
-    return ns;
-}
-
 // ------------------------------------------------------------ level step
 // A level step is four launches:
 //   k_level_tiles  one warp per tile: the tile's level-lev_in segments and
@@ -240,23 +214,6 @@ template <int K, int IPT>
 constexpr size_t level_smem_bytes(bool move) {
     return (size_t)LEVEL_STAGES *
            (trec_words(K) + level_nbp(K) + (move ? K : K - 1) * (LEVEL_THREADS * IPT + PLANE_SLACK)) * 4;
-}
-
-// Segment slot of cloud-local position pos among the tile's ns segments
-// [lo[x], hi[x]]; -1 for an address that is a node of a shallower level
-// (no element there).
-__device__ __forceinline__ int tile_slot(const int32_t (&lo)[LEVEL_NSMAX], const int32_t (&hi)[LEVEL_NSMAX], int ns,
-                                         int32_t pos) {
-    int sj = 0;
-    int32_t a = lo[0], z = hi[0];
-#pragma unroll
-    for (int x = 1; x < LEVEL_NSMAX; ++x)
-        if (x < ns && pos >= lo[x]) {
-            sj = x;
-            a = lo[x];
-            z = hi[x];
-        }
-    return (ns > 0 && pos >= a && pos <= z) ? sj : -1;
 }
 
 // Segment bounds of a tile record, in registers.

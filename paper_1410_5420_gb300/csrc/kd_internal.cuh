@@ -318,6 +318,49 @@ __host__ __device__ __forceinline__ int32_t child_mid(int32_t lo, int32_t hi) {
     return hi < lo ? -1 : lo + ((hi - lo) >> 1);
 }
 
+// Level-L segments touching the tile [pos0, pos0 + npos): at most
+// LEVEL_NSMAX (the host sizes tiles so that this holds).  Thread 0 only.
+__device__ __forceinline__ int tile_segments(int32_t pos0, int32_t npos, int32_t m, int L, int32_t* lo, int32_t* hi,
+                                             int32_t* idx, int* err) {
+    int ns = 0;
+    int32_t i = pos0;
+    const int32_t pend = pos0 + npos - 1;
+    while (i <= pend) {
+        const Seg sg = segment_of(i, m, L);
+        if (sg.idx < 0) {
+            ++i;
+            continue;
+        }
+        if (ns == LEVEL_NSMAX) {
+            atomicOr(err, ERR_INTERNAL);
+            break;
+        }
+        lo[ns] = sg.lo;
+        hi[ns] = sg.hi;
+        idx[ns] = sg.idx;
+        ++ns;
+        i = sg.hi + 1;
+    }
+    return ns;
+}
+
+// Segment slot of cloud-local position pos among the tile's ns segments
+// [lo[x], hi[x]]; -1 for an address that is a node of a shallower level
+// (no element there).
+__device__ __forceinline__ int tile_slot(const int32_t (&lo)[LEVEL_NSMAX], const int32_t (&hi)[LEVEL_NSMAX], int ns,
+                                         int32_t pos) {
+    int sj = 0;
+    int32_t a = lo[0], z = hi[0];
+#pragma unroll
+    for (int x = 1; x < LEVEL_NSMAX; ++x)
+        if (x < ns && pos >= lo[x]) {
+            sj = x;
+            a = lo[x];
+            z = hi[x];
+        }
+    return (ns > 0 && pos >= a && pos <= z) ? sj : -1;
+}
+
 // ------------------------------------------------------ launch plumbing
 struct PayloadArgs {
     const uint32_t* src[MAXPAY];  // nullptr: the source position (iota)

@@ -16,8 +16,9 @@ builder's own per-kernel byte model is reported beside it.
 ``cpu_baseline``: the single-threaded C oracle on a bounded sample of the
 same workload.  ``batched``: the 4096-cloud workload in one kd_build_batch
 call against per-cloud builds (serial, and pipelined over host threads).
-``served``: the 20000-request Poisson stream through kd_submit / kd_wait
-against serial plain builds.
+``sweep``: n = 2^22 at k = 2..6 for the presorting build and the O(n log n)
+median-selection build side by side.  ``served``: the 20000-request Poisson
+stream through kd_submit / kd_wait against serial plain builds.
 
 Multi-GPU: the build does not shard; ``--gpus N`` under torchrun runs N
 independent replicas (weak scaling, no collective on the data path).
@@ -331,41 +332,59 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
-def run_sweep(args):
+def sweep_result(args, dev_index=0):
     """Dimension sweep: n = 2^22 tuples at k = 2..6, int64 uniform in
-    [0, 2^40) (seed 3 + k): points/s of presort + build and the bytes each
-    level step moves per element as k grows."""
+    [0, 2^40) (seed 3 + k): points/s of the presorting build (kd_presort +
+    kd_build) and of the O(n log n) median-selection build
+    (kd_build_select) on the same clouds, the bytes each level step of the
+    presorting build moves per element, and where the two cross."""
     import torch
     import kdgen
     from paper_1410_5420_gb300 import api
     n = min(args.n, 1 << 22)
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.current_stream(dev_index)
     rows = []
     for k in range(2, 7):
-        x = torch.from_numpy(kdgen.sweep_int64(k, n=n)).cuda()
-        ctx = api.kd_create(0, stream=stream, debug=2)
-        for _ in range(max(1, args.warmup)):
-            api.build_tree(ctx, x, on_device=True)
+        x = torch.from_numpy(kdgen.sweep_int64(k, n=n)).cuda(dev_index)
+
+        def timed(fn, steps):
+            for _ in range(max(1, min(args.warmup, 3))):
+                fn()
+            torch.cuda.synchronize(dev_index)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                r = fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev_index)
+            return e0.elapsed_time(e1) / steps, r
+
+        ctx = api.kd_create(dev_index, stream=stream, debug=2)
+        ms_p, t = timed(lambda: api.build_tree(ctx, x, on_device=True), args.steps)
+        ms_s, t2 = timed(lambda: api.kd_build_select(ctx, x, on_device=True), args.steps)
+        same = bool(torch.equal(t["node_tuple"], t2["node_tuple"]))
         api.kd_kernel_stats_reset(ctx)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            t = api.build_tree(ctx, x, on_device=True)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / args.steps
+        api.build_tree(ctx, x, on_device=True)
         st = api.kd_kernel_stats(ctx)
         lv = st["level_pass"]
-        rows.append({"k": k, "m": t["m"], "ms": ms, "points_per_s": n / (ms / 1000.0),
-                     "level_steps": lv["launches"] / args.steps,
-                     "level_bytes_per_element": lv["bytes"] / lv["units"] if lv["units"] else None,
-                     "families_ms": {f: v["ms"] / args.steps for f, v in st.items() if v["launches"]}})
+        rows.append({"k": k, "m": t["m"], "presort_ms": ms_p, "presort_points_per_s": n / (ms_p / 1000.0),
+                     "select_ms": ms_s, "select_points_per_s": n / (ms_s / 1000.0), "trees_identical": same,
+                     "level_steps": lv["launches"],
+                     "level_bytes_per_element": lv["bytes"] / lv["units"] if lv["units"] else None})
         ctx.close()
+        del x
+    faster = [r["k"] for r in rows if r["select_ms"] < r["presort_ms"]]
+    return {"workload": f"dimension sweep: n={n} tuples, k=2..6, int64 uniform in [0, 2^40) (seed 3+k)",
+            "rows": rows, "select_faster_at_k": faster,
+            "presort_ms_per_dimension": (rows[-1]["presort_ms"] - rows[0]["presort_ms"]) / (len(rows) - 1),
+            "select_ms_per_dimension": (rows[-1]["select_ms"] - rows[0]["select_ms"]) / (len(rows) - 1)}
+
+
+def run_sweep(args):
+    r = sweep_result(args)
     line = {"metric": METRIC, "mode": "sweep", "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": f"dimension sweep: n={n} tuples, k=2..6, int64 uniform in [0, 2^40) (seed 3+k)"},
-            "rows": rows}
+            "config": {"workload": r["workload"]}, "sweep": r}
     print(json.dumps(line), flush=True)
 
 
@@ -700,6 +719,8 @@ def main():
     torch.cuda.empty_cache()
     if not args.no_extras and world == 1:
         line["batched"] = batched_result(args, dev)
+        torch.cuda.empty_cache()
+        line["sweep"] = sweep_result(args, dev)
         torch.cuda.empty_cache()
         line["served"] = served_result(args, dev)
     if not args.no_cpu_baseline and world >= 1:

@@ -65,17 +65,6 @@ __device__ __forceinline__ int sel_shift(int r) {
     return 8 * (B - 1 - r % B);
 }
 
-// Do the bits of words[0 .. j] above bit `sh` of word j (and all of the
-// earlier words) equal the prefix?
-template <typename KW>
-__device__ __forceinline__ bool sel_prefix_match(const KW* words, const KW* prefix, int j, int sh) {
-    for (int jj = 0; jj < j; ++jj)
-        if (words[jj] != prefix[jj]) return false;
-    constexpr int BITS = 8 * sizeof(KW);
-    if (sh + 8 >= BITS) return true;  // nothing of word j chosen yet
-    return (words[j] >> (sh + 8)) == (prefix[j] >> (sh + 8));
-}
-
 template <typename KW>
 __global__ void k_sel_init(int32_t m, int L, int nseg, SelSeg<KW>* __restrict__ segs, uint32_t* __restrict__ ghist) {
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nseg; s += gridDim.x * blockDim.x) {
@@ -140,20 +129,33 @@ __global__ void __launch_bounds__(SEL_THREADS) k_sel_hist(const __grid_constant_
     const int p = L % k;
     for (int e = 0; e < SEL_IPT; ++e) {
         const int o = e * SEL_THREADS + tid;
-        if (o >= npos) break;
         const int32_t pos = pos0 + o;
-        const int sj = tile_slot(T.lo, T.hi, T.ns, pos);
-        if (sj < 0 || T.pos[sj] != -1) continue;
-        KW w[MAXK];
-        for (int jj = 0; jj <= j; ++jj) {
-            int d = p + jj;
-            if (d >= k) d -= k;
-            w[jj] = bufs.key[cur][d][pos];
+        int sj = o < npos ? tile_slot(T.lo, T.hi, T.ns, pos) : -1;
+        bool cand = sj >= 0 && T.pos[sj] == -1;
+        uint32_t dig = 0;
+        if (cand) {
+            // the words of the super key up to word j, compared with the prefix
+            KW wj = 0;
+#pragma unroll
+            for (int jj = 0; jj < MAXK; ++jj) {
+                if (jj > j) break;
+                int d = p + jj;
+                if (d >= k) d -= k;
+                const KW x = bufs.key[cur][d][pos];
+                if (jj < j) cand = cand && x == T.prefix[sj][jj];
+                else wj = x;
+            }
+            if (cand && sh + 8 < 8 * B) cand = (wj >> (sh + 8)) == (T.prefix[sj][j] >> (sh + 8));
+            dig = (uint32_t)(wj >> sh) & 255u;
         }
-        if (!sel_prefix_match<KW>(w, T.prefix[sj], j, sh)) continue;
-        const uint32_t dig = (uint32_t)(w[j] >> sh) & 255u;
-        atomicAdd(&h[sj][dig], 1u);
-        any[sj][dig] = pos;
+        // candidates of one segment and digit in this warp add once (long runs of
+        // equal top bytes would otherwise serialise on one counter)
+        const uint32_t key = cand ? ((uint32_t)sj << 8 | dig) : 0xffffffffu;
+        const uint32_t peers = __match_any_sync(0xffffffffu, key);
+        if (cand && (threadIdx.x & 31) == __ffs(peers) - 1) {
+            atomicAdd(&h[sj][dig], (uint32_t)__popc(peers));
+            any[sj][dig] = pos;
+        }
     }
     __syncthreads();
     for (int x = 0; x < T.ns; ++x) {
@@ -234,14 +236,6 @@ __global__ void k_sel_choose(int nseg, int r, int nbytes, SelSeg<KW>* __restrict
     for (int i = 0; i < 8; ++i) hs[lane * 8 + i] = 0;
 }
 
-// Super-key compare of an element's words with the median's: -1, 0, 1.
-template <typename KW>
-__device__ __forceinline__ int sel_cmp(const KW* a, const KW* b, int k) {
-    for (int j = 0; j < k; ++j)
-        if (a[j] != b[j]) return a[j] < b[j] ? -1 : 1;
-    return 0;
-}
-
 // Partition around the resolved medians; the median of each segment becomes
 // the node at the segment's middle address.
 template <typename KW>
@@ -283,13 +277,15 @@ __global__ void __launch_bounds__(SEL_THREADS) k_sel_move(const __grid_constant_
             atomicOr(err, ERR_INTERNAL);
             continue;
         }
-        KW w[MAXK];
-        for (int j = 0; j < k; ++j) {
+        int c = 0;
+#pragma unroll
+        for (int j = 0; j < MAXK; ++j) {
+            if (j >= k || c != 0) break;
             int d = p + j;
             if (d >= k) d -= k;
-            w[j] = bufs.key[cur][d][pos];
+            const KW x = bufs.key[cur][d][pos], y = med[sj][j];
+            if (x != y) c = x < y ? -1 : 1;
         }
-        const int c = sel_cmp<KW>(w, med[sj], k);
         slot[e] = sj;
         if (c == 0) {
             if (pos != T.pos[sj]) atomicOr(err, ERR_INTERNAL);
@@ -373,23 +369,26 @@ __global__ void __launch_bounds__(SEL_THREADS) k_sel_finish(const __grid_constan
         return;
     }
     // shared memory layout (see sel_finish_smem)
-    KW* keys[2];
-    uint32_t* ids[2];
     unsigned char* q = sf_raw;
-    for (int bb = 0; bb < 2; ++bb) {
-        keys[bb] = reinterpret_cast<KW*>(q);
-        q += (size_t)T * k * sizeof(KW);
-        ids[bb] = reinterpret_cast<uint32_t*>(q);
-        q += (size_t)T * 4;
-    }
+    KW* const keys0 = reinterpret_cast<KW*>(q);
+    q += (size_t)T * k * sizeof(KW);
+    uint32_t* const ids0 = reinterpret_cast<uint32_t*>(q);
+    q += (size_t)T * 4;
+    KW* const keys1 = reinterpret_cast<KW*>(q);
+    q += (size_t)T * k * sizeof(KW);
+    uint32_t* const ids1 = reinterpret_cast<uint32_t*>(q);
+    q += (size_t)T * 4;
+    // buffer bb of the element planes (selected, not indexed, to stay in registers)
+    auto KB = [&](int bb) { return bb ? keys1 : keys0; };
+    auto IB = [&](int bb) { return bb ? ids1 : ids0; };
     uint32_t* segw = reinterpret_cast<uint32_t*>(q);
     q += (size_t)T * 4;
     uint8_t* subid = q;
     q += ((size_t)T + 15) & ~(size_t)15;
     SelSub<KW>* sub = reinterpret_cast<SelSub<KW>*>(q);
     for (int i = tid; i < S; i += SEL_THREADS) {
-        ids[0][i] = bufs.id[cur][ulo + i];
-        for (int d = 0; d < k; ++d) keys[0][d * T + i] = bufs.key[cur][d][ulo + i];
+        ids0[i] = bufs.id[cur][ulo + i];
+        for (int d = 0; d < k; ++d) keys0[d * T + i] = bufs.key[cur][d][ulo + i];
         segw[i] = (uint32_t)(S - 1) << 12;  // lo 0, hi S-1
         subid[i] = 0;
     }
@@ -426,22 +425,29 @@ __global__ void __launch_bounds__(SEL_THREADS) k_sel_finish(const __grid_constan
             const int sh = 8 * (B - 1 - r % B) + ((r4 & 1) ? 0 : 4);
             int dj = p + j;
             if (dj >= k) dj -= k;
-            for (int i = tid; i < S; i += SEL_THREADS) {
-                if (segw[i] & SF_DONE) continue;
-                SelSub<KW>& U = sub[subid[i]];
-                if (U.pos != -1) continue;
-                bool cand = true;
-                for (int jj = 0; jj < j && cand; ++jj) {
-                    int d = p + jj;
-                    if (d >= k) d -= k;
-                    cand = keys[b][d * T + i] == U.prefix[jj];
+            for (int i0 = 0; i0 < S; i0 += SEL_THREADS) {  // whole warps, for the aggregation below
+                const int i = i0 + tid;
+                bool cand = i < S && !(segw[i] & SF_DONE);
+                const int su = cand ? subid[i] : 0;
+                cand = cand && sub[su].pos == -1;
+                uint32_t nib = 0;
+                if (cand) {
+                    const SelSub<KW>& U = sub[su];
+                    for (int jj = 0; jj < j && cand; ++jj) {
+                        int d = p + jj;
+                        if (d >= k) d -= k;
+                        cand = KB(b)[d * T + i] == U.prefix[jj];
+                    }
+                    const KW wj = KB(b)[dj * T + i];
+                    if (cand && sh + 4 < 8 * B) cand = (wj >> (sh + 4)) == (U.prefix[j] >> (sh + 4));
+                    nib = (uint32_t)(wj >> sh) & 15u;
                 }
-                const KW wj = keys[b][dj * T + i];
-                if (cand && sh + 4 < 8 * B) cand = (wj >> (sh + 4)) == (U.prefix[j] >> (sh + 4));
-                if (!cand) continue;
-                const uint32_t nib = (uint32_t)(wj >> sh) & 15u;
-                atomicAdd(&U.hist[nib], 1u);
-                U.any[nib] = i;
+                const uint32_t key = cand ? ((uint32_t)su << 4 | nib) : 0xffffffffu;
+                const uint32_t peers = __match_any_sync(0xffffffffu, key);
+                if (cand && lane == __ffs(peers) - 1) {
+                    atomicAdd(&sub[su].hist[nib], (uint32_t)__popc(peers));
+                    sub[su].any[nib] = i;
+                }
             }
             __syncthreads();
             bool open = false;
@@ -493,12 +499,12 @@ __global__ void __launch_bounds__(SEL_THREADS) k_sel_finish(const __grid_constan
             for (int jj = 0; jj < k && c == 0; ++jj) {
                 int d = p + jj;
                 if (d >= k) d -= k;
-                const KW x = keys[b][d * T + i], y = keys[b][d * T + U.pos];
+                const KW x = KB(b)[d * T + i], y = KB(b)[d * T + U.pos];
                 if (x != y) c = x < y ? -1 : 1;
             }
             if (c == 0) {
                 if (i != U.pos) bad = true;
-                sf_emit<KW>(node, left, right, dim, ulo, U.lo, U.hi, mid, ids[b][i], in_off, p);
+                sf_emit<KW>(node, left, right, dim, ulo, U.lo, U.hi, mid, IB(b)[i], in_off, p);
                 continue;
             }
             const int f = c > 0 ? 1 : 0;
@@ -507,8 +513,8 @@ __global__ void __launch_bounds__(SEL_THREADS) k_sel_finish(const __grid_constan
                 bad = true;
                 continue;
             }
-            ids[b ^ 1][dst] = ids[b][i];
-            for (int d = 0; d < k; ++d) keys[b ^ 1][d * T + dst] = keys[b][d * T + i];
+            IB(b ^ 1)[dst] = IB(b)[i];
+            for (int d = 0; d < k; ++d) KB(b ^ 1)[d * T + dst] = KB(b)[d * T + i];
         }
         __syncthreads();
         // the segment of every position at the next level
@@ -549,33 +555,32 @@ __global__ void __launch_bounds__(SEL_THREADS) k_sel_finish(const __grid_constan
         }
         const bool in = lane < n;
         KW w[MAXK];
-        uint32_t id = in ? ids[b][lo + lane] : 0u;
+        uint32_t id = in ? IB(b)[lo + lane] : 0u;
 #pragma unroll
-        for (int d = 0; d < MAXK; ++d) w[d] = (in && d < k) ? keys[b][d * T + lo + lane] : (KW)0;
+        for (int d = 0; d < MAXK; ++d) w[d] = (in && d < k) ? KB(b)[d * T + lo + lane] : (KW)0;
         uint32_t less[MAXK];
 #pragma unroll
         for (int qd = 0; qd < MAXK; ++qd) less[qd] = 0;
+        // per source lane: which of its coordinate words are below / equal to
+        // this lane's (bit d); super key q then reads them rotated by q
+        const uint32_t full = (1u << k) - 1u;
         for (int src = 0; src < n; ++src) {
-            KW o[MAXK];
+            uint32_t ltm = 0, eqm = 0;
 #pragma unroll
-            for (int d = 0; d < MAXK; ++d) o[d] = d < k ? __shfl_sync(0xffffffffu, w[d], src) : (KW)0;
+            for (int d = 0; d < MAXK; ++d) {
+                if (d < k) {
+                    const KW o = __shfl_sync(0xffffffffu, w[d], src);
+                    ltm |= (o < w[d] ? 1u : 0u) << d;
+                    eqm |= (o == w[d] ? 1u : 0u) << d;
+                }
+            }
 #pragma unroll
             for (int qd = 0; qd < MAXK; ++qd) {
-                if (qd >= k) break;
-                int c = 0;
-                for (int jj = 0; jj < k && c == 0; ++jj) {
-                    int d = qd + jj;
-                    if (d >= k) d -= k;
-                    KW a = 0, bw = 0;
-#pragma unroll
-                    for (int dd = 0; dd < MAXK; ++dd)
-                        if (dd == d) {
-                            a = o[dd];
-                            bw = w[dd];
-                        }
-                    if (a != bw) c = a < bw ? -1 : 1;
+                if (qd < k) {
+                    const uint32_t ne = ~((eqm >> qd) | (eqm << (k - qd))) & full;
+                    const uint32_t lt = ((ltm >> qd) | (ltm << (k - qd))) & full;
+                    if (ne && ((lt >> (__ffs(ne) - 1)) & 1u)) less[qd] |= 1u << src;
                 }
-                if (c < 0) less[qd] |= 1u << src;
             }
         }
         uint32_t subm = __ballot_sync(0xffffffffu, in);

@@ -363,12 +363,20 @@ def sweep_result(args, dev_index=0):
         ms_p, t = timed(lambda: api.build_tree(ctx, x, on_device=True), args.steps)
         ms_s, t2 = timed(lambda: api.kd_build_select(ctx, x, on_device=True), args.steps)
         same = bool(torch.equal(t["node_tuple"], t2["node_tuple"]))
+        sched_ms = {}
+        for name, sc in (("deferred", 1), ("every_level", 2)):
+            c2 = api.kd_create(dev_index, stream=stream, schedule=sc)
+            ms_x, t3 = timed(lambda: api.build_tree(c2, x, on_device=True), args.steps)
+            same = same and bool(torch.equal(t["node_tuple"], t3["node_tuple"]))
+            sched_ms[name] = ms_x
+            c2.close()
         api.kd_kernel_stats_reset(ctx)
         api.build_tree(ctx, x, on_device=True)
         st = api.kd_kernel_stats(ctx)
         lv = st["level_pass"]
         rows.append({"k": k, "m": t["m"], "presort_ms": ms_p, "presort_points_per_s": n / (ms_p / 1000.0),
                      "select_ms": ms_s, "select_points_per_s": n / (ms_s / 1000.0), "trees_identical": same,
+                     "schedule_ms": {"multi_level": ms_p, **sched_ms},
                      "level_steps": lv["launches"],
                      "level_bytes_per_element": lv["bytes"] / lv["units"] if lv["units"] else None})
         ctx.close()
@@ -624,6 +632,16 @@ def main():
     stats = api.kd_kernel_stats(ctx_t)
     ctx_t.close()
 
+    # the level schedules at the headline size (same tree): the paper's
+    # Section 2.1 form, its deferred partitioning, and the default
+    sched_ab = {"multi_level": ms_step}
+    for name, sc in (("deferred", 1), ("every_level", 2)):
+        c2 = api.kd_create(dev, stream=stream, schedule=sc, switch_threshold=tuned["switch_threshold"],
+                           level_tile=tuned["level_tile"])
+        step(c2)
+        sched_ab[name] = timed_steps(c2, max(1, min(args.steps, 3)))
+        c2.close()
+
     # end to end: pinned host coordinates in, whole tree back to pinned host
     out_node = torch.empty(n, dtype=torch.int32).pin_memory()
     out_l = torch.empty(n, dtype=torch.int32).pin_memory()
@@ -709,6 +727,7 @@ def main():
                         "own_gbs": gbs(v["bytes"], v["ms"]) or None}
                     for f, v in stats.items() if v["launches"]},
         "ms_per_step_with_launch_events": ms_step_events,
+        "schedule_ms_per_step": sched_ab,
         "clocks": clk,
         "e2e": {"value": whole_job_value(world, n, e2e_s), "unit": UNIT, "h2d_bytes_per_step": n * K * 4,
                 "d2h_bytes_per_step": m * 13},

@@ -67,7 +67,19 @@ typedef struct {
                                 thousand polls and make the next presort's first look-back
                                 wait run out once, which it reports as KD_ETIMEOUT */
     const char *tune_cache;  /* autotuner cache file (read by kd_create, rewritten by kd_autotune); NULL: none */
+    int schedule;            /* level schedule of kd_build (same tree under each):
+                                KD_SCHEDULE_MULTI (0, default): an array is partitioned only when it is
+                                  about to become primary, through up to k-1 levels in one pass;
+                                KD_SCHEDULE_DEFERRED: Appendix "Deferred Merge Sort and Partitioning":
+                                  array d first appears at level d, then every non-primary array is
+                                  partitioned at every level;
+                                KD_SCHEDULE_EVERY_LEVEL: Section 2.1: every non-primary array is
+                                  partitioned at every level */
 } kd_config;
+
+#define KD_SCHEDULE_MULTI 0
+#define KD_SCHEDULE_DEFERRED 1
+#define KD_SCHEDULE_EVERY_LEVEL 2
 
 typedef struct {
     const void *coords; /* row-major n x k array of dtype; borrowed for the call */

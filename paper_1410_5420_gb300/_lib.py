@@ -17,6 +17,7 @@ KD_MAX_K = 8
 KD_MAX_N = (1 << 30) - 1
 KD_NOALLOC_MAX_N = 16384
 KD_KNN_MAX = 32
+KD_SCHEDULE_MULTI, KD_SCHEDULE_DEFERRED, KD_SCHEDULE_EVERY_LEVEL = 0, 1, 2
 STATUS_NAMES = {0: "KD_OK", -1: "KD_EINVAL", -2: "KD_ENOMEM", -3: "KD_EDEVICE", -4: "KD_ETIMEOUT",
                 -5: "KD_EBUSY", -6: "KD_ENAN"}
 
@@ -34,7 +35,8 @@ EXPORTS = ["kd_create", "kd_presort", "kd_handle_info", "kd_handle_arrays", "kd_
 class KdConfig(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
                 ("mem_budget_bytes", ctypes.c_size_t), ("level_tile", ctypes.c_int),
-                ("switch_threshold", ctypes.c_int), ("debug", ctypes.c_int), ("tune_cache", ctypes.c_char_p)]
+                ("switch_threshold", ctypes.c_int), ("debug", ctypes.c_int), ("tune_cache", ctypes.c_char_p),
+                ("schedule", ctypes.c_int)]
 
 
 class KdCloud(ctypes.Structure):

@@ -69,16 +69,18 @@ class Handle:
 
 
 def kd_create(device: int = 0, stream=None, mem_budget_bytes: int = 0, switch_threshold: int = 0,
-              debug: int = 0, level_tile: int = 0, tune_cache: str | None = None) -> Context:
+              debug: int = 0, level_tile: int = 0, tune_cache: str | None = None,
+              schedule: int = 0) -> Context:
     """kd_create.  ``stream``: a torch.cuda.Stream, an int handle, or None for
     torch's current stream on ``device``.  ``switch_threshold`` / ``level_tile``:
-    0 for the tuned (or default) values; ``tune_cache``: the autotuner's file."""
+    0 for the tuned (or default) values; ``tune_cache``: the autotuner's file;
+    ``schedule``: the level schedule (KD_SCHEDULE_MULTI / _DEFERRED / _EVERY_LEVEL)."""
     lib = _lib.load()
     if stream is None and torch is not None and torch.cuda.is_available():
         stream = torch.cuda.current_stream(device)
     sh = stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0)
     cfg = KdConfig(device, ctypes.c_void_p(sh), mem_budget_bytes, level_tile, switch_threshold, debug,
-                   tune_cache.encode() if tune_cache else None)
+                   tune_cache.encode() if tune_cache else None, schedule)
     out = ctypes.c_void_p()
     rc = lib.kd_create(ctypes.byref(out), ctypes.byref(cfg))
     if rc != _lib.KD_OK:

@@ -130,6 +130,7 @@ struct kd_ctx {
     std::map<uint32_t, Tuned> tuning;
     std::string tune_cache;
     int force_smax = 0, force_ltile = 0;  // the candidate kd_autotune is timing
+    int schedule = KD_SCHEDULE_MULTI;     // level schedule (kd_config.schedule)
     int last_smax = 0, last_ltile = 0;    // what the last build used
     // Failure-detection tests (debug bit 8): the look-back polls are bounded
     // by a few thousand instead of 2^24, and the next presort's first sort
@@ -1044,11 +1045,32 @@ kd_status build_batch(kd_ctx* ctx, kd_presorted* H, kd_tree* outs) {
     }
     bool need_bufs = false;
     if (k >= 2) {
-        int tmax = 0;
-        for (int i = 0; i < count; ++i)
-            if (lam[i] >= 1) tmax = std::max(tmax, lam[i] + k - 2);
-        for (int t = 1; t <= tmax; ++t) {
-            const int q = t % k;
+        // Level schedule.  Array q lies sorted within the segments of some
+        // level; a step moves it from level lin to level lout (applying the
+        // splits of levels lin .. lout-1 around their medians).  At its
+        // primary level its halves are in place (a free split).
+        //   KD_SCHEDULE_MULTI (default): step t moves array t mod k to level
+        //     t, through up to k-1 levels at once: each array is partitioned
+        //     only when it is about to become primary, one pass per level.
+        //   KD_SCHEDULE_DEFERRED (Appendix "Deferred Merge Sort and
+        //     Partitioning"): array d first appears at level d, already split
+        //     by levels 0 .. d-1 (one pass); from then on every non-primary
+        //     array is partitioned at every level, one level per pass.
+        //   KD_SCHEDULE_EVERY_LEVEL (Section 2.1): every non-primary array is
+        //     partitioned at every level, one level per pass.
+        const int sched = ctx->schedule;
+        int lmax = 0;
+        for (int i = 0; i < count; ++i) lmax = std::max(lmax, lam[i]);
+        std::vector<std::pair<int, int>> steps;  // (t, q): move array q to level t
+        if (sched == KD_SCHEDULE_MULTI) {
+            for (int t = 1; t <= lmax + k - 2; ++t) steps.push_back({t, t % k});
+        } else {
+            for (int t = 1; t <= lmax; ++t)
+                for (int q = 0; q < k; ++q)
+                    if (!(sched == KD_SCHEDULE_DEFERRED && q >= 1 && t < q)) steps.push_back({t, q});
+        }
+        for (const auto& tq : steps) {
+            const int t = tq.first, q = tq.second;
             std::vector<LevelJob> jl;
             int64_t ntl = 0;
             double el = 0;
@@ -1483,6 +1505,8 @@ kd_status kd_create(kd_ctx** out, const kd_config* cfg) {
     ctx->debug = c.debug;
     ctx->smax_override = c.switch_threshold;
     if (c.level_tile != 0 && c.level_tile != 1024 && c.level_tile != 2048) return KD_EINVAL;
+    if (c.schedule < KD_SCHEDULE_MULTI || c.schedule > KD_SCHEDULE_EVERY_LEVEL) return KD_EINVAL;
+    ctx->schedule = c.schedule;
     ctx->level_tile_override = c.level_tile;
     if (c.tune_cache) ctx->tune_cache = c.tune_cache;
     ctx->cfg.tune_cache = ctx->tune_cache.empty() ? nullptr : ctx->tune_cache.c_str();  // owned copy for workers

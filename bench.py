@@ -359,7 +359,7 @@ def sweep_result(args, dev_index=0):
             torch.cuda.synchronize(dev_index)
             return e0.elapsed_time(e1) / steps, r
 
-        ctx = api.kd_create(dev_index, stream=stream, debug=2)
+        ctx = api.kd_create(dev_index, stream=stream)  # no per-launch events in the timed builds
         ms_p, t = timed(lambda: api.build_tree(ctx, x, on_device=True), args.steps)
         ms_s, t2 = timed(lambda: api.kd_build_select(ctx, x, on_device=True), args.steps)
         same = bool(torch.equal(t["node_tuple"], t2["node_tuple"]))
@@ -370,9 +370,10 @@ def sweep_result(args, dev_index=0):
             same = same and bool(torch.equal(t["node_tuple"], t3["node_tuple"]))
             sched_ms[name] = ms_x
             c2.close()
-        api.kd_kernel_stats_reset(ctx)
-        api.build_tree(ctx, x, on_device=True)
-        st = api.kd_kernel_stats(ctx)
+        ctx_t = api.kd_create(dev_index, stream=stream, debug=2)  # per-launch events: level bytes
+        api.build_tree(ctx_t, x, on_device=True)
+        st = api.kd_kernel_stats(ctx_t)
+        ctx_t.close()
         lv = st["level_pass"]
         rows.append({"k": k, "m": t["m"], "presort_ms": ms_p, "presort_points_per_s": n / (ms_p / 1000.0),
                      "select_ms": ms_s, "select_points_per_s": n / (ms_s / 1000.0), "trees_identical": same,

@@ -49,6 +49,7 @@ cudaError_t launch_perm_scatter(const int64_t* m_ptr, int64_t max_m, const uint3
 cudaError_t launch_arrays_out(const int64_t* m_ptr, int64_t max_m, int k, const AllPlanes& rec,
                               const uint32_t* perm0, int32_t* out, cudaStream_t s);
 int level_tile(int k);
+cudaError_t launch_shape(int32_t m, int k, int32_t* left, int32_t* right, uint8_t* dim, cudaStream_t s);
 cudaError_t launch_tune_cloud(int dtype, void* coords, int64_t count, uint64_t seed, cudaStream_t s);
 size_t sel_seg_bytes(int key64);
 int sel_finish_tile(int key64, int k);
@@ -1145,6 +1146,32 @@ kd_status build_batch(kd_ctx* ctx, kd_presorted* H, kd_tree* outs) {
     for (int i = 0; i < count; ++i)
         unit_prefix[i + 1] = unit_prefix[i] + ((k >= 2 && cd[i].m > 0) ? ((int64_t)1 << lam[i]) : 0);
     const int64_t nunits = unit_prefix[count];
+    // A single cloud with page-locked host outputs: the children and split
+    // dimensions (pure functions of m) are computed first and copied back on
+    // a second stream while the level passes run; the finisher then runs in
+    // chunks of units and each chunk's node tuples are copied back while the
+    // next chunk runs.
+    const bool overlap_copy = any_host && count == 1 && nunits >= 64 && !(ctx->debug & 4) && !outs[0].on_device &&
+                              pinned_host(outs[0].node_tuple) && (!outs[0].left || pinned_host(outs[0].left)) &&
+                              (!outs[0].right || pinned_host(outs[0].right)) &&
+                              (!outs[0].dim || pinned_host(outs[0].dim));
+    const int nchunks = overlap_copy ? 8 : 1;
+    if (overlap_copy) {
+        CKS(ensure_copy_stream(ctx, nchunks + 2));
+        const int32_t mm = cd[0].m;
+        {
+            LaunchTimer lt(ctx, F_OTHER, 0.0);
+            CK(launch_shape(mm, k, cd[0].left, cd[0].right, cd[0].dim, s));
+        }
+        CK(cudaEventRecord(ctx->chunk_events[nchunks + 1], s));
+        CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->chunk_events[nchunks + 1], 0));
+        cudaStream_t cs = ctx->copy_stream;
+        if (outs[0].left) CK(cudaMemcpyAsync(outs[0].left, st_left, (size_t)mm * 4, cudaMemcpyDeviceToHost, cs));
+        if (outs[0].right) CK(cudaMemcpyAsync(outs[0].right, st_right, (size_t)mm * 4, cudaMemcpyDeviceToHost, cs));
+        if (outs[0].dim) CK(cudaMemcpyAsync(outs[0].dim, st_dim, (size_t)mm, cudaMemcpyDeviceToHost, cs));
+        cd[0].left = cd[0].right = nullptr;  // the level kernels and the finisher write node tuples only
+        cd[0].dim = nullptr;
+    }
     std::vector<LevelJob> flat;
     std::vector<size_t> job_off;
     for (auto& v : step_jobs) {
@@ -1183,16 +1210,6 @@ kd_status build_batch(kd_ctx* ctx, kd_presorted* H, kd_tree* outs) {
         CK(launch_level_pass(k, tile, bufs, step_q[st], d_jobs + job_off[st], (int)step_jobs[st].size(),
                              (int)step_ntiles[st], d_cd, medr, H->perm0, d_status, d_err, s));
     }
-    // A single cloud with page-locked host outputs: the finisher runs in chunks of
-    // units and each chunk's address range (which also holds the nodes
-    // above the finisher level between its units, final by now) is copied
-    // to the host on a second stream while the next chunk runs.
-    const bool overlap_copy = any_host && count == 1 && nunits >= 64 && !(ctx->debug & 4) && !outs[0].on_device &&
-                              pinned_host(outs[0].node_tuple) && (!outs[0].left || pinned_host(outs[0].left)) &&
-                              (!outs[0].right || pinned_host(outs[0].right)) &&
-                              (!outs[0].dim || pinned_host(outs[0].dim));
-    const int nchunks = overlap_copy ? 8 : 1;
-    if (overlap_copy) CKS(ensure_copy_stream(ctx, nchunks + 1));
     if (nunits > 0) {
         unsigned long long* phase = nullptr;
         if (ctx->debug & 4) {
@@ -1223,15 +1240,11 @@ kd_status build_batch(kd_ctx* ctx, kd_presorted* H, kd_tree* outs) {
                 const int64_t a0 = c == 0 ? 0 : unit_lo(u0), a1 = c + 1 == nchunks ? m0 : unit_lo(u1);
                 CK(cudaEventRecord(ctx->chunk_events[c], s));
                 CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->chunk_events[c], 0));
-                if (a1 > a0) {
-                    const size_t na = (size_t)(a1 - a0);
-                    cudaStream_t cs = ctx->copy_stream;
-                    CK(cudaMemcpyAsync(outs[0].node_tuple + a0, st_node + a0, na * 4, cudaMemcpyDeviceToHost, cs));
-                    if (outs[0].left) CK(cudaMemcpyAsync(outs[0].left + a0, st_left + a0, na * 4, cudaMemcpyDeviceToHost, cs));
-                    if (outs[0].right)
-                        CK(cudaMemcpyAsync(outs[0].right + a0, st_right + a0, na * 4, cudaMemcpyDeviceToHost, cs));
-                    if (outs[0].dim) CK(cudaMemcpyAsync(outs[0].dim + a0, st_dim + a0, na, cudaMemcpyDeviceToHost, cs));
-                }
+                // (the chunk's address range also holds the nodes above the
+                // finisher level between its units, final by now)
+                if (a1 > a0)
+                    CK(cudaMemcpyAsync(outs[0].node_tuple + a0, st_node + a0, (size_t)(a1 - a0) * 4,
+                                       cudaMemcpyDeviceToHost, ctx->copy_stream));
             }
         }
         if (phase) {

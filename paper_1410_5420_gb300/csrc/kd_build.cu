@@ -1132,6 +1132,36 @@ __global__ void k_top_nodes(const CloudDev* __restrict__ clouds, const int64_t* 
     }
 }
 
+// --------------------------------------------------------------- shape
+// Children and split dimension of every address of one tree over m
+// addresses: pure functions of m (the walk from the root to the segment
+// whose median is the address).  Used when the tree goes to host memory, so
+// that these outputs are copied back while the level passes run.
+__global__ void k_shape(int32_t m, int k, int32_t* __restrict__ left, int32_t* __restrict__ right,
+                        uint8_t* __restrict__ dim) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t a = (int32_t)i;
+        int32_t lo = 0, hi = m - 1;
+        int depth = 0;
+        for (; depth < 32; ++depth) {  // at most ceil(log2(m + 1)) steps
+            const int32_t mid = lo + ((hi - lo) >> 1);
+            if (a == mid) break;
+            if (a < mid) hi = mid - 1; else lo = mid + 1;
+        }
+        if (left) left[a] = child_mid(lo, a - 1);
+        if (right) right[a] = child_mid(a + 1, hi);
+        if (dim) dim[a] = (uint8_t)(depth % k);
+    }
+}
+
+cudaError_t launch_shape(int32_t m, int k, int32_t* left, int32_t* right, uint8_t* dim, cudaStream_t s) {
+    if (m <= 0 || (!left && !right && !dim)) return cudaSuccess;
+    int64_t g = ((int64_t)m + 255) / 256;
+    if (g > 152 * 32) g = 152 * 32;
+    k_shape<<<(unsigned)g, 256, 0, s>>>(m, k, left, right, dim);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ launchers
 int level_tile(int k) { return level_tile_of(k); }
 bool level_tile_supported(int k, int tile) {

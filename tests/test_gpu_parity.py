@@ -177,3 +177,30 @@ def test_batch_host_buffers_int64(cuda_lib, ctx):
     outs = cuda_lib.kd_build_batch(ctx, clouds)
     for c, got in zip(clouds, outs):
         assert_same_tree(got, oracle.build_tree(c))
+
+
+def test_pinned_host_inputs_and_outputs(cuda_lib, ctx):
+    """Page-locked host coordinates in and page-locked host outputs out (the
+    bench's end-to-end path): the coordinates go up in chunks, the children
+    and split dimensions come back while the level passes run and the node
+    tuples chunk by chunk behind the finisher."""
+    import ctypes
+    import torch
+    from paper_1410_5420_gb300 import _lib
+    n = (1 << 20) + 333  # above 2^20 (chunked upload) and more than 64 on-chip units
+    coords = kdgen.cloud_gmm(n, 3, 611)
+    ref = oracle.build_tree(coords)
+    pin = torch.from_numpy(coords).pin_memory()
+    outs = {"node_tuple": torch.full((n,), -9, dtype=torch.int32).pin_memory(),
+            "left": torch.full((n,), -9, dtype=torch.int32).pin_memory(),
+            "right": torch.full((n,), -9, dtype=torch.int32).pin_memory(),
+            "dim": torch.full((n,), 99, dtype=torch.uint8).pin_memory()}
+    lib = _lib.load()
+    c = _lib.KdCloud(pin.data_ptr(), n, 3, _lib.KD_F32, 0)
+    h = ctypes.c_void_p()
+    ctx.check(lib.kd_presort(ctx.ptr, ctypes.byref(c), ctypes.byref(h)))
+    tr = _lib.KdTree(0, -1, *(ctypes.c_void_p(outs[f].data_ptr()) for f in FIELDS), 0)
+    ctx.check(lib.kd_build(ctx.ptr, h, ctypes.byref(tr)))
+    got = {"m": tr.m, "root": tr.root}
+    got.update({f: outs[f].numpy()[: tr.m] for f in FIELDS})
+    assert_same_tree(got, ref)

@@ -1335,11 +1335,24 @@ kd_status select_build(kd_ctx* ctx, kd_presorted* H, kd_tree* out) {
         LaunchTimer lt(ctx, F_SELECT, (double)M, nullptr, 0.0);
         CK(launch_sel_level(key64, ids, keys, cur, k, (int32_t)M, L, stile, segs, ghist, gany, unresolved, node, 0, d_err, s,
                             0, 0, 0));
-        // rounds 0 and 1 always run; later rounds until no segment is open
+        // the leading bytes each segment shares are skipped: selection starts
+        // at the first byte where some segment's elements differ; then two
+        // rounds, then rounds until no segment is open
+        int32_t r0 = 0;
+        {
+            const int32_t init = nbytes;
+            CK(cudaMemcpyAsync(unresolved, &init, 4, cudaMemcpyHostToDevice, s));
+            CK(launch_sel_level(key64, ids, keys, cur, k, (int32_t)M, L, stile, segs, ghist, gany, unresolved, node, 0,
+                                d_err, s, 0, 0, 3));
+            ctx->launches += 2;
+            CK(cudaMemcpyAsync(&r0, unresolved, 4, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            r0 = std::max(0, std::min(r0, nbytes - 1));
+        }
         CK(launch_sel_level(key64, ids, keys, cur, k, (int32_t)M, L, stile, segs, ghist, gany, unresolved, node, 0, d_err, s,
-                            0, std::min(2, nbytes), 1));
-        ctx->launches += 2 * std::min(2, nbytes);
-        for (int r = 2; r < nbytes; ++r) {
+                            r0, std::min(r0 + 2, nbytes), 1));
+        ctx->launches += 2 * (std::min(r0 + 2, nbytes) - r0);
+        for (int r = r0 + 2; r < nbytes; ++r) {
             uint32_t open = 0;
             CK(cudaMemsetAsync(unresolved, 0, 4, s));
             CK(launch_sel_level(key64, ids, keys, cur, k, (int32_t)M, L, stile, segs, ghist, gany, unresolved, node, 0,

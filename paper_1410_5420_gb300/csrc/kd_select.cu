@@ -53,7 +53,9 @@ struct SelSeg {
     int32_t pos;      // array position of the median; -1 unresolved, -2 empty segment
     uint32_t target;  // rank of the median among the current candidates
     uint32_t cnt[2];  // partition: elements placed in the lower / upper half
-    uint32_t pad[2];
+    int32_t start;    // first byte of the super key the candidates do not all share
+    uint32_t pad;
+    KW span_and, span_or;  // AND and OR of the segment's leading key words
     KW prefix[MAXK];  // super-key words; the bytes chosen so far (high bytes first)
 };
 
@@ -73,7 +75,10 @@ __global__ void k_sel_init(int32_t m, int L, int nseg, SelSeg<KW>* __restrict__ 
         S.pos = S.hi < S.lo ? -2 : -1;
         S.target = S.hi < S.lo ? 0u : (uint32_t)((S.hi - S.lo) >> 1);
         S.cnt[0] = S.cnt[1] = 0;
-        S.pad[0] = S.pad[1] = 0;
+        S.start = 0;
+        S.pad = 0;
+        S.span_and = ~(KW)0;
+        S.span_or = 0;
         for (int j = 0; j < MAXK; ++j) S.prefix[j] = 0;
         segs[s] = S;
     }
@@ -88,6 +93,7 @@ struct SelTile {
     int ns;
     int32_t lo[LEVEL_NSMAX], hi[LEVEL_NSMAX], idx[LEVEL_NSMAX];
     int32_t pos[LEVEL_NSMAX];
+    int32_t start[LEVEL_NSMAX];
     KW prefix[LEVEL_NSMAX][MAXK];
 };
 
@@ -99,6 +105,7 @@ __device__ __forceinline__ void sel_load_tile(SelTile<KW>& T, int32_t pos0, int3
         for (int x = 0; x < T.ns; ++x) {
             const SelSeg<KW>& S = segs[T.idx[x]];
             T.pos[x] = S.pos;
+            T.start[x] = S.start;
             for (int j = 0; j < MAXK; ++j) T.prefix[x][j] = S.prefix[j];
         }
     }
@@ -120,8 +127,8 @@ __global__ void __launch_bounds__(SEL_THREADS) k_sel_hist(const __grid_constant_
     const int32_t npos = min(tile, m - pos0);
     sel_load_tile(T, pos0, npos, m, L, segs, err);
     bool open = false;
-    for (int x = 0; x < T.ns; ++x) open |= T.pos[x] == -1;
-    if (!open) return;  // uniform: every segment of the tile is resolved
+    for (int x = 0; x < T.ns; ++x) open |= T.pos[x] == -1 && r >= T.start[x];
+    if (!open) return;  // uniform: every segment of the tile is resolved, or shares byte r
     for (int i = tid; i < LEVEL_NSMAX * RADIX; i += SEL_THREADS) (&h[0][0])[i] = 0;
     __syncthreads();
     constexpr int B = sizeof(KW);
@@ -131,7 +138,7 @@ __global__ void __launch_bounds__(SEL_THREADS) k_sel_hist(const __grid_constant_
         const int o = e * SEL_THREADS + tid;
         const int32_t pos = pos0 + o;
         int sj = o < npos ? tile_slot(T.lo, T.hi, T.ns, pos) : -1;
-        bool cand = sj >= 0 && T.pos[sj] == -1;
+        bool cand = sj >= 0 && T.pos[sj] == -1 && r >= T.start[sj];
         uint32_t dig = 0;
         if (cand) {
             // the words of the super key up to word j, compared with the prefix
@@ -168,6 +175,77 @@ __global__ void __launch_bounds__(SEL_THREADS) k_sel_hist(const __grid_constant_
     }
 }
 
+// AND and OR of a 64- or 32-bit word over the lanes of `mask` (all calling).
+__device__ __forceinline__ void sel_warp_and_or(uint32_t mask, uint32_t w, uint32_t& a, uint32_t& o) {
+    a = __reduce_and_sync(mask, w);
+    o = __reduce_or_sync(mask, w);
+}
+__device__ __forceinline__ void sel_warp_and_or(uint32_t mask, uint64_t w, uint64_t& a, uint64_t& o) {
+    const uint32_t ah = __reduce_and_sync(mask, (uint32_t)(w >> 32)), al = __reduce_and_sync(mask, (uint32_t)w);
+    const uint32_t oh = __reduce_or_sync(mask, (uint32_t)(w >> 32)), ol = __reduce_or_sync(mask, (uint32_t)w);
+    a = ((uint64_t)ah << 32) | al;
+    o = ((uint64_t)oh << 32) | ol;
+}
+
+__device__ __forceinline__ void sel_atomic_and_or(uint32_t* a, uint32_t* o, uint32_t va, uint32_t vo) {
+    atomicAnd(a, va);
+    atomicOr(o, vo);
+}
+__device__ __forceinline__ void sel_atomic_and_or(uint64_t* a, uint64_t* o, uint64_t va, uint64_t vo) {
+    atomicAnd(reinterpret_cast<unsigned long long*>(a), (unsigned long long)va);
+    atomicOr(reinterpret_cast<unsigned long long*>(o), (unsigned long long)vo);
+}
+
+// Span of every segment's leading key words (x_p of super key p): the
+// bits on which AND and OR agree are shared by all of its elements.
+template <typename KW>
+__global__ void __launch_bounds__(SEL_THREADS) k_sel_span(const __grid_constant__ SelBufs<KW> bufs, int cur, int k,
+                                                          int32_t m, int L, int tile, SelSeg<KW>* __restrict__ segs,
+                                                          int* __restrict__ err) {
+    __shared__ SelTile<KW> T;
+    __shared__ KW s_and[LEVEL_NSMAX], s_or[LEVEL_NSMAX];
+    const int tid = threadIdx.x;
+    const int32_t pos0 = blockIdx.x * tile;
+    const int32_t npos = min(tile, m - pos0);
+    if (tid < LEVEL_NSMAX) {
+        s_and[tid] = ~(KW)0;
+        s_or[tid] = 0;
+    }
+    sel_load_tile(T, pos0, npos, m, L, segs, err);  // (synchronises the block)
+    const int p = L % k;
+    // warp, then block, then one global update per segment of the tile
+    for (int e = 0; e < SEL_IPT; ++e) {
+        const int o = e * SEL_THREADS + tid;
+        const int sj = o < npos ? tile_slot(T.lo, T.hi, T.ns, pos0 + o) : -1;
+        const KW w = sj >= 0 ? bufs.key[cur][p][pos0 + o] : (KW)0;
+        const uint32_t peers = __match_any_sync(0xffffffffu, (uint32_t)sj);  // lanes of one segment
+        KW a, b;
+        sel_warp_and_or(peers, w, a, b);
+        if (sj >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) sel_atomic_and_or(&s_and[sj], &s_or[sj], a, b);
+    }
+    __syncthreads();
+    if (tid < T.ns) sel_atomic_and_or(&segs[T.idx[tid]].span_and, &segs[T.idx[tid]].span_or, s_and[tid], s_or[tid]);
+}
+
+// The leading bytes every element of a segment shares become its prefix;
+// selection starts at the first byte where they differ.  *first receives
+// the smallest such byte over the level's open segments.
+template <typename KW>
+__global__ void k_sel_skip(int nseg, SelSeg<KW>* __restrict__ segs, int32_t* __restrict__ first) {
+    constexpr int B = sizeof(KW);
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nseg; s += gridDim.x * blockDim.x) {
+        SelSeg<KW>& S = segs[s];
+        if (S.pos != -1) continue;
+        const KW diff = S.span_and ^ S.span_or;
+        const int lead = diff == 0 ? 8 * B : (B == 8 ? __clzll((long long)diff) : __clz((int)(uint32_t)diff));
+        const int cb = lead / 8 < B ? lead / 8 : B - 1;  // keep at least the last byte of the word to select
+        const KW mask = cb == 0 ? (KW)0 : ~(KW)0 << (8 * (B - cb));
+        S.prefix[0] = S.span_and & mask;
+        S.start = cb;
+        atomicMin(first, cb);
+    }
+}
+
 // One warp per segment: the bin holding the median's rank becomes the next
 // prefix byte; a bin of one element resolves the segment.
 template <typename KW>
@@ -178,7 +256,7 @@ __global__ void k_sel_choose(int nseg, int r, int nbytes, SelSeg<KW>* __restrict
     const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (s >= nseg) return;
     SelSeg<KW>& S = segs[s];
-    if (S.pos != -1) return;  // uniform per warp
+    if (S.pos != -1 || r < S.start) return;  // uniform per warp (byte r is shared: already in the prefix)
     uint32_t* hs = ghist + (int64_t)s * RADIX;
     uint32_t v[8], sum = 0;
 #pragma unroll
@@ -331,6 +409,9 @@ struct SelSub {
     int32_t lo, hi, pos;
     uint32_t target;
     uint32_t cnt[2];
+    int32_t start;  // first nibble of the super key the sub-segment's elements do not all share
+    uint32_t pad;
+    KW sand, sor;   // AND and OR of its leading key words
     uint32_t hist[16];
     int32_t any[16];
     KW prefix[MAXK];
@@ -359,6 +440,7 @@ __global__ void __launch_bounds__(SEL_THREADS) k_sel_finish(const __grid_constan
                                                             uint8_t* __restrict__ dim, int64_t in_off,
                                                             int* __restrict__ err) {
     extern __shared__ __align__(16) unsigned char sf_raw[];
+    __shared__ int s_first;  // smallest first nibble to select over the sub-segments of a level
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     int32_t ulo, uhi;
     segment_bounds(m, lam, blockIdx.x, ulo, uhi);
@@ -414,12 +496,40 @@ __global__ void __launch_bounds__(SEL_THREADS) k_sel_finish(const __grid_constan
             U.pos = hi < lo ? -2 : -1;
             U.target = hi < lo ? 0u : (uint32_t)((hi - lo) >> 1);
             U.cnt[0] = U.cnt[1] = 0;
+            U.start = 0;
+            U.sand = ~(KW)0;
+            U.sor = 0;
             for (int x = 0; x < 16; ++x) U.hist[x] = 0;
             for (int j = 0; j < MAXK; ++j) U.prefix[j] = 0;
         }
+        if (tid == 0) s_first = 2 * B - 1;
+        __syncthreads();
+        // the leading nibbles every element of a sub-segment shares become
+        // its prefix; its selection starts at the first nibble where they differ
+        for (int i0 = 0; i0 < S; i0 += SEL_THREADS) {
+            const int i = i0 + tid;
+            const bool v = i < S && !(segw[i] & SF_DONE);
+            const uint32_t su = v ? subid[i] : 0xffffffffu;
+            const KW w = v ? KB(b)[p * T + i] : (KW)0;
+            const uint32_t peers = __match_any_sync(0xffffffffu, su);
+            KW a, o;
+            sel_warp_and_or(peers, w, a, o);
+            if (v && lane == __ffs(peers) - 1) sel_atomic_and_or(&sub[su].sand, &sub[su].sor, a, o);
+        }
+        __syncthreads();
+        for (int s = tid; s < nsub; s += SEL_THREADS) {
+            SelSub<KW>& U = sub[s];
+            if (U.pos != -1) continue;
+            const KW diff = U.sand ^ U.sor;
+            const int lead = diff == 0 ? 8 * B : (B == 8 ? __clzll((long long)diff) : __clz((int)(uint32_t)diff));
+            const int cn = lead / 4 < 2 * B ? lead / 4 : 2 * B - 1;
+            U.prefix[0] = cn == 0 ? (KW)0 : (U.sand & (~(KW)0 << (4 * (2 * B - cn))));
+            U.start = cn;
+            atomicMin(&s_first, cn);
+        }
         __syncthreads();
         // selection: 4-bit rounds, most significant nibble first
-        for (int r4 = 0; r4 < nnib; ++r4) {
+        for (int r4 = s_first; r4 < nnib; ++r4) {
             const int r = r4 >> 1;
             const int j = r / B;
             const int sh = 8 * (B - 1 - r % B) + ((r4 & 1) ? 0 : 4);
@@ -429,7 +539,7 @@ __global__ void __launch_bounds__(SEL_THREADS) k_sel_finish(const __grid_constan
                 const int i = i0 + tid;
                 bool cand = i < S && !(segw[i] & SF_DONE);
                 const int su = cand ? subid[i] : 0;
-                cand = cand && sub[su].pos == -1;
+                cand = cand && sub[su].pos == -1 && r4 >= sub[su].start;
                 uint32_t nib = 0;
                 if (cand) {
                     const SelSub<KW>& U = sub[su];
@@ -454,6 +564,10 @@ __global__ void __launch_bounds__(SEL_THREADS) k_sel_finish(const __grid_constan
             for (int s = tid; s < nsub; s += SEL_THREADS) {
                 SelSub<KW>& U = sub[s];
                 if (U.pos != -1) continue;
+                if (r4 < U.start) {  // this nibble is shared: already in the prefix
+                    open = true;
+                    continue;
+                }
                 uint32_t c = 0, hb = 0;
                 int bb = -1;
                 for (int x = 0; x < 16; ++x) {
@@ -653,6 +767,12 @@ static cudaError_t sel_level(const SelBufs<KW>& B, int cur, int k, int32_t m, in
         k_sel_init<KW><<<g, 256, 0, s>>>(m, L, nseg, sg, ghist);
         return cudaGetLastError();
     }
+    if (phase == 3) {
+        k_sel_span<KW><<<ntiles, SEL_THREADS, 0, s>>>(B, cur, k, m, L, tile, sg, err);
+        k_sel_skip<KW><<<std::min(152 * 8, (nseg + 255) / 256), 256, 0, s>>>(nseg, sg,
+                                                                            reinterpret_cast<int32_t*>(unresolved));
+        return cudaGetLastError();
+    }
     if (phase == 1) {
         for (int r = round_begin; r < round_end; ++r) {
             k_sel_hist<KW><<<ntiles, SEL_THREADS, 0, s>>>(B, cur, k, m, L, r, tile, sg, ghist, gany, err);
@@ -668,9 +788,11 @@ static cudaError_t sel_level(const SelBufs<KW>& B, int cur, int k, int32_t m, in
 // One level of the selection build over every segment of level L, in tiles
 // of `tile` positions (a tile must touch at most LEVEL_NSMAX segments: with
 // segments of at least T tuples, 2048 for T >= 1024 and 1024 for T = 512).
-// phase 0: reset the segments' state; 1: selection rounds [round_begin,
-// round_end) (each adds the segments still unresolved to *unresolved);
-// 2: partition around the medians.
+// phase 0: reset the segments' state; 3: the shared leading bytes of every
+// segment (*unresolved, as an int32, receives the smallest first byte to
+// select; it must hold the byte count before); 1: selection rounds
+// [round_begin, round_end) (each adds the segments still unresolved to
+// *unresolved); 2: partition around the medians.
 cudaError_t launch_sel_level(int key64, void* const* id, void* const* key, int cur, int k, int32_t m, int L, int tile,
                              void* segs, uint32_t* ghist, int32_t* gany, uint32_t* unresolved, int32_t* node,
                              int64_t in_off, int* err, cudaStream_t s, int round_begin, int round_end, int phase) {

@@ -65,10 +65,10 @@ def parse():
                     help="cpu_baseline: oracle sample size in points (2^24: about 15 s of one core)")
     ap.add_argument("--ref-sample", type=int, default=1 << 21,
                     help="--impl reference: oracle sample per step in points (about 2 s of one core)")
-    ap.add_argument("--mode", default="plain", choices=["plain", "batched", "served", "sweep", "knn"],
+    ap.add_argument("--mode", default="plain", choices=["plain", "batched", "served", "sweep", "knn", "profile"],
                     help="plain: the 2^26 build (default line, with batched and served inside); batched / "
                          "served: only those results; sweep: n=2^22 at k=2..6; knn: searches over a "
-                         "2^22-tuple tree")
+                         "2^22-tuple tree; profile: warm-up then timed plain builds only (for profilers)")
     ap.add_argument("--clouds", type=int, default=4096)
     ap.add_argument("--requests", type=int, default=20000)
     return ap.parse_args()
@@ -555,12 +555,30 @@ def run_served(args):
     print(json.dumps(line), flush=True)
 
 
+def run_profile(args):
+    """Plain device-resident builds of the mixture at --n only (default
+    parameters, no tuning, no extras): --warmup steps, then --steps steps,
+    so that a profiler's launch list holds whole steps in order."""
+    import torch
+    import kdgen
+    from paper_1410_5420_gb300 import api
+    x = torch.from_numpy(kdgen.large_gmm(n=args.n)).cuda()
+    ctx = api.kd_create(0, stream=torch.cuda.current_stream())
+    for _ in range(args.warmup + args.steps):
+        t = api.build_tree(ctx, x, children=True, on_device=True)
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "profile", "n": args.n, "m": t["m"], "steps": args.warmup + args.steps,
+                      "launches_per_step": api.kd_launch_count(ctx) / (args.warmup + args.steps)}), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.mode != "plain" and args.impl == "gb300":
         if rank == 0:
-            {"batched": run_batched, "served": run_served, "sweep": run_sweep, "knn": run_knn}[args.mode](args)
+            {"batched": run_batched, "served": run_served, "sweep": run_sweep, "knn": run_knn,
+             "profile": run_profile}[args.mode](args)
         return
     if world > 1:
         import torch.distributed as dist

@@ -321,8 +321,8 @@ int64_t kd_launch_count(kd_ctx *ctx);
  * recorded on the context's stream around every launch, summed per kernel
  * family (0 transform, 1 sort pass, 2 dedup, 3 records, 4 level pass,
  * 5 finisher, 6 top nodes, 7 other, 8 key gathers, 9 median selection and
- * partition of kd_build_select, 10 its finisher).  *ms: device time, *launches: launch
- * count, *units: elements the launches processed, *bytes: the algorithmic
+ * partition of kd_build_select, 10 its finisher, 11 ordering the runs of
+ * equal x_0 in array 0).  *ms: device time, *launches: launch count, *units: elements the launches processed, *bytes: the algorithmic
  * bytes those launches must move (reads + writes per element of each kernel,
  * summed over launches).  Any output pointer may be NULL.  Synchronises the
  * stream.

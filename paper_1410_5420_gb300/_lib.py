@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "KD_OK", -1: "KD_EINVAL", -2: "KD_ENOMEM", -3: "KD_EDEVICE", 
 
 # kernel families reported by kd_kernel_stats
 FAMILIES = ["transform", "sort_pass", "dedup", "records", "level_pass", "finish", "top_nodes", "other", "gather",
-            "select", "select_finish"]
+            "select", "select_finish", "ties"]
 
 EXPORTS = ["kd_create", "kd_presort", "kd_handle_info", "kd_handle_arrays", "kd_build", "kd_release",
            "kd_build_batch", "kd_submit", "kd_wait", "kd_serving_stats", "kd_destroy", "kd_last_error",

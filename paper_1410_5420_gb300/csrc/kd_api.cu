@@ -38,11 +38,19 @@ cudaError_t launch_pack_clouds(const PackDesc* d, int count, void* dst, cudaStre
 cudaError_t launch_gather(int key64, const int64_t* count_ptr, int64_t max_count, const void* plane,
                           const uint32_t* ids, void* out, int* err, cudaStream_t s);
 size_t dedup_scratch_words(int64_t n);
-cudaError_t launch_dedup(int key64, int64_t n, const void* key0, const uint32_t* ids, const void* tail, int k,
-                         const uint32_t* cloud_plane, int cloud_digits, uint32_t* ids_out, void* y1, void* y2,
+cudaError_t launch_dedup(int key64, int64_t n, const void* key0, const uint32_t* ids, const void* T, int64_t tstride,
+                         int k, const uint32_t* cloud_plane, int cloud_digits, uint32_t* ids_out, void* y1, void* y2,
                          void* y1_out, void* y2_out, uint32_t* scratch, int64_t* m_out, uint32_t* hist,
                          int32_t* mcloud, int* err, cudaStream_t s);
 cudaError_t launch_own_ranks(const int64_t* m_ptr, int64_t max_m, int k, const AllPlanes& rec, cudaStream_t s);
+cudaError_t launch_run_stats(int key64, const int64_t* count_ptr, int64_t max_count, const void* key0, int tk,
+                             uint2* range, uint2* cross_runs, uint32_t* run_meta, cudaStream_t s);
+size_t run_tile_count(int64_t max_count);
+cudaError_t launch_tail_gather(int key64, const int64_t* count_ptr, int64_t max_count, const uint32_t* ids,
+                               const void* tail, int tk, void* T, int64_t tstride, int* err, cudaStream_t s);
+cudaError_t launch_tie_runs(int key64, const int64_t* count_ptr, int64_t max_count, const void* key0, uint32_t* ids,
+                            void* T, int64_t tstride, int tk, const uint2* range, const uint2* cross_runs,
+                            const uint32_t* run_meta, int* err, cudaStream_t s);
 cudaError_t launch_perm_bases(const int64_t* m_ptr, int shift, uint32_t* bases, cudaStream_t s);
 cudaError_t launch_perm_scatter(const int64_t* m_ptr, int64_t max_m, const uint32_t* dest, const PayloadArgs& pa,
                                 cudaStream_t s);
@@ -81,10 +89,16 @@ using namespace kd;
 
 namespace {
 
+// Array 0 by x_0 alone, then its runs of equal x_0 ordered on chip by
+// compares, unless the runs of more than 32 tuples would cost more than this
+// many compares per tuple (sum of their L^2 over n); then by the whole key.
+constexpr uint64_t RUN_COST_PER_TUPLE = 128;
+
 enum Family {
     F_TRANSFORM = 0, F_SORT, F_DEDUP, F_RECORDS, F_LEVEL, F_FINISH, F_TOP, F_OTHER, F_GATHER,
     F_SELECT,         // median-selection build: selection rounds and partitions of the levels
     F_SELECT_FINISH,  // median-selection build: on-chip finisher
+    F_TIES,           // array 0: runs of equal x_0 ordered by the other coordinates
     F_COUNT
 };
 
@@ -612,57 +626,106 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
     auto plane64 = [&](int plane) { return plane >= 0 ? key64 : 0; };
 
     // S_0: ids by super key 0 (all n tuples) ----------------------------
-    // With 32-bit keys, the passes of plane k-1 carry plane k-2 along as a
-    // second payload, so that plane k-2's first pass reads its keys in order
-    // instead of gathering them at random (a gather reads a few 32-byte
-    // sectors per 4-byte key; the carry adds 8 streamed bytes per pass).
-    const int carry_plane = (k >= 2 && !key64) ? k - 2 : -1;
-    int cy = 0;                       // carried plane: current ping-pong buffer
-    const uint32_t* carried = nullptr;  // plane k-2 in the current order, once carried
+    // Array 0 is sorted by x_0 alone, and each run of equal x_0 is then
+    // ordered by the remaining coordinates on chip (launch_tie_runs).  Only
+    // if a run is too long for that does array 0 take the sort by the whole
+    // super key, least significant coordinate first.  With 32-bit keys, the
+    // passes of plane k-1 carry plane k-2 along as a second payload, so that
+    // plane k-2's first pass reads its keys in order instead of gathering
+    // them at random (a gather reads a few 32-byte sectors per 4-byte key;
+    // the carry adds 8 streamed bytes per pass).
     int kc = 0, ic = 0;  // current key / id buffer
-    for (size_t i = 0; i < s0.size(); ++i) {
-        const Pass& P = s0[i];
-        const bool last = i + 1 == s0.size();
-        const bool carry = carry_plane >= 0 && P.plane == k - 1;
-        const bool from_carry = carry_plane >= 0 && P.plane == carry_plane && P.mode == KEY_GATHER;
-        const bool next_gathers = !last && s0[i + 1].mode != KEY_BUF;
-        PayloadArgs pay{};
-        pay.n = 1;
-        pay.src[0] = P.mode == KEY_DIRECT ? nullptr : ibuf[ic];
-        pay.dst[0] = ibuf[ic ^ 1];
-        if (carry) {
-            pay.n = 2;
-            pay.src[1] = P.mode == KEY_DIRECT ? (const uint32_t*)plane_ptr(carry_plane) : pbuf[cy][0];
-            pay.dst[1] = pbuf[cy ^ 1][0];
+    auto sort_array0 = [&](const std::vector<Pass>& list, bool whole_key) -> kd_status {
+        const int carry_plane = (whole_key && k >= 2 && !key64) ? k - 2 : -1;
+        int cy = 0;                         // carried plane: current ping-pong buffer
+        const uint32_t* carried = nullptr;  // plane k-2 in the current order, once carried
+        kc = 0;
+        ic = 0;
+        for (size_t i = 0; i < list.size(); ++i) {
+            const Pass& P = list[i];
+            const bool last = i + 1 == list.size();
+            const bool carry = carry_plane >= 0 && P.plane == k - 1;
+            const bool from_carry = carry_plane >= 0 && P.plane == carry_plane && P.mode == KEY_GATHER;
+            const bool next_gathers = !last && list[i + 1].mode != KEY_BUF;
+            PayloadArgs pay{};
+            pay.n = 1;
+            pay.src[0] = P.mode == KEY_DIRECT ? nullptr : ibuf[ic];
+            pay.dst[0] = ibuf[ic ^ 1];
+            if (carry) {
+                pay.n = 2;
+                pay.src[1] = P.mode == KEY_DIRECT ? (const uint32_t*)plane_ptr(carry_plane) : pbuf[cy][0];
+                pay.dst[1] = pbuf[cy ^ 1][0];
+            }
+            const void* ksrc = P.mode == KEY_BUF ? (const void*)kbuf[kc] : plane_ptr(P.plane);
+            void* kdst = next_gathers ? nullptr : (void*)kbuf[kc ^ 1];
+            if (from_carry) {
+                if (!carried) return fail(ctx, KD_EINVAL, "internal: carried plane missing");
+                ksrc = carried;
+            } else if (P.mode == KEY_GATHER) {  // gather the new plane's keys into order first
+                LaunchTimer lg(ctx, F_GATHER, (double)N, nullptr, 4.0 + 2.0 * P.w);
+                CK(launch_gather(plane64(P.plane), d_n, N, plane_ptr(P.plane), ibuf[ic], kbuf[kc], d_err, s));
+                ksrc = kbuf[kc];
+            }
+            const bool inject = ctx->inject_timeout && i == 0;
+            {
+                LaunchTimer lt(ctx, F_SORT, (double)N, nullptr, pass_bytes(P, kdst != nullptr, pay.n));
+                ctx->launches += 2;  // count and scan kernels of the pass
+                CK(launch_sort_pass(plane64(P.plane), d_n, N, ksrc, kdst, pay,
+                                    bases_all + (size_t)row_of(P.plane, P.digit) * RADIX, 8 * P.digit, status, d_err, s,
+                                    ctx->spin_limit, inject ? 1 : 0));
+            }
+            if (inject) {  // the injected wait: report it before anything else runs
+                ctx->inject_timeout = false;
+                CKS(check_device_err(ctx, d_err));
+            }
+            kc ^= 1;
+            ic ^= 1;
+            if (carry) {
+                cy ^= 1;
+                carried = pbuf[cy][0];
+            }
         }
-        const void* ksrc = P.mode == KEY_BUF ? (const void*)kbuf[kc] : plane_ptr(P.plane);
-        void* kdst = next_gathers ? nullptr : (void*)kbuf[kc ^ 1];
-        if (from_carry) {
-            if (!carried) return fail(ctx, KD_EINVAL, "internal: carried plane missing");
-            ksrc = carried;
-        } else if (P.mode == KEY_GATHER) {  // gather the new plane's keys into order first
-            LaunchTimer lg(ctx, F_GATHER, (double)N, nullptr, 4.0 + 2.0 * P.w);
-            CK(launch_gather(plane64(P.plane), d_n, N, plane_ptr(P.plane), ibuf[ic], kbuf[kc], d_err, s));
-            ksrc = kbuf[kc];
-        }
-        const bool inject = ctx->inject_timeout && i == 0;
+        return KD_OK;
+    };
+    std::vector<Pass> s0_x0;
+    plane_passes(s0_x0, 0, D, true);
+    const bool by_runs = k >= 2 && N >= 2;
+    bool whole_key = !by_runs;
+    CKS(sort_array0(by_runs ? s0_x0 : s0, whole_key));
+    uint32_t* run_meta = nullptr;
+    uint2 *run_range = nullptr, *cross_runs = nullptr;
+    if (by_runs) {
+        CKS(S.get(&run_meta, 4 * sizeof(uint32_t)));
+        CKS(S.get(&run_range, run_tile_count(N) * sizeof(uint2)));
+        CKS(S.get(&cross_runs, run_tile_count(N) * sizeof(uint2)));
         {
-            LaunchTimer lt(ctx, F_SORT, (double)N, nullptr, pass_bytes(P, kdst != nullptr, pay.n));
-            ctx->launches += 2;  // count and scan kernels of the pass
-            CK(launch_sort_pass(plane64(P.plane), d_n, N, ksrc, kdst, pay,
-                                bases_all + (size_t)row_of(P.plane, P.digit) * RADIX, 8 * P.digit, status, d_err, s,
-                                ctx->spin_limit, inject ? 1 : 0));
+            LaunchTimer lt(ctx, F_TIES, (double)N, nullptr, (double)w);
+            CK(launch_run_stats(key64, d_n, N, kbuf[kc], k - 1, run_range, cross_runs, run_meta, s));
         }
-        if (inject) {  // the injected wait: report it before anything else runs
-            ctx->inject_timeout = false;
-            CKS(check_device_err(ctx, d_err));
+        uint32_t meta[4] = {0, 0, 0, 0};
+        CK(cudaMemcpyAsync(meta, run_meta, sizeof(meta), cudaMemcpyDeviceToHost, s));
+        CKS(check_device_err(ctx, d_err));  // synchronises
+        // ordering the runs by compares costs sum(L^2) over the long ones;
+        // above RUN_COST_PER_TUPLE per tuple the whole-key sort is cheaper
+        const uint64_t cost = (uint64_t)meta[0] | ((uint64_t)meta[1] << 32);
+        if (meta[2] || cost > (uint64_t)RUN_COST_PER_TUPLE * (uint64_t)N) {
+            whole_key = true;
+            CKS(sort_array0(s0, true));
         }
-        kc ^= 1;
-        ic ^= 1;
-        if (carry) {
-            cy ^= 1;
-            carried = pbuf[cy][0];
-        }
+    }
+    // x_1..x_{k-1} of every position of array 0, so that run ordering and
+    // duplicate removal stream
+    unsigned char* tplanes = nullptr;
+    if (k >= 2) {
+        CKS(S.get(&tplanes, (size_t)(k - 1) * NS * w + 16));
+        LaunchTimer lg(ctx, F_GATHER, (double)N, nullptr, 4.0 + 2.0 * (k - 1) * w);
+        CK(launch_tail_gather(key64, d_n, N, ibuf[ic], tail, k - 1, tplanes, NS, d_err, s));
+    }
+    if (!whole_key) {
+        LaunchTimer lt(ctx, F_TIES, (double)N, nullptr, 2.0 * (4.0 + (k - 1) * w) + w);
+        ctx->launches += 1;  // tiles, crossing runs
+        CK(launch_tie_runs(key64, d_n, N, kbuf[kc], ibuf[ic], tplanes, NS, k - 1, run_range, cross_runs, run_meta,
+                           d_err, s));
     }
     // dedup ---------------------------------------------------------------
     uint32_t* dedup_out = count == 1 ? H->perm0 : ibuf[ic ^ 1];
@@ -681,7 +744,7 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
     {
         LaunchTimer lt(ctx, F_DEDUP, (double)N, nullptr, 2.0 * w + 8 + (k - 1) * w);
         ctx->launches += 2;  // flags, tile scan, compaction
-        CK(launch_dedup(key64, N, kbuf[kc], ibuf[ic], tail, k, cloud_plane, cloud_digits, dedup_out, y1tmp, y2tmp,
+        CK(launch_dedup(key64, N, kbuf[kc], ibuf[ic], tplanes, NS, k, cloud_plane, cloud_digits, dedup_out, y1tmp, y2tmp,
                         y_first ? (void*)kbuf[kc] : nullptr, y2c, status + status_words, H->d_m, hist, mcloud,
                         d_err, s));
     }

@@ -552,14 +552,14 @@ constexpr int DEDUP_TILE = 4096;
 
 // Duplicate flags over array 0 (sorted by super key 0, equal tuples in index
 // order): a tuple equal to its predecessor goes.  The keys x_1..x_{k-1} of
-// each tuple come from its tail record (one random access per element; the
-// predecessor's record is the neighbour lane's).  The kept tuples' counts
-// leave the digit histograms, and y1 / y2 (if not NULL) receive x_{k-1} and
-// x_{k-2} in array-0 order for the first two sorts of the chain.
+// position i are T[d * tstride + i], in array-0 order (the predecessor's
+// are the neighbour lane's).  The kept tuples' counts leave the digit
+// histograms, and y1 / y2 (if not NULL) receive x_{k-1} and x_{k-2} in
+// array-0 order for the first two sorts of the chain.
 template <typename KW>
 __global__ void __launch_bounds__(256) k_dedup_flags(int64_t n, const KW* __restrict__ key0,
-                                                     const uint32_t* __restrict__ ids, const KW* __restrict__ tail,
-                                                     int k, const uint32_t* __restrict__ cloud_plane,
+                                                     const uint32_t* __restrict__ ids, const KW* __restrict__ T,
+                                                     int64_t tstride, int k, const uint32_t* __restrict__ cloud_plane,
                                                      int cloud_digits, KW* __restrict__ y1, KW* __restrict__ y2,
                                                      uint32_t* __restrict__ keepbits, uint32_t* __restrict__ tile_cnt,
                                                      uint32_t* __restrict__ hist, int32_t* __restrict__ mcloud,
@@ -589,7 +589,7 @@ __global__ void __launch_bounds__(256) k_dedup_flags(int64_t n, const KW* __rest
             lastk0 = key0[p0 - 1];
 #pragma unroll
             for (int d = 0; d < TM; ++d)
-                if (d < tk) last[d] = tail[(int64_t)lastid * tk + d];
+                if (d < tk) last[d] = T[d * tstride + p0 - 1];
         }
     }
     uint32_t wcount = 0;
@@ -605,7 +605,7 @@ __global__ void __launch_bounds__(256) k_dedup_flags(int64_t n, const KW* __rest
         const KW k0 = valid ? key0[pos] : (KW)0;
         KW r[TM];
 #pragma unroll
-        for (int d = 0; d < TM; ++d) r[d] = (valid && d < tk) ? tail[(int64_t)id * tk + d] : (KW)0;
+        for (int d = 0; d < TM; ++d) r[d] = (valid && d < tk) ? T[d * tstride + pos] : (KW)0;
         KW pk0 = __shfl_up_sync(0xffffffffu, k0, 1);
         uint32_t pid = __shfl_up_sync(0xffffffffu, id, 1);
         bool same = true;
@@ -713,6 +713,369 @@ __global__ void __launch_bounds__(256) k_dedup_compact(int64_t n, const uint32_t
             if (y2_out) y2_out[o] = y2[pos];
         }
         out += __popc(ball[j]);
+    }
+}
+
+// ------------------------------------------------------------- tie runs
+// Array 0 in super-key-0 order from a sort by x_0 alone.  A stable sort of
+// the ids (index order) by x_0 leaves every run of equal x_0 in index
+// order; super key 0 orders such a run by x_1, ..., x_{k-1}, and equal
+// tuples keep index order (Section 2.1: the super key definition, and the
+// duplicates paragraph, which keeps one of the equal tuples).
+//   k_run_stats    one warp per tile of RT_TILE positions: the runs'
+//                  lengths L (whether one exceeds rmax, and the sum of L^2
+//                  over runs of L > RT_WARP, the work of ordering them by
+//                  compares: the caller sorts array 0 by the whole super key
+//                  instead when either is too large), and the tile's range
+//                  of whole runs for k_run_tiles: from its first run start
+//                  to the next tile's, less a run of more than RT_EXT
+//                  positions at its end, which is listed instead;
+//   k_tail_gather  T[d][i] = x_{d+1} of the tuple at position i (its tail
+//                  record, read once per position), so that everything
+//                  after it streams;
+//   k_run_tiles    one block per tile range (at most RT_CAP positions),
+//                  staged in shared memory: each position of a run goes to
+//                  run start + the number of run members whose (x_1, ...,
+//                  x_{k-1}, index) is smaller (no two are equal);
+//   k_run_cross    one block per listed run, the same ranking over up to
+//                  rmax positions.
+constexpr int RT_TILE = 2048;
+constexpr int RT_EXT = 512;
+constexpr int RT_CAP = RT_TILE + RT_EXT;  // positions a tile range holds at most
+constexpr int RT_WARP = 32;
+constexpr int RUN_BLOCK = 4096;
+
+// Shared memory of k_run_tiles (x_0, tk tail words and the id per staged
+// position) and of k_run_cross (tk tail words and the id).
+static size_t run_tile_smem(int key64, int tk) { return (size_t)RT_CAP * ((size_t)(tk + 1) * (key64 ? 8 : 4) + 4); }
+static size_t run_cross_smem(int key64, int tk, int rmax) { return (size_t)rmax * ((size_t)tk * (key64 ? 8 : 4) + 4); }
+// Longest run k_run_cross orders: RUN_BLOCK, halved while its stage would
+// exceed 160 KB (64-bit keys with many dimensions).
+int run_block_max(int key64, int tk) {
+    int r = RUN_BLOCK;
+    while (r > RT_TILE && run_cross_smem(key64, tk, r) > (size_t)160 * 1024) r >>= 1;
+    return r;
+}
+
+// Last position of the run of key0[i] = v holding position i, searched up
+// to i + limit (key0 is sorted): galloping, then bisection.
+template <typename KW>
+__device__ __forceinline__ int64_t run_last(const KW* __restrict__ key0, int64_t n, int64_t i, KW v, int64_t limit) {
+    const int64_t cap = n - 1 < i + limit ? n - 1 : i + limit;
+    int64_t lo = i, step = 1;
+    while (lo + step <= cap && key0[lo + step] == v) {
+        lo += step;
+        step <<= 1;
+    }
+    int64_t hi = lo + step - 1 < cap ? lo + step - 1 : cap;  // key0[lo] == v; key0[hi + 1] != v or hi == cap
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (key0[mid] == v) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// run_meta: [0..1] sum of L^2 over runs of more than RT_WARP positions
+// (64-bit), [2] a run exceeds rmax positions, [3] runs listed for
+// k_run_cross.  range[t] = (first, end) positions of tile t's whole runs.
+// A run's length is the distance from its first position to the next
+// run's, both in the tile, or found by galloping for the run open at the
+// tile's end (the tile holding a run's first position accounts for it).
+template <typename KW>
+__global__ void __launch_bounds__(256) k_run_stats(const int64_t* __restrict__ count_ptr, const KW* __restrict__ key0,
+                                                   int rmax, uint2* __restrict__ range, uint2* __restrict__ cross_runs,
+                                                   uint32_t* __restrict__ run_meta) {
+    __shared__ unsigned long long s_cost[8];
+    const int64_t n = *count_ptr;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t lt = lanemask_lt();
+    unsigned long long cost = 0;
+    bool lng = false;
+#define RUN_ACCOUNT(L_)                                                 \
+    do {                                                                \
+        const int64_t l_ = (L_);                                        \
+        if (l_ > rmax) lng = true;                                      \
+        else if (l_ > RT_WARP) cost += (unsigned long long)(l_ * l_);   \
+    } while (0)
+    const int64_t ntiles = (n + RT_TILE - 1) / RT_TILE;
+    for (int64_t t = (int64_t)blockIdx.x * 8 + warp; t < ntiles; t += (int64_t)gridDim.x * 8) {
+        const int64_t c0 = t * RT_TILE;
+        int64_t open = -1;   // first position of the run still open, if it began in this tile
+        int64_t first = -1;  // the tile's first run start
+#pragma unroll 8
+        for (int r = 0; r < RT_TILE / 32; ++r) {
+            const int64_t e = c0 + r * 32 + lane;
+            const bool valid = e < n;
+            const KW v = valid ? key0[e] : (KW)0;
+            KW pv = __shfl_up_sync(0xffffffffu, v, 1);
+            if (lane == 0 && valid && e > 0) pv = key0[e - 1];
+            const bool head = valid && (e == 0 || pv != v);
+            const uint32_t hb = __ballot_sync(0xffffffffu, head);
+            const uint32_t below = hb & lt;
+            const int64_t prev = below ? c0 + r * 32 + 31 - __clz(below) : open;
+            if (head && prev >= 0) RUN_ACCOUNT(e - prev);
+            if (hb) {
+                if (first < 0) first = c0 + r * 32 + __ffs(hb) - 1;
+                open = c0 + r * 32 + 31 - __clz(hb);
+            }
+        }
+        if (lane == 0) {
+            // the run holding the tile's last position ends at `last`
+            const int64_t tl = c0 + RT_TILE - 1 < n - 1 ? c0 + RT_TILE - 1 : n - 1;
+            const int64_t last = run_last<KW>(key0, n, tl, key0[tl], rmax);
+            const int64_t next = last + 1;  // the next tile's first run start (or n)
+            int64_t end = next;
+            if (open >= 0) {
+                const int64_t L = last - open + 1;
+                RUN_ACCOUNT(L);
+                if (last > tl && L > RT_EXT) {  // a long run leaving the tile: listed
+                    end = open;
+                    if (L <= rmax) {
+                        const uint32_t slot = atomicAdd(&run_meta[3], 1u);
+                        cross_runs[slot] = make_uint2((uint32_t)open, (uint32_t)L);
+                    }
+                }
+            }
+            if (first < 0) first = next;  // the tile lies inside one run
+            range[t] = make_uint2((uint32_t)first, (uint32_t)(end > first ? end : first));
+        }
+    }
+#undef RUN_ACCOUNT
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) cost += __shfl_xor_sync(0xffffffffu, cost, o);
+    if (lane == 0) s_cost[warp] = cost;
+    lng = __syncthreads_or(lng);
+    if (tid == 0) {
+        unsigned long long c = 0;
+        for (int w = 0; w < 8; ++w) c += s_cost[w];
+        if (c) atomicAdd(reinterpret_cast<unsigned long long*>(run_meta), c);
+        if (lng) atomicOr(&run_meta[2], 1u);
+    }
+}
+
+constexpr int TG_ITEMS = 8;  // positions per thread of k_tail_gather
+template <typename KW>
+__global__ void __launch_bounds__(256) k_tail_gather(const int64_t* __restrict__ count_ptr,
+                                                     const uint32_t* __restrict__ ids, const KW* __restrict__ tail,
+                                                     int tk, int64_t id_limit, KW* __restrict__ T, int64_t tstride,
+                                                     int* __restrict__ err) {
+    constexpr int TM = MAXK - 1;
+    const int64_t n = *count_ptr;
+    const int64_t base = (int64_t)blockIdx.x * 256 * TG_ITEMS + threadIdx.x;
+    if (base >= n) return;
+    uint32_t id[TG_ITEMS];
+#pragma unroll
+    for (int e = 0; e < TG_ITEMS; ++e) {
+        const int64_t i = base + (int64_t)e * 256;
+        id[e] = i < n ? ids[i] : 0u;
+        if (i < n && (int64_t)id[e] >= id_limit) {
+            atomicOr(err, ERR_INTERNAL);
+            id[e] = 0;
+        }
+    }
+    if (tk * sizeof(KW) == 8) {  // one 8-byte record (two 32-bit words or one 64-bit word)
+        uint2 v[TG_ITEMS];
+        const uint2* rec = reinterpret_cast<const uint2*>(tail);
+#pragma unroll
+        for (int e = 0; e < TG_ITEMS; ++e) v[e] = base + (int64_t)e * 256 < n ? rec[id[e]] : make_uint2(0u, 0u);
+#pragma unroll
+        for (int e = 0; e < TG_ITEMS; ++e) {
+            const int64_t i = base + (int64_t)e * 256;
+            if (i < n) {
+                if (sizeof(KW) == 8) {
+                    T[i] = (KW)(((uint64_t)v[e].y << 32) | v[e].x);
+                } else {
+                    T[i] = (KW)v[e].x;
+                    T[tstride + i] = (KW)v[e].y;
+                }
+            }
+        }
+        return;
+    }
+#pragma unroll
+    for (int d = 0; d < TM; ++d) {
+        if (d >= tk) break;
+        KW v[TG_ITEMS];
+#pragma unroll
+        for (int e = 0; e < TG_ITEMS; ++e) v[e] = base + (int64_t)e * 256 < n ? tail[(int64_t)id[e] * tk + d] : (KW)0;
+#pragma unroll
+        for (int e = 0; e < TG_ITEMS; ++e) {
+            const int64_t i = base + (int64_t)e * 256;
+            if (i < n) T[d * tstride + i] = v[e];
+        }
+    }
+}
+
+// Number of positions j in [s, f] of a staged run whose (tail words, id)
+// precede those of position i (tail word d of j at st[d * stride + j]).
+// TK > 0: that many tail words, known at compile time; 0: tk of them.
+template <typename KW, int TK>
+__device__ __forceinline__ uint32_t run_rank(const KW* __restrict__ st, int stride, const uint32_t* __restrict__ sid,
+                                             int tk, int s, int f, int i) {
+    constexpr int TM = TK > 0 ? TK : MAXK - 1;
+    const int nk = TK > 0 ? TK : tk;
+    KW a[TM];
+#pragma unroll
+    for (int d = 0; d < TM; ++d) a[d] = d < nk ? st[d * stride + i] : (KW)0;
+    const uint32_t ia = sid[i];
+    uint32_t r = 0;
+    for (int j = s; j <= f; ++j) {
+        bool less = false, eq = true;
+#pragma unroll
+        for (int d = 0; d < TM; ++d) {
+            if (d < nk) {
+                const KW b = st[d * stride + j];
+                less = less || (eq && b < a[d]);
+                eq = eq && b == a[d];
+            }
+        }
+        r += (less || (eq && sid[j] < ia)) ? 1u : 0u;
+    }
+    return r;
+}
+
+// First / last position of the staged run holding position e (sk sorted
+// over [0, cnt)).
+template <typename KW>
+__device__ __forceinline__ int staged_first(const KW* __restrict__ sk, int e) {
+    const KW v = sk[e];
+    int lo = 0, hi = e;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (sk[mid] < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+template <typename KW>
+__device__ __forceinline__ int staged_last(const KW* __restrict__ sk, int cnt, int e) {
+    const KW v = sk[e];
+    int lo = e, hi = cnt - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (sk[mid] > v) hi = mid - 1; else lo = mid;
+    }
+    return lo;
+}
+
+// A tile range holds whole runs.  Bounds: warp w takes staged positions
+// [w * RT_CAP / 8, ...) as rows of 32; a run's first and last positions
+// come from ballots of the "differs from the previous / next position"
+// flags, carried from row to row (and found by bisection once per warp for
+// a run entering or leaving its span).  Ranking: row R goes to warp R mod
+// 8, so that a long run is shared by all warps.
+template <typename KW, int TK>
+__global__ void __launch_bounds__(256) k_run_tiles(const int64_t* __restrict__ count_ptr, const KW* __restrict__ key0,
+                                                   const uint2* __restrict__ range, uint32_t* __restrict__ ids,
+                                                   KW* __restrict__ T, int64_t tstride, int tk,
+                                                   int* __restrict__ err) {
+    constexpr int ROWS = RT_CAP / 256;  // rows per warp
+    constexpr int SPAN = ROWS * 32;     // positions per warp for the bounds
+    extern __shared__ __align__(16) unsigned char rt_smem[];
+    KW* sk = reinterpret_cast<KW*>(rt_smem);                                 // [RT_CAP] x_0, then packed bounds
+    KW* st = sk + RT_CAP;                                                    // [tk][RT_CAP]
+    uint32_t* sid = reinterpret_cast<uint32_t*>(st + (size_t)tk * RT_CAP);  // [RT_CAP]
+    uint32_t* sb = reinterpret_cast<uint32_t*>(sk);                          // [RT_CAP] first | last << 16
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t lt = lanemask_lt();
+    const uint32_t le = lt | (1u << lane), ge = ~lt;
+    const int wb = warp * SPAN;
+    const int64_t n = *count_ptr;
+    const int64_t ntiles = (n + RT_TILE - 1) / RT_TILE;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const uint2 R = range[t];
+        const int64_t base = R.x;
+        const int64_t span = (int64_t)R.y - (int64_t)R.x;
+        int cnt = (int)span;
+        if (span < 0 || span > RT_CAP || (int64_t)R.y > n) {
+            if (tid == 0) atomicOr(err, ERR_INTERNAL);
+            cnt = 0;
+        }
+        if (cnt <= 1) continue;  // (uniform over the block)
+        for (int e = tid; e < cnt; e += 256) {
+            sk[e] = key0[base + e];
+            sid[e] = ids[base + e];
+            for (int d = 0; d < tk; ++d) st[d * RT_CAP + e] = T[d * tstride + base + e];
+        }
+        __syncthreads();
+        int fs[ROWS], ls[ROWS];
+        {
+            int carry = wb;  // first position of the run holding the warp's first position
+            if (wb > 0 && wb < cnt && sk[wb - 1] == sk[wb]) carry = staged_first<KW>(sk, wb);
+#pragma unroll
+            for (int r = 0; r < ROWS; ++r) {
+                const int e = wb + r * 32 + lane;
+                const bool head = e >= cnt || e == 0 || sk[e - 1] != sk[e];
+                const uint32_t hb = __ballot_sync(0xffffffffu, head);
+                const uint32_t m = hb & le;
+                fs[r] = m ? wb + r * 32 + 31 - __clz(m) : carry;
+                if (hb) carry = wb + r * 32 + 31 - __clz(hb);
+            }
+        }
+        {
+            const int wl = wb + SPAN - 1 < cnt - 1 ? wb + SPAN - 1 : cnt - 1;  // the warp's last position
+            int carry = wl;  // last position of the run holding it
+            if (wl >= wb && wl + 1 < cnt && sk[wl + 1] == sk[wl]) carry = staged_last<KW>(sk, cnt, wl);
+#pragma unroll
+            for (int r = ROWS - 1; r >= 0; --r) {
+                const int e = wb + r * 32 + lane;
+                const bool tail = e >= cnt - 1 || sk[e + 1] != sk[e];
+                const uint32_t tb = __ballot_sync(0xffffffffu, tail);
+                const uint32_t m = tb & ge;
+                ls[r] = m ? wb + r * 32 + __ffs(m) - 1 : carry;
+                if (tb) carry = wb + r * 32 + __ffs(tb) - 1;
+            }
+        }
+        __syncthreads();  // every read of x_0 is done: the bounds replace it
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r) {
+            const int e = wb + r * 32 + lane;
+            if (e < cnt) sb[e] = (uint32_t)fs[r] | ((uint32_t)ls[r] << 16);
+        }
+        __syncthreads();
+        // every global read of the staged positions precedes the barriers
+        // above, so each position is written as soon as it is ranked
+#pragma unroll 1
+        for (int q = 0; q < ROWS; ++q) {
+            const int e = (q * 8 + warp) * 32 + lane;
+            if (e >= cnt) continue;
+            const uint32_t bnd = sb[e];
+            const int f0 = (int)(bnd & 0xffffu), f1 = (int)(bnd >> 16);
+            if (f1 == f0) continue;
+            const int o = f0 + (int)run_rank<KW, TK>(st, RT_CAP, sid, tk, f0, f1, e);
+            if (o != e) {
+                ids[base + o] = sid[e];
+                for (int d = 0; d < tk; ++d) T[d * tstride + base + o] = st[d * RT_CAP + e];
+            }
+        }
+        __syncthreads();  // the stage is reused by the next tile
+    }
+}
+
+template <typename KW>
+__global__ void __launch_bounds__(256) k_run_cross(const uint32_t* __restrict__ run_meta,
+                                                   const uint2* __restrict__ runs, int64_t max_count,
+                                                   uint32_t* __restrict__ ids, KW* __restrict__ T, int64_t tstride,
+                                                   int tk, int rmax) {
+    extern __shared__ __align__(16) unsigned char rc_smem[];
+    KW* st = reinterpret_cast<KW*>(rc_smem);                              // [tk][rmax]
+    uint32_t* sid = reinterpret_cast<uint32_t*>(st + (size_t)tk * rmax);  // [rmax]
+    const int tid = threadIdx.x;
+    const uint32_t nr = run_meta[3];
+    for (uint32_t r = blockIdx.x; r < nr; r += gridDim.x) {
+        const uint2 R = runs[r];
+        const int L = R.y <= (uint32_t)rmax && (int64_t)R.x + R.y <= max_count ? (int)R.y : 0;
+        for (int i = tid; i < L; i += 256) {
+            sid[i] = ids[R.x + i];
+            for (int d = 0; d < tk; ++d) st[d * rmax + i] = T[d * tstride + R.x + i];
+        }
+        __syncthreads();
+        // every read of the run precedes the barrier: positions are written as ranked
+        for (int i = tid; i < L; i += 256) {
+            const uint32_t o = run_rank<KW, 0>(st, rmax, sid, tk, 0, L - 1, i);
+            ids[R.x + o] = sid[i];
+            for (int d = 0; d < tk; ++d) T[d * tstride + R.x + o] = st[d * rmax + i];
+        }
+        __syncthreads();  // the stage is reused by the next run
     }
 }
 
@@ -932,6 +1295,18 @@ cudaError_t init_presort_kernels() {
     set((const void*)k_transform<int32_t, uint32_t>, TRANSFORM_SMEM_MAX);
     set((const void*)k_transform<int64_t, uint64_t>, TRANSFORM_SMEM_MAX);
     set((const void*)k_transform<float, uint32_t>, TRANSFORM_SMEM_MAX);
+    set((const void*)k_run_tiles<uint32_t, 0>, run_tile_smem(0, MAXK - 1));
+    set((const void*)k_run_tiles<uint32_t, 1>, run_tile_smem(0, 1));
+    set((const void*)k_run_tiles<uint32_t, 2>, run_tile_smem(0, 2));
+    set((const void*)k_run_tiles<uint32_t, 3>, run_tile_smem(0, 3));
+    set((const void*)k_run_tiles<uint64_t, 0>, run_tile_smem(1, MAXK - 1));
+    set((const void*)k_run_tiles<uint64_t, 1>, run_tile_smem(1, 1));
+    set((const void*)k_run_tiles<uint64_t, 2>, run_tile_smem(1, 2));
+    for (int key64 = 0; key64 < 2; ++key64) {
+        size_t most = 0;  // the largest stage over every tuple width
+        for (int tk = 1; tk < MAXK; ++tk) most = std::max(most, run_cross_smem(key64, tk, run_block_max(key64, tk)));
+        set(key64 ? (const void*)k_run_cross<uint64_t> : (const void*)k_run_cross<uint32_t>, most);
+    }
     int dev = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g_rs_sms, cudaDevAttrMultiProcessorCount, dev);
@@ -968,8 +1343,8 @@ size_t dedup_scratch_words(int64_t n) {
     return (size_t)((n + 31) / 32) + 2 * (size_t)tiles + 4;
 }
 
-cudaError_t launch_dedup(int key64, int64_t n, const void* key0, const uint32_t* ids, const void* tail, int k,
-                         const uint32_t* cloud_plane, int cloud_digits, uint32_t* ids_out, void* y1, void* y2,
+cudaError_t launch_dedup(int key64, int64_t n, const void* key0, const uint32_t* ids, const void* T, int64_t tstride,
+                         int k, const uint32_t* cloud_plane, int cloud_digits, uint32_t* ids_out, void* y1, void* y2,
                          void* y1_out, void* y2_out, uint32_t* scratch, int64_t* m_out, uint32_t* hist,
                          int32_t* mcloud, int* err, cudaStream_t s) {
     const int64_t tiles = (n + DEDUP_TILE - 1) / DEDUP_TILE;
@@ -978,7 +1353,8 @@ cudaError_t launch_dedup(int key64, int64_t n, const void* key0, const uint32_t*
     uint32_t* tcnt = keepbits + (n + 31) / 32;
     uint32_t* toff = tcnt + tiles;
 #define KD_DEDUP(KW)                                                                                          \
-    k_dedup_flags<KW><<<(unsigned)tiles, 256, 0, s>>>(n, (const KW*)key0, ids, (const KW*)tail, k, cloud_plane, \
+    k_dedup_flags<KW><<<(unsigned)tiles, 256, 0, s>>>(n, (const KW*)key0, ids, (const KW*)T, tstride, k,        \
+                                                      cloud_plane,                                            \
                                                       cloud_digits, (KW*)y1, (KW*)y2, keepbits, tcnt, hist,   \
                                                       mcloud, err);                                           \
     k_tile_scan<<<1, 1024, 0, s>>>(tiles, tcnt, toff, m_out);                                                 \
@@ -990,6 +1366,76 @@ cudaError_t launch_dedup(int key64, int64_t n, const void* key0, const uint32_t*
         KD_DEDUP(uint32_t)
     }
 #undef KD_DEDUP
+    return cudaGetLastError();
+}
+
+// Run statistics of array 0 after its sort by x_0 alone, and the tile
+// ranges and long crossing runs for launch_tie_runs (run_meta 4 words,
+// cleared here; range ntiles entries, cross_runs ntiles entries, ntiles =
+// ceil(max_count / RT_TILE); see k_run_stats).
+cudaError_t launch_run_stats(int key64, const int64_t* count_ptr, int64_t max_count, const void* key0, int tk,
+                             uint2* range, uint2* cross_runs, uint32_t* run_meta, cudaStream_t s) {
+    const int rmax = run_block_max(key64, tk);
+    cudaError_t e = cudaMemsetAsync(run_meta, 0, 4 * sizeof(uint32_t), s);
+    if (e != cudaSuccess || max_count < 2) return e;
+    const int grid = grid_for((max_count + RT_TILE - 1) / RT_TILE, 8, 152 * 8);
+    if (key64)
+        k_run_stats<uint64_t><<<grid, 256, 0, s>>>(count_ptr, (const uint64_t*)key0, rmax, range, cross_runs,
+                                                   run_meta);
+    else
+        k_run_stats<uint32_t><<<grid, 256, 0, s>>>(count_ptr, (const uint32_t*)key0, rmax, range, cross_runs,
+                                                   run_meta);
+    return cudaGetLastError();
+}
+
+size_t run_tile_count(int64_t max_count) { return (size_t)((max_count + RT_TILE - 1) / RT_TILE); }
+
+// T[d][i] (plane stride tstride words) = tail word d of the tuple ids[i].
+cudaError_t launch_tail_gather(int key64, const int64_t* count_ptr, int64_t max_count, const uint32_t* ids,
+                               const void* tail, int tk, void* T, int64_t tstride, int* err, cudaStream_t s) {
+    if (max_count == 0 || tk < 1) return cudaSuccess;
+    const int64_t blocks = (max_count + 256 * TG_ITEMS - 1) / (256 * TG_ITEMS);
+    if (key64)
+        k_tail_gather<uint64_t><<<(unsigned)blocks, 256, 0, s>>>(count_ptr, ids, (const uint64_t*)tail, tk, max_count,
+                                                                 (uint64_t*)T, tstride, err);
+    else
+        k_tail_gather<uint32_t><<<(unsigned)blocks, 256, 0, s>>>(count_ptr, ids, (const uint32_t*)tail, tk, max_count,
+                                                                 (uint32_t*)T, tstride, err);
+    return cudaGetLastError();
+}
+
+template <typename KW, int TK>
+static void run_tiles_as(int grid, size_t smem, const int64_t* count_ptr, const void* key0, const uint2* range,
+                         uint32_t* ids, void* T, int64_t tstride, int tk, int* err, cudaStream_t s) {
+    k_run_tiles<KW, TK><<<grid, 256, smem, s>>>(count_ptr, (const KW*)key0, range, ids, (KW*)T, tstride, tk, err);
+}
+
+// Orders every run of equal x_0 (ids and the T planes, in place) by the
+// tail words and then the id: the tile ranges and listed runs of
+// launch_run_stats, which must have found no run above run_block_max
+// positions.
+cudaError_t launch_tie_runs(int key64, const int64_t* count_ptr, int64_t max_count, const void* key0, uint32_t* ids,
+                            void* T, int64_t tstride, int tk, const uint2* range, const uint2* cross_runs,
+                            const uint32_t* run_meta, int* err, cudaStream_t s) {
+    if (max_count < 2 || tk < 1) return cudaSuccess;
+    const int rmax = run_block_max(key64, tk);
+    const int tgrid = grid_for((max_count + RT_TILE - 1) / RT_TILE, 1, 152 * 8);
+    const int cgrid = grid_for(max_count / RT_TILE + 1, 1, 152 * 4);
+    const size_t tsm = run_tile_smem(key64, tk);
+    if (key64) {
+        if (tk == 1) run_tiles_as<uint64_t, 1>(tgrid, tsm, count_ptr, key0, range, ids, T, tstride, tk, err, s);
+        else if (tk == 2) run_tiles_as<uint64_t, 2>(tgrid, tsm, count_ptr, key0, range, ids, T, tstride, tk, err, s);
+        else run_tiles_as<uint64_t, 0>(tgrid, tsm, count_ptr, key0, range, ids, T, tstride, tk, err, s);
+        k_run_cross<uint64_t><<<cgrid, 256, run_cross_smem(1, tk, rmax), s>>>(run_meta, cross_runs, max_count, ids,
+                                                                              (uint64_t*)T, tstride, tk, rmax);
+    } else {
+        if (tk == 1) run_tiles_as<uint32_t, 1>(tgrid, tsm, count_ptr, key0, range, ids, T, tstride, tk, err, s);
+        else if (tk == 2) run_tiles_as<uint32_t, 2>(tgrid, tsm, count_ptr, key0, range, ids, T, tstride, tk, err, s);
+        else if (tk == 3) run_tiles_as<uint32_t, 3>(tgrid, tsm, count_ptr, key0, range, ids, T, tstride, tk, err, s);
+        else run_tiles_as<uint32_t, 0>(tgrid, tsm, count_ptr, key0, range, ids, T, tstride, tk, err, s);
+        k_run_cross<uint32_t><<<cgrid, 256, run_cross_smem(0, tk, rmax), s>>>(run_meta, cross_runs, max_count, ids,
+                                                                              (uint32_t*)T, tstride, tk, rmax);
+    }
     return cudaGetLastError();
 }
 

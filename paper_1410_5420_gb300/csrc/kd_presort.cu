@@ -745,9 +745,13 @@ constexpr int RT_CAP = RT_TILE + RT_EXT;  // positions a tile range holds at mos
 constexpr int RT_WARP = 32;
 constexpr int RUN_BLOCK = 4096;
 
-// Shared memory of k_run_tiles (x_0, tk tail words and the id per staged
-// position) and of k_run_cross (tk tail words and the id).
-static size_t run_tile_smem(int key64, int tk) { return (size_t)RT_CAP * ((size_t)(tk + 1) * (key64 ? 8 : 4) + 4); }
+// Shared memory of k_run_tiles (x_0, tk tail words or a packed 64-bit key,
+// and the id per staged position) and of k_run_cross (tk tail words and
+// the id).
+static size_t run_tile_smem(int key64, int tk) {
+    const size_t w = key64 ? 8 : 4;
+    return (size_t)RT_CAP * (w + std::max<size_t>((size_t)tk * w, 8) + 4);
+}
 static size_t run_cross_smem(int key64, int tk, int rmax) { return (size_t)rmax * ((size_t)tk * (key64 ? 8 : 4) + 4); }
 // Longest run k_run_cross orders: RUN_BLOCK, halved while its stage would
 // exceed 160 KB (64-bit keys with many dimensions).
@@ -957,6 +961,15 @@ __device__ __forceinline__ int staged_last(const KW* __restrict__ sk, int cnt, i
     return lo;
 }
 
+// Packed rank keys, one 64-bit word per staged position, for the common
+// widths: 1 = x_1 << 32 | id (32-bit keys, k = 2: the id completes the
+// key), 2 = x_1 << 32 | x_2 (32-bit keys, k = 3), 3 = x_1 (64-bit keys,
+// k = 2); ties of forms 2 and 3 go to the id.  0: tail words as staged.
+template <typename KW, int TK>
+__host__ __device__ constexpr int packed_form() {
+    return (sizeof(KW) == 4 && TK == 1) ? 1 : (sizeof(KW) == 4 && TK == 2) ? 2 : (sizeof(KW) == 8 && TK == 1) ? 3 : 0;
+}
+
 // A tile range holds whole runs.  Bounds: warp w takes staged positions
 // [w * RT_CAP / 8, ...) as rows of 32; a run's first and last positions
 // come from ballots of the "differs from the previous / next position"
@@ -970,11 +983,14 @@ __global__ void __launch_bounds__(256) k_run_tiles(const int64_t* __restrict__ c
                                                    int* __restrict__ err) {
     constexpr int ROWS = RT_CAP / 256;  // rows per warp
     constexpr int SPAN = ROWS * 32;     // positions per warp for the bounds
+    constexpr int PF = packed_form<KW, TK>();
     extern __shared__ __align__(16) unsigned char rt_smem[];
-    KW* sk = reinterpret_cast<KW*>(rt_smem);                                 // [RT_CAP] x_0, then packed bounds
-    KW* st = sk + RT_CAP;                                                    // [tk][RT_CAP]
-    uint32_t* sid = reinterpret_cast<uint32_t*>(st + (size_t)tk * RT_CAP);  // [RT_CAP]
-    uint32_t* sb = reinterpret_cast<uint32_t*>(sk);                          // [RT_CAP] first | last << 16
+    KW* sk = reinterpret_cast<KW*>(rt_smem);                                // [RT_CAP] x_0, then packed bounds
+    uint64_t* pk = reinterpret_cast<uint64_t*>(sk + RT_CAP);                // [RT_CAP] packed keys (PF > 0)
+    KW* st = sk + RT_CAP;                                                   // [tk][RT_CAP] tail words (PF == 0)
+    uint32_t* sid = PF ? reinterpret_cast<uint32_t*>(pk + RT_CAP)          // [RT_CAP]
+                       : reinterpret_cast<uint32_t*>(st + (size_t)tk * RT_CAP);
+    uint32_t* sb = reinterpret_cast<uint32_t*>(sk);                         // [RT_CAP] first | last << 16
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t lt = lanemask_lt();
     const uint32_t le = lt | (1u << lane), ge = ~lt;
@@ -992,9 +1008,21 @@ __global__ void __launch_bounds__(256) k_run_tiles(const int64_t* __restrict__ c
         }
         if (cnt <= 1) continue;  // (uniform over the block)
         for (int e = tid; e < cnt; e += 256) {
-            sk[e] = key0[base + e];
-            sid[e] = ids[base + e];
-            for (int d = 0; d < tk; ++d) st[d * RT_CAP + e] = T[d * tstride + base + e];
+            const int64_t g = base + e;
+            sk[e] = key0[g];
+            const uint32_t id = ids[g];
+            if constexpr (PF == 1) {
+                pk[e] = ((uint64_t)(uint32_t)T[g] << 32) | id;
+            } else if constexpr (PF == 2) {
+                pk[e] = ((uint64_t)(uint32_t)T[g] << 32) | (uint32_t)T[tstride + g];
+                sid[e] = id;
+            } else if constexpr (PF == 3) {
+                pk[e] = (uint64_t)T[g];
+                sid[e] = id;
+            } else {
+                sid[e] = id;
+                for (int d = 0; d < tk; ++d) st[d * RT_CAP + e] = T[d * tstride + g];
+            }
         }
         __syncthreads();
         int fs[ROWS], ls[ROWS];
@@ -1041,10 +1069,41 @@ __global__ void __launch_bounds__(256) k_run_tiles(const int64_t* __restrict__ c
             const uint32_t bnd = sb[e];
             const int f0 = (int)(bnd & 0xffffu), f1 = (int)(bnd >> 16);
             if (f1 == f0) continue;
-            const int o = f0 + (int)run_rank<KW, TK>(st, RT_CAP, sid, tk, f0, f1, e);
-            if (o != e) {
-                ids[base + o] = sid[e];
-                for (int d = 0; d < tk; ++d) T[d * tstride + base + o] = st[d * RT_CAP + e];
+            if constexpr (PF == 1) {
+                const uint64_t a = pk[e];
+                uint32_t r = 0;
+#pragma unroll 4
+                for (int j = f0; j <= f1; ++j) r += pk[j] < a ? 1u : 0u;
+                const int64_t o = base + f0 + r;
+                if (o != base + e) {
+                    ids[o] = (uint32_t)a;
+                    T[o] = (KW)(uint32_t)(a >> 32);
+                }
+            } else if constexpr (PF == 2 || PF == 3) {
+                const uint64_t a = pk[e];
+                const uint32_t ia = sid[e];
+                uint32_t r = 0;
+#pragma unroll 4
+                for (int j = f0; j <= f1; ++j) {
+                    const uint64_t b = pk[j];
+                    r += (b < a || (b == a && sid[j] < ia)) ? 1u : 0u;
+                }
+                const int64_t o = base + f0 + r;
+                if (o != base + e) {
+                    ids[o] = ia;
+                    if constexpr (PF == 2) {
+                        T[o] = (KW)(uint32_t)(a >> 32);
+                        T[tstride + o] = (KW)(uint32_t)a;
+                    } else {
+                        T[o] = (KW)a;
+                    }
+                }
+            } else {
+                const int o = f0 + (int)run_rank<KW, TK>(st, RT_CAP, sid, tk, f0, f1, e);
+                if (o != e) {
+                    ids[base + o] = sid[e];
+                    for (int d = 0; d < tk; ++d) T[d * tstride + base + o] = st[d * RT_CAP + e];
+                }
             }
         }
         __syncthreads();  // the stage is reused by the next tile

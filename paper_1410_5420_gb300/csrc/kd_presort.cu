@@ -1082,11 +1082,15 @@ __global__ void __launch_bounds__(256) k_run_tiles(const int64_t* __restrict__ c
             } else if constexpr (PF == 2 || PF == 3) {
                 const uint64_t a = pk[e];
                 const uint32_t ia = sid[e];
-                uint32_t r = 0;
+                uint32_t r = 0, eq = 0;
 #pragma unroll 4
                 for (int j = f0; j <= f1; ++j) {
                     const uint64_t b = pk[j];
-                    r += (b < a || (b == a && sid[j] < ia)) ? 1u : 0u;
+                    r += b < a ? 1u : 0u;
+                    eq += b == a ? 1u : 0u;
+                }
+                if (eq > 1) {  // equal tuples (besides itself): index order among them
+                    for (int j = f0; j <= f1; ++j) r += (pk[j] == a && sid[j] < ia) ? 1u : 0u;
                 }
                 const int64_t o = base + f0 + r;
                 if (o != base + e) {

@@ -863,27 +863,21 @@ __device__ __forceinline__ void fin_load_unit(const AllBufs& bufs, const CloudDe
 // so that one kernel's registers are not sized for every k.
 __host__ __device__ constexpr int fin_kmax(int smax) { return smax >= 4096 ? 3 : (smax >= 2048 ? 4 : 8); }
 
-template <int K, int SMAX>
-__device__ __forceinline__ void fin_load_dispatch(const AllBufs& bufs, const CloudDev& C, int64_t g, int S,
-                                                  uint32_t* rk, uint16_t* arr, int* bad) {
-    if constexpr (K <= fin_kmax(SMAX))
-        fin_load_unit<K, SMAX>(bufs, C, g, S, rk, arr, bad);
-    else
-        *bad = 1;
-}
-
 // Blocks per SM the finisher is compiled for: at 1024 tuples five blocks
 // fit the shared memory, and trading registers for them (a few spills)
 // hides more of the shared-memory latency.
 __host__ __device__ constexpr int fin_min_blocks(int smax) { return smax >= 4096 ? 2 : (smax <= 1024 ? 5 : 3); }
 
-template <int SMAX>
+// K: the number of dimensions, so that the unit's per-dimension arrays and
+// loops are sized exactly.
+template <int SMAX, int K>
 __global__ void __launch_bounds__(FIN_THREADS, fin_min_blocks(SMAX))
-    k_finish(const __grid_constant__ AllBufs bufs, int k, const int64_t* __restrict__ unit_prefix, int ncloud,
+    k_finish(const __grid_constant__ AllBufs bufs, const int64_t* __restrict__ unit_prefix, int ncloud,
              int64_t unit_base, const CloudDev* __restrict__ clouds, const uint32_t* __restrict__ perm0,
              int* __restrict__ err, unsigned long long* __restrict__ phase_ns) {
     constexpr int GMAX = SMAX / FIN_THREADS;
     constexpr int smax = SMAX;
+    constexpr int k = K;
     extern __shared__ __align__(16) uint32_t sm[];
     __shared__ uint32_t s_wc[FIN_WARPS][fin_labels(SMAX)];
     __shared__ int2 s_lab[fin_labels(SMAX)];
@@ -917,16 +911,7 @@ __global__ void __launch_bounds__(FIN_THREADS, fin_min_blocks(SMAX))
     // sorted by rank 0) and the rank-0 plane of arrays 1..k-1; every load is
     // issued before any is used.  Then each element of array d finds its lid
     // (its position in array 0) by a branch-free binary search of its rank 0.
-    switch (k) {
-        case 2: fin_load_dispatch<2, SMAX>(bufs, C, g, S, rk, arr, &bad); break;
-        case 3: fin_load_dispatch<3, SMAX>(bufs, C, g, S, rk, arr, &bad); break;
-        case 4: fin_load_dispatch<4, SMAX>(bufs, C, g, S, rk, arr, &bad); break;
-        case 5: fin_load_dispatch<5, SMAX>(bufs, C, g, S, rk, arr, &bad); break;
-        case 6: fin_load_dispatch<6, SMAX>(bufs, C, g, S, rk, arr, &bad); break;
-        case 7: fin_load_dispatch<7, SMAX>(bufs, C, g, S, rk, arr, &bad); break;
-        case 8: fin_load_dispatch<8, SMAX>(bufs, C, g, S, rk, arr, &bad); break;
-        default: bad = 1;
-    }
+    fin_load_unit<K, SMAX>(bufs, C, g, S, rk, arr, &bad);
     for (int i = tid; i < S; i += FIN_THREADS) {
         arr[i] = (uint16_t)i;  // array 0 is the rank table's own order
         lab[i] = 0;
@@ -1023,9 +1008,9 @@ __global__ void __launch_bounds__(FIN_THREADS, fin_min_blocks(SMAX))
         uint32_t* scr = seg + a0;  // n words, owned by this warp for this segment
         if (in) lane_of[lid] = (uint8_t)lane;
         __syncwarp();
-        uint32_t less[MAXK];
+        uint32_t less[K];
 #pragma unroll
-        for (int q = 0; q < MAXK; ++q) {
+        for (int q = 0; q < K; ++q) {
             less[q] = 0;
             if (q < k) {
                 if (q == p0) {
@@ -1055,11 +1040,11 @@ __global__ void __launch_bounds__(FIN_THREADS, fin_min_blocks(SMAX))
         uint32_t sub = __ballot_sync(0xffffffffu, in);
         bool active = in;
         int32_t mlo = a0, mhi = b0;
-        for (int l = dl; __any_sync(0xffffffffu, active); ++l) {
-            const int p = (C.lam + l) % k;
+        int p = p0;  // the dimension of level l
+        for (int l = dl; __any_sync(0xffffffffu, active); ++l, p = p + 1 == K ? 0 : p + 1) {
             uint32_t lp = 0;
 #pragma unroll
-            for (int q = 0; q < MAXK; ++q)
+            for (int q = 0; q < K; ++q)
                 if (q == p) lp = less[q];
             const int rank = __popc(lp & sub);
             const int32_t c = mlo + ((mhi - mlo) >> 1);
@@ -1294,13 +1279,47 @@ cudaError_t init_build_kernels() {
     auto set = [&](const void* f, size_t bytes) {
         if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     };
-    set((const void*)k_finish<1024>, finish_smem(fin_kmax(1024), 1024));
-    set((const void*)k_finish<2048>, finish_smem(fin_kmax(2048), 2048));
-    set((const void*)k_finish<4096>, finish_smem(fin_kmax(4096), 4096));
+    set((const void*)k_finish<1024, 2>, finish_smem(2, 1024));
+    set((const void*)k_finish<1024, 3>, finish_smem(3, 1024));
+    set((const void*)k_finish<1024, 4>, finish_smem(4, 1024));
+    set((const void*)k_finish<1024, 5>, finish_smem(5, 1024));
+    set((const void*)k_finish<1024, 6>, finish_smem(6, 1024));
+    set((const void*)k_finish<1024, 7>, finish_smem(7, 1024));
+    set((const void*)k_finish<1024, 8>, finish_smem(8, 1024));
+    set((const void*)k_finish<2048, 2>, finish_smem(2, 2048));
+    set((const void*)k_finish<2048, 3>, finish_smem(3, 2048));
+    set((const void*)k_finish<2048, 4>, finish_smem(4, 2048));
+    set((const void*)k_finish<4096, 2>, finish_smem(2, 4096));
+    set((const void*)k_finish<4096, 3>, finish_smem(3, 4096));
     return e;
 }
 
 // Finisher over units [unit_base, unit_base + nunits).
+template <int SMAX, int K>
+static void finish_as(const AllBufs& bufs, const int64_t* unit_prefix, int ncloud, int64_t unit_base, int nunits,
+                      const CloudDev* clouds, const uint32_t* perm0, size_t smem, int* err,
+                      unsigned long long* phase_ns, cudaStream_t s) {
+    if constexpr (K <= fin_kmax(SMAX))
+        k_finish<SMAX, K><<<nunits, FIN_THREADS, smem, s>>>(bufs, unit_prefix, ncloud, unit_base, clouds, perm0, err,
+                                                           phase_ns);
+}
+
+template <int SMAX>
+static cudaError_t finish_for(int k, const AllBufs& bufs, const int64_t* unit_prefix, int ncloud, int64_t unit_base,
+                              int nunits, const CloudDev* clouds, const uint32_t* perm0, size_t smem, int* err,
+                              unsigned long long* phase_ns, cudaStream_t s) {
+#define KD_FIN(K)                                                                                              \
+    case K:                                                                                                    \
+        finish_as<SMAX, K>(bufs, unit_prefix, ncloud, unit_base, nunits, clouds, perm0, smem, err, phase_ns, s); \
+        break;
+    switch (k) {
+        KD_FIN(2) KD_FIN(3) KD_FIN(4) KD_FIN(5) KD_FIN(6) KD_FIN(7) KD_FIN(8)
+        default: return cudaErrorInvalidValue;
+    }
+#undef KD_FIN
+    return cudaGetLastError();
+}
+
 cudaError_t launch_finish(const AllBufs& bufs, int k, const int64_t* unit_prefix, int ncloud, int64_t unit_base,
                           int nunits, const CloudDev* clouds, const uint32_t* perm0, int smax, int* err,
                           unsigned long long* phase_ns, cudaStream_t s) {
@@ -1308,17 +1327,12 @@ cudaError_t launch_finish(const AllBufs& bufs, int k, const int64_t* unit_prefix
     if (k > fin_kmax(smax)) return cudaErrorInvalidValue;
     const size_t smem = finish_smem(k, smax);
     if (smax == 2048)
-        k_finish<2048><<<nunits, FIN_THREADS, smem, s>>>(bufs, k, unit_prefix, ncloud, unit_base, clouds, perm0, err,
-                                                         phase_ns);
-    else if (smax == 1024)
-        k_finish<1024><<<nunits, FIN_THREADS, smem, s>>>(bufs, k, unit_prefix, ncloud, unit_base, clouds, perm0, err,
-                                                         phase_ns);
-    else if (smax == 4096)
-        k_finish<4096><<<nunits, FIN_THREADS, smem, s>>>(bufs, k, unit_prefix, ncloud, unit_base, clouds, perm0, err,
-                                                         phase_ns);
-    else
-        return cudaErrorInvalidValue;
-    return cudaGetLastError();
+        return finish_for<2048>(k, bufs, unit_prefix, ncloud, unit_base, nunits, clouds, perm0, smem, err, phase_ns, s);
+    if (smax == 1024)
+        return finish_for<1024>(k, bufs, unit_prefix, ncloud, unit_base, nunits, clouds, perm0, smem, err, phase_ns, s);
+    if (smax == 4096)
+        return finish_for<4096>(k, bufs, unit_prefix, ncloud, unit_base, nunits, clouds, perm0, smem, err, phase_ns, s);
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_top_nodes(const CloudDev* clouds, const int64_t* prefix, int ncloud, int64_t total, int k,

@@ -863,15 +863,19 @@ __device__ __forceinline__ void fin_load_unit(const AllBufs& bufs, const CloudDe
 // so that one kernel's registers are not sized for every k.
 __host__ __device__ constexpr int fin_kmax(int smax) { return smax >= 4096 ? 3 : (smax >= 2048 ? 4 : 8); }
 
-// Blocks per SM the finisher is compiled for: at 1024 tuples five blocks
-// fit the shared memory, and trading registers for them (a few spills)
-// hides more of the shared-memory latency.
-__host__ __device__ constexpr int fin_min_blocks(int smax) { return smax >= 4096 ? 2 : (smax <= 1024 ? 5 : 3); }
+// Blocks per SM the finisher is compiled for: at 1024 tuples and k <= 4
+// six blocks fit the shared memory, and trading registers for them (a few
+// spills) hides more of the shared-memory latency (3.20 ms per 2^26 step at
+// k = 3, against 3.33 at five blocks and 3.58 at seven); wider tuples fit
+// fewer.
+__host__ __device__ constexpr int fin_min_blocks(int smax, int k) {
+    return smax >= 4096 ? 2 : (smax >= 2048 ? 3 : (k <= 4 ? 6 : (k <= 6 ? 5 : 4)));
+}
 
 // K: the number of dimensions, so that the unit's per-dimension arrays and
 // loops are sized exactly.
 template <int SMAX, int K>
-__global__ void __launch_bounds__(FIN_THREADS, fin_min_blocks(SMAX))
+__global__ void __launch_bounds__(FIN_THREADS, fin_min_blocks(SMAX, K))
     k_finish(const __grid_constant__ AllBufs bufs, const int64_t* __restrict__ unit_prefix, int ncloud,
              int64_t unit_base, const CloudDev* __restrict__ clouds, const uint32_t* __restrict__ perm0,
              int* __restrict__ err, unsigned long long* __restrict__ phase_ns) {

@@ -838,25 +838,30 @@ __device__ __forceinline__ void fin_load_unit(const AllBufs& bufs, const CloudDe
         }
     __syncthreads();
 #pragma unroll
-    for (int d = 1; d < K; ++d) {
-        int pos[PPT];
+    // the K-1 arrays' searches advance together: (K-1) x PPT independent chains
+    int pos[K - 1][PPT];
 #pragma unroll
-        for (int j = 0; j < PPT; ++j) pos[j] = 0;
+    for (int d = 0; d < K - 1; ++d)
 #pragma unroll
-        for (int step = SMAX / 2; step >= 1; step >>= 1) {
+        for (int j = 0; j < PPT; ++j) pos[d][j] = 0;
+#pragma unroll
+    for (int step = SMAX / 2; step >= 1; step >>= 1) {
+#pragma unroll
+        for (int d = 0; d < K - 1; ++d)
 #pragma unroll
             for (int j = 0; j < PPT; ++j)
-                if (pos[j] + step <= S && rk[pos[j] + step - 1] < v[K - 1 + d][j]) pos[j] += step;
-        }
+                if (pos[d][j] + step <= S && rk[pos[d][j] + step - 1] < v[K + d][j]) pos[d][j] += step;
+    }
+#pragma unroll
+    for (int d = 1; d < K; ++d)
 #pragma unroll
         for (int j = 0; j < PPT; ++j) {
             const int i = tid + j * FIN_THREADS;
             if (i < S) {
-                if (pos[j] >= S || rk[pos[j]] != v[K - 1 + d][j]) *bad = 1;
-                arr[d * SMAX + i] = (uint16_t)min(pos[j], S - 1);
+                if (pos[d - 1][j] >= S || rk[pos[d - 1][j]] != v[K - 1 + d][j]) *bad = 1;
+                arr[d * SMAX + i] = (uint16_t)min(pos[d - 1][j], S - 1);
             }
         }
-    }
 }
 
 // Largest k each on-chip subtree size serves (the host clamps accordingly),
@@ -934,6 +939,22 @@ __global__ void __launch_bounds__(FIN_THREADS, fin_min_blocks(SMAX, K))
     int dl = 0;
     for (; (S >> dl) > 32; ++dl) {
         const int p = (C.lam + dl) % k;
+        if (dl == 0) {
+            // the unit is one segment: a tuple's rank is its position in array p
+            const uint16_t* A = arr + p * smax;
+            const int32_t off = (S - 1) >> 1;
+            for (int i = tid; i < S; i += FIN_THREADS) {
+                const uint16_t lid = A[i];
+                if (i == off) {
+                    fin_emit(C, nodelid, lo, 0, S - 1, off, lid, p);
+                    lab[lid] = LAB_DONE;
+                } else {
+                    lab[lid] = (uint8_t)(i > off ? 1 : 0);
+                }
+            }
+            __syncthreads();
+            continue;
+        }
         uint32_t lid[GMAX], dig[GMAX], rank[GMAX];
         fin_label_rank<SMAX>(arr + p * smax, S, dl, lab, s_wc, s_lab, lid, dig, rank, &bad);
         const uint32_t marker = 1u << dl;

@@ -476,25 +476,73 @@ __global__ void __launch_bounds__(RS_BLOCK, (rs_min_blocks<KW, TILE, SP>()))
                 }
             }
         }
-        for (int p = 0; p < pay.n; ++p) {
-            consumer_sync<RS_THREADS>();  // earlier readers of the sorted tile are done
-            const uint32_t* src = pay.src[p];
+        if constexpr (sizeof(KW) == 8) {
+            // payload planes two at a time through the sorted tile (8-byte
+            // words); staged planes come from registers, the others from global
+            // memory in source order
+            uint2* sbp = reinterpret_cast<uint2*>(sb32);
+            for (int p = 0; p < pay.n; p += 2) {
+                const bool two = p + 1 < pay.n;
+                consumer_sync<RS_THREADS>();  // earlier readers of the sorted tile are done
 #pragma unroll
-            for (int j = 0; j < IPT; ++j) {
-                const int o = wbase + j * 32 + lane;
-                if (dig[j] < RADIX) {
-                    uint32_t val = src ? src[M.base + o] : (uint32_t)(M.base + o);
+                for (int j = 0; j < IPT; ++j) {
+                    const int o = wbase + j * 32 + lane;
+                    if (dig[j] < RADIX) {
+                        uint32_t a = 0, b = 0;
+                        if (p < SP) {
 #pragma unroll
-                    for (int q = 0; q < SP; ++q)
-                        if (q == p) val = preg[q][j];
-                    sb32[slot[j]] = val;
+                            for (int q = 0; q < SP; ++q)
+                                if (q == p) a = preg[q][j];
+                        } else {
+                            a = pay.src[p] ? pay.src[p][M.base + o] : (uint32_t)(M.base + o);
+                        }
+                        if (two) {
+                            if (p + 1 < SP) {
+#pragma unroll
+                                for (int q = 0; q < SP; ++q)
+                                    if (q == p + 1) b = preg[q][j];
+                            } else {
+                                b = pay.src[p + 1] ? pay.src[p + 1][M.base + o] : (uint32_t)(M.base + o);
+                            }
+                        }
+                        sbp[slot[j]] = make_uint2(a, b);
+                    }
+                }
+                consumer_sync<RS_THREADS>();
+                uint32_t* dst0 = pay.dst[p];
+                uint32_t* dst1 = two ? pay.dst[p + 1] : nullptr;
+#pragma unroll
+                for (int r = 0; r < IPT; ++r) {
+                    if (dest[r] != 0xffffffffu) {
+                        const uint2 v = sbp[r * RS_THREADS + tid];
+                        dst0[dest[r]] = v.x;
+                        if (two) dst1[dest[r]] = v.y;
+                    }
                 }
             }
-            consumer_sync<RS_THREADS>();
-            uint32_t* dst = pay.dst[p];
+        } else {
+            // one plane at a time (these kernels also hold the one- and
+            // two-payload forms above, whose registers this keeps)
+            for (int p = 0; p < pay.n; ++p) {
+                consumer_sync<RS_THREADS>();  // earlier readers of the sorted tile are done
+                const uint32_t* src = pay.src[p];
 #pragma unroll
-            for (int r = 0; r < IPT; ++r)
-                if (dest[r] != 0xffffffffu) dst[dest[r]] = sb32[r * RS_THREADS + tid];
+                for (int j = 0; j < IPT; ++j) {
+                    const int o = wbase + j * 32 + lane;
+                    if (dig[j] < RADIX) {
+                        uint32_t val = src ? src[M.base + o] : (uint32_t)(M.base + o);
+#pragma unroll
+                        for (int q = 0; q < SP; ++q)
+                            if (q == p) val = preg[q][j];
+                        sb32[slot[j]] = val;
+                    }
+                }
+                consumer_sync<RS_THREADS>();
+                uint32_t* dst = pay.dst[p];
+#pragma unroll
+                for (int r = 0; r < IPT; ++r)
+                    if (dest[r] != 0xffffffffu) dst[dest[r]] = sb32[r * RS_THREADS + tid];
+            }
         }
         // every read of this stage (and of the sorted tile over it) is behind the barriers above
         if (INPLACE) fence_proxy_async_smem();

@@ -530,10 +530,14 @@ __global__ void __launch_bounds__(RS_BLOCK, (rs_min_blocks<KW, TILE, SP>()))
                 for (int j = 0; j < IPT; ++j) {
                     const int o = wbase + j * 32 + lane;
                     if (dig[j] < RADIX) {
-                        uint32_t val = src ? src[M.base + o] : (uint32_t)(M.base + o);
+                        uint32_t val = 0;
+                        if (p < SP) {  // staged: already in registers
 #pragma unroll
-                        for (int q = 0; q < SP; ++q)
-                            if (q == p) val = preg[q][j];
+                            for (int q = 0; q < SP; ++q)
+                                if (q == p) val = preg[q][j];
+                        } else {
+                            val = src ? src[M.base + o] : (uint32_t)(M.base + o);
+                        }
                         sb32[slot[j]] = val;
                     }
                 }

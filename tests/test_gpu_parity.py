@@ -172,6 +172,20 @@ def test_batch_equals_single_builds(cuda_lib, ctx):
         assert_same_tree(got, oracle.build_tree(c))
 
 
+def test_batch_packed_equals_list(cuda_lib, ctx):
+    """Clouds stored back to back in one tensor give the same trees as the
+    same clouds passed one tensor each."""
+    import torch
+    clouds = kdgen.batch_clouds(count=60, seed=46, lo_log2=2.0, hi_log2=13.0)
+    packed = torch.from_numpy(np.concatenate(clouds)).cuda()
+    a = cuda_lib.kd_build_batch_packed(ctx, packed, [c.shape[0] for c in clouds])
+    b = cuda_lib.kd_build_batch(ctx, [torch.from_numpy(c).cuda() for c in clouds])
+    for i, c in enumerate(clouds):
+        for f in FIELDS:
+            np.testing.assert_array_equal(to_np(a[i][f]), to_np(b[i][f]), err_msg=f)
+        assert_same_tree(a[i], oracle.build_tree(c))
+
+
 def test_batch_host_buffers_int64(cuda_lib, ctx):
     clouds = [kdgen.cloud_int_uniform(n, 4, 10, 50 + n, np.int64, dup_frac=0.03) for n in (1, 5000, 300, 9000)]
     outs = cuda_lib.kd_build_batch(ctx, clouds)

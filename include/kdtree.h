@@ -117,7 +117,10 @@ kd_status kd_create(kd_ctx **out, const kd_config *cfg);
  * duplicate tuples.  *out receives a handle owning the device arrays
  * (the k index orders and their rank vectors); pass it to kd_build or
  * release it with kd_release.  Errors: KD_EINVAL, KD_ENAN, KD_ENOMEM,
- * KD_EDEVICE, KD_ETIMEOUT.  Synchronises the stream once to learn m.
+ * KD_EDEVICE, KD_ETIMEOUT.  Synchronises the stream three times: to read
+ * the key-byte histograms (constant digits are skipped), the run lengths of
+ * array 0 after its sort by x_0 (k >= 2: long or costly runs take the
+ * whole-key sort), and m.
  */
 kd_status kd_presort(kd_ctx *ctx, const kd_cloud *cloud, kd_handle *out);
 

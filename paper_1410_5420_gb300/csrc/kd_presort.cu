@@ -247,10 +247,11 @@ constexpr size_t rs_move_smem() {
 }
 
 // Resident blocks the move kernel is compiled for: as many as its shared
-// memory allows (32-bit keys: 4 with one staged payload, 3 with two).
+// memory allows (32-bit keys: 4 with one staged payload, 3 with two, 2
+// with three).
 template <typename KW, int TILE, int SP>
 constexpr int rs_min_blocks() {
-    return rs_inplace<KW>() ? (SP == 1 ? 4 : 3) : 2;
+    return rs_inplace<KW>() ? (SP == 1 ? 4 : (SP == 2 ? 3 : 2)) : 2;
 }
 
 template <typename KW, int TILE, int SP>
@@ -263,7 +264,8 @@ __global__ void __launch_bounds__(RS_BLOCK, (rs_min_blocks<KW, TILE, SP>()))
     constexpr int SW = RADIX + TILE * KWW + SP * TILE;  // stage words: offsets row | keys | payloads
     constexpr bool INPLACE = rs_inplace<KW>();
     constexpr bool PAIR = sizeof(KW) == 4 && SP == 1;    // key and payload sorted together
-    constexpr bool TRIPLE = sizeof(KW) == 4 && SP >= 2;  // key and two payloads: an 8-byte and a 4-byte word
+    constexpr bool TRIPLE = sizeof(KW) == 4 && SP == 2;  // key and two payloads: an 8-byte and a 4-byte word
+    constexpr bool QUAD = sizeof(KW) == 4 && SP == 3;    // key and three payloads: two 8-byte words
     extern __shared__ __align__(128) uint32_t rsm[];     // [2][SW] stages (then the sorted tile for 64-bit keys)
     __shared__ __align__(8) uint64_t full[2], empty[2];
     __shared__ SortMeta meta[2];
@@ -443,6 +445,44 @@ __global__ void __launch_bounds__(RS_BLOCK, (rs_min_blocks<KW, TILE, SP>()))
                             if (key_dst) key_dst[dd] = (KW)kv.x;
                             dst0[dd] = kv.y;
                             dst1[dd] = sb1[i];
+                        } else {
+                            atomicOr(err, ERR_INTERNAL);
+                        }
+                    }
+                }
+                if (INPLACE) fence_proxy_async_smem();  // our writes to the stage before the next bulk copy into it
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[s]);  // this warp's reads of the stage are done
+                continue;
+            }
+        }
+        if constexpr (QUAD) {
+            if (pay.n == 3) {
+                uint2* sa = reinterpret_cast<uint2*>(sb32);             // (key, payload 0)
+                uint2* sq = reinterpret_cast<uint2*>(sb32 + 2 * TILE);  // (payload 1, payload 2)
+#pragma unroll
+                for (int j = 0; j < IPT; ++j) {
+                    if (dig[j] < RADIX) {
+                        sa[slot[j]] = make_uint2((uint32_t)kreg[j], preg[0][j]);
+                        sq[slot[j]] = make_uint2(preg[1][j], preg[2][j]);
+                    }
+                }
+                consumer_sync<RS_THREADS>();
+                uint32_t* dst0 = pay.dst[0];
+                uint32_t* dst1 = pay.dst[1];
+                uint32_t* dst2 = pay.dst[2];
+#pragma unroll
+                for (int r = 0; r < IPT; ++r) {
+                    const int i = r * RS_THREADS + tid;
+                    if (i < M.n) {
+                        const uint2 kv = sa[i];
+                        const uint2 pq = sq[i];
+                        const uint32_t dd = s_goff[digit_of((KW)kv.x, shift)] + (uint32_t)i;
+                        if ((int64_t)dd < count) {
+                            if (key_dst) key_dst[dd] = (KW)kv.x;
+                            dst0[dd] = kv.y;
+                            dst1[dd] = pq.x;
+                            dst2[dd] = pq.y;
                         } else {
                             atomicOr(err, ERR_INTERNAL);
                         }
@@ -1342,7 +1382,7 @@ size_t sort_status_words(int64_t max_count) {
 }
 
 // Resident blocks per SM of the move kernels (by variant) and the SM count.
-static int g_rs_occ[4];
+static int g_rs_occ[5];
 static int g_rs_sms = 0;
 
 template <typename KW, int TILE, int SP>
@@ -1380,6 +1420,9 @@ cudaError_t launch_sort_pass(int key64, const int64_t* count_ptr, int64_t max_co
     if (g_rs_sms == 0) return cudaErrorInvalidValue;
     const SortStatusArea A = sort_status_layout(max_count, status);
     const bool many = pay.n > 1;
+    if (!key64 && pay.n >= 3)
+        return rs_pass<uint32_t, 2048, 3>(count_ptr, max_count, key_src, key_dst, pay, digit_base, shift, A,
+                                          g_rs_occ[4], err, spin_limit, withhold, s);
     if (key64)
         return many ? rs_pass<uint64_t, 1024, 4>(count_ptr, max_count, key_src, key_dst, pay, digit_base, shift, A,
                                                  g_rs_occ[3], err, spin_limit, withhold, s)
@@ -1429,6 +1472,7 @@ cudaError_t init_presort_kernels() {
     if (e == cudaSuccess) e = init_rs_move<uint32_t, 2048, 2>(&g_rs_occ[1]);
     if (e == cudaSuccess) e = init_rs_move<uint64_t, 2048, 1>(&g_rs_occ[2]);
     if (e == cudaSuccess) e = init_rs_move<uint64_t, 1024, 4>(&g_rs_occ[3]);
+    if (e == cudaSuccess) e = init_rs_move<uint32_t, 2048, 3>(&g_rs_occ[4]);
     return e;
 }
 

@@ -810,19 +810,20 @@ __device__ __forceinline__ unsigned long long global_ns() {
         }                                                                          \
     } while (0)
 
-// A finisher unit's input: rk[p][i] = rank p of array 0's element i (array
-// 0 is sorted by rank 0), and for arrays d >= 1 the lid of each element
-// (position in array 0 of the tuple with its rank 0).  All (2K-1) loads per
-// position are in flight before the first is used.
+// A finisher unit's input: rk[i] = rank 0 of array 0's element i (array 0
+// is sorted by rank 0), and for arrays d >= 1 the lid of each element (its
+// position in array 0).  All K loads per position are in flight before the
+// first is used.  (Array 0's other rank planes are not needed here: the
+// unit's levels compare positions in the arrays.)
 template <int K, int SMAX>
 __device__ __forceinline__ void fin_load_unit(const AllBufs& bufs, const CloudDev& C, int64_t g, int S,
                                               uint32_t* rk, uint16_t* arr, int* bad) {
     constexpr int PPT = SMAX / FIN_THREADS;
     const int tid = threadIdx.x;
-    uint32_t v[2 * K - 1][PPT];
+    uint32_t v[K][PPT];
 #pragma unroll
-    for (int p = 0; p < 2 * K - 1; ++p) {
-        const uint32_t* src = p < K ? bufs.p[0][C.buf[0]][p] : bufs.p[p - K + 1][C.buf[p - K + 1]][0];
+    for (int p = 0; p < K; ++p) {
+        const uint32_t* src = bufs.p[p][C.buf[p]][0];  // rank 0 of array p
 #pragma unroll
         for (int j = 0; j < PPT; ++j) {
             const int i = tid + j * FIN_THREADS;
@@ -830,14 +831,11 @@ __device__ __forceinline__ void fin_load_unit(const AllBufs& bufs, const CloudDe
         }
     }
 #pragma unroll
-    for (int p = 0; p < K; ++p)
-#pragma unroll
-        for (int j = 0; j < PPT; ++j) {
-            const int i = tid + j * FIN_THREADS;
-            if (i < S) rk[p * SMAX + i] = v[p][j];
-        }
+    for (int j = 0; j < PPT; ++j) {
+        const int i = tid + j * FIN_THREADS;
+        if (i < S) rk[i] = v[0][j];
+    }
     __syncthreads();
-#pragma unroll
     // the K-1 arrays' searches advance together: (K-1) x PPT independent chains
     int pos[K - 1][PPT];
 #pragma unroll
@@ -850,7 +848,7 @@ __device__ __forceinline__ void fin_load_unit(const AllBufs& bufs, const CloudDe
         for (int d = 0; d < K - 1; ++d)
 #pragma unroll
             for (int j = 0; j < PPT; ++j)
-                if (pos[d][j] + step <= S && rk[pos[d][j] + step - 1] < v[K + d][j]) pos[d][j] += step;
+                if (pos[d][j] + step <= S && rk[pos[d][j] + step - 1] < v[d + 1][j]) pos[d][j] += step;
     }
 #pragma unroll
     for (int d = 1; d < K; ++d)
@@ -858,7 +856,7 @@ __device__ __forceinline__ void fin_load_unit(const AllBufs& bufs, const CloudDe
         for (int j = 0; j < PPT; ++j) {
             const int i = tid + j * FIN_THREADS;
             if (i < S) {
-                if (pos[d - 1][j] >= S || rk[pos[d - 1][j]] != v[K - 1 + d][j]) *bad = 1;
+                if (pos[d - 1][j] >= S || rk[pos[d - 1][j]] != v[d][j]) *bad = 1;
                 arr[d * SMAX + i] = (uint16_t)min(pos[d - 1][j], S - 1);
             }
         }
@@ -892,8 +890,8 @@ __global__ void __launch_bounds__(FIN_THREADS, fin_min_blocks(SMAX, K))
     __shared__ int2 s_lab[fin_labels(SMAX)];
     __shared__ int s_cur[MAXK + 1];
     __shared__ int s_nseg;
-    uint32_t* rk = sm;                                          // rk[p * smax + lid]
-    uint32_t* seg = rk + (size_t)k * smax;                      // packed segment per position
+    uint32_t* rk = sm;                                          // rk[lid]: rank 0
+    uint32_t* seg = rk + smax;                                  // packed segment per position
     uint16_t* arr = reinterpret_cast<uint16_t*>(seg + smax);   // (k+1) storages of lids
     uint16_t* nodelid = arr + (size_t)(k + 1) * smax;           // tuple chosen at each position
     uint8_t* lab = reinterpret_cast<uint8_t*>(nodelid + smax);   // per lid: segment label at the current level
@@ -1283,7 +1281,7 @@ static cudaError_t init_level_kernels() {
 
 int finish_kmax(int smax) { return fin_kmax(smax); }
 size_t finish_smem(int k, int smax) {
-    return (size_t)k * smax * 4 + (size_t)smax * 4 + (size_t)(k + 2) * smax * 2 + (size_t)smax;
+    return (size_t)smax * 4 + (size_t)smax * 4 + (size_t)(k + 2) * smax * 2 + (size_t)smax;
 }
 
 cudaError_t init_build_kernels() {

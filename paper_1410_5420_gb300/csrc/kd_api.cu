@@ -1157,7 +1157,7 @@ kd_status build_batch(kd_ctx* ctx, kd_presorted* H, kd_tree* outs) {
                 J.lev_out = lout;
                 J.src_buf = buf_after(moves[i][q]);
                 J.dst_buf = buf_after(moves[i][q] + 1);
-                J.write_med = (lout % k == q) && (lout < lam[i]);
+                J.write_med = (lout % k == q) && (lout < lam[i]) ? LEVEL_MED : 0;
                 J.tile_begin = ntl;
                 jl.push_back(J);
                 ntl += (H->m_c[i] + tile - 1) / tile;
@@ -1184,6 +1184,19 @@ kd_status build_batch(kd_ctx* ctx, kd_presorted* H, kd_tree* outs) {
     }
     for (int i = 0; i < count; ++i)
         for (int q = 0; q < k && q < MAXK; ++q) cd[i].buf[q] = (uint8_t)buf_after(moves[i][q]);
+    // an array's last move before the finisher writes rank 0 alone: the
+    // finisher reads no other plane
+    {
+        std::vector<uint8_t> seen((size_t)count * k, 0);
+        for (size_t st = step_jobs.size(); st-- > 0;)
+            for (auto& J : step_jobs[st]) {
+                uint8_t& f = seen[(size_t)J.cloud * k + step_q[st]];
+                if (!f) {
+                    J.write_med |= LEVEL_FINAL;
+                    f = 1;
+                }
+            }
+    }
 
     AllBufs bufs{};
     for (int d = 0; d < k && k >= 2; ++d)

@@ -651,7 +651,7 @@ __global__ void __launch_bounds__(LEVEL_BLOCK, K <= 3 ? 3 : 2)
                 c += x;
             }
             s_dlh[d] = make_int2(a, z);
-            s_dmid[d] = M.write_med ? a + ((z - a) >> 1) : -1;
+            s_dmid[d] = (M.write_med & LEVEL_MED) ? a + ((z - a) >> 1) : -1;
         }
         if (tid < LEVEL_NSMAX) s_segidx[tid] = (int32_t)rec[9 + tid];
         consumer_sync<LEVEL_THREADS>();
@@ -670,7 +670,7 @@ __global__ void __launch_bounds__(LEVEL_BLOCK, K <= 3 ? 3 : 2)
                 const int2 lh = s_dlh[d];
                 if (dd >= lh.x && dd <= lh.y) {
                     dest[j] = dd;
-                    if (M.write_med && dd == s_dmid[d]) {
+                    if ((M.write_med & LEVEL_MED) && dd == s_dmid[d]) {
                         const int sj = (int)(d >> F);
                         const int32_t si = (s_segidx[sj] << F) + (int32_t)(d - ((uint32_t)sj << F));
                         // rank 0 of the median (its position in array 0) gives
@@ -694,9 +694,10 @@ __global__ void __launch_bounds__(LEVEL_BLOCK, K <= 3 ? 3 : 2)
         }
         // each run of equal digits goes to consecutive addresses: stores from
         // registers, coalesced per run
+        const bool final_move = (M.write_med & LEVEL_FINAL) != 0;  // only rank 0 is read after it
 #pragma unroll
         for (int f = 0; f < K; ++f) {
-            if (f == own) continue;
+            if (f == own || (final_move && (M.lev_in + f) % K != 0)) continue;
             uint32_t* dp = bufs.p[q][M.dst_buf][(M.lev_in + f) % K] + M.goff;
 #pragma unroll
             for (int j = 0; j < IPT; ++j)

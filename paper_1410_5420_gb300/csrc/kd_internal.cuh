@@ -397,7 +397,7 @@ struct LevelTile {
     int32_t lev_in;   // level of the input view (after the free split)
     int32_t lev_out;  // level after the pass
     int32_t src_buf, dst_buf;
-    int32_t write_med;  // lev_out is this array's primary level and < lam
+    int32_t write_med;  // LEVEL_MED: lev_out is this array's primary level and < lam; | LEVEL_FINAL
     int64_t pos0;       // first cloud-local position of the tile
     int32_t npos;       // positions in the tile
     int32_t first;      // 1: first tile of this cloud in this launch (no look-back past it)
@@ -407,6 +407,12 @@ struct FinUnit {
     int32_t cloud;
     int32_t seg;  // segment index at level lam of the cloud
 };
+
+// Flags of a level job: the pass writes the medians of lev_out
+// (LEVEL_MED); it is the array's last move before the finisher, which reads
+// rank 0 alone, so the other planes are not written (LEVEL_FINAL).
+constexpr int32_t LEVEL_MED = 1;
+constexpr int32_t LEVEL_FINAL = 2;
 
 // One cloud's share of a level step: its tiles are tile_begin ..
 // tile_begin + ceil(m / tile) - 1 of the launch.

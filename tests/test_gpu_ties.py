@@ -72,6 +72,14 @@ def test_runs_at_tile_edges(cuda_lib, ctx, dtype, k):
     check(cuda_lib, ctx, runs_cloud(EDGES, k, dtype, 750 + k, other_bits=7))
 
 
+@pytest.mark.parametrize("length", [100, 300], ids=["runs_ordered_on_chip", "runs_costly_whole_key_sort"])
+def test_run_cost_threshold(cuda_lib, ctx, length):
+    """Runs of 100 tuples cost 100 compares per tuple (ordered on chip);
+    runs of 300 cost 300, above the threshold, so array 0 takes the
+    whole-key sort: both equal the oracle."""
+    check(cuda_lib, ctx, runs_cloud([length] * 40, 3, np.int32, 760 + length, other_bits=8))
+
+
 def test_all_tuples_share_x0(cuda_lib, ctx):
     c = runs_cloud([30000], 3, np.int64, 731, other_bits=9)
     check(cuda_lib, ctx, c)

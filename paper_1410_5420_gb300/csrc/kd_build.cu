@@ -871,9 +871,9 @@ __host__ __device__ constexpr int fin_kmax(int smax) { return smax >= 4096 ? 3 :
 // six blocks fit the shared memory, and trading registers for them (a few
 // spills) hides more of the shared-memory latency (3.20 ms per 2^26 step at
 // k = 3, against 3.33 at five blocks and 3.58 at seven); wider tuples fit
-// fewer.
+// fewer.  At 2048 tuples five blocks (3.77 ms) beat four (3.88).
 __host__ __device__ constexpr int fin_min_blocks(int smax, int k) {
-    return smax >= 4096 ? 2 : (smax >= 2048 ? 3 : (k <= 4 ? 6 : (k <= 6 ? 5 : 4)));
+    return smax >= 4096 ? 2 : (smax >= 2048 ? 5 : (k <= 4 ? 6 : (k <= 6 ? 5 : 4)));
 }
 
 // K: the number of dimensions, so that the unit's per-dimension arrays and

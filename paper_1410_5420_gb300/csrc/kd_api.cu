@@ -39,9 +39,9 @@ cudaError_t launch_gather(int key64, const int64_t* count_ptr, int64_t max_count
                           const uint32_t* ids, void* out, int* err, cudaStream_t s);
 size_t dedup_scratch_words(int64_t n);
 cudaError_t launch_dedup(int key64, int64_t n, const void* key0, const uint32_t* ids, const void* T, int64_t tstride,
-                         int k, const uint32_t* cloud_plane, int cloud_digits, uint32_t* ids_out, void* y1, void* y2,
-                         void* y1_out, void* y2_out, uint32_t* scratch, int64_t* m_out, uint32_t* hist,
-                         int32_t* mcloud, int* err, cudaStream_t s);
+                         int k, const uint32_t* cloud_plane, int cloud_digits, uint32_t* ids_out, void* y1_out,
+                         void* y2_out, uint32_t* scratch, int64_t* m_out, uint32_t* hist, int32_t* mcloud, int* err,
+                         cudaStream_t s);
 cudaError_t launch_own_ranks(const int64_t* m_ptr, int64_t max_m, int k, const AllPlanes& rec, cudaStream_t s);
 cudaError_t launch_run_stats(int key64, const int64_t* count_ptr, int64_t max_count, const void* key0, int tk,
                              uint2* range, uint2* cross_runs, uint32_t* run_meta, cudaStream_t s);
@@ -735,18 +735,14 @@ kd_status presort_batch(kd_ctx* ctx, const kd_cloud* clouds, int count, kd_preso
     // array-0 order, so neither needs a gather
     const bool y_first = count == 1 && k >= 2 && all_arrays;
     const bool y_second = y_first && k >= 3 && !key64;
-    unsigned char *y1tmp = nullptr, *y2tmp = nullptr, *y2c = nullptr;
-    if (y_first) CKS(S.get(&y1tmp, (size_t)NS * w + 16));
-    if (y_second) {
-        CKS(S.get(&y2tmp, (size_t)NS * w + 16));
-        CKS(S.get(&y2c, (size_t)NS * w + 16));
-    }
+    unsigned char* y2c = nullptr;
+    if (y_second) CKS(S.get(&y2c, (size_t)NS * w + 16));
     {
         LaunchTimer lt(ctx, F_DEDUP, (double)N, nullptr, 2.0 * w + 8 + (k - 1) * w);
         ctx->launches += 2;  // flags, tile scan, compaction
-        CK(launch_dedup(key64, N, kbuf[kc], ibuf[ic], tplanes, NS, k, cloud_plane, cloud_digits, dedup_out, y1tmp, y2tmp,
-                        y_first ? (void*)kbuf[kc] : nullptr, y2c, status + status_words, H->d_m, hist, mcloud,
-                        d_err, s));
+        CK(launch_dedup(key64, N, kbuf[kc], ibuf[ic], tplanes, NS, k, cloud_plane, cloud_digits, dedup_out,
+                        y_first ? (void*)kbuf[kc] : nullptr, y2c, status + status_words, H->d_m, hist, mcloud, d_err,
+                        s));
     }
     ic ^= 1;
     {

@@ -646,13 +646,12 @@ constexpr int DEDUP_TILE = 4096;
 // order): a tuple equal to its predecessor goes.  The keys x_1..x_{k-1} of
 // position i are T[d * tstride + i], in array-0 order (the predecessor's
 // are the neighbour lane's).  The kept tuples' counts leave the digit
-// histograms, and y1 / y2 (if not NULL) receive x_{k-1} and x_{k-2} in
-// array-0 order for the first two sorts of the chain.
+// histograms.
 template <typename KW>
 __global__ void __launch_bounds__(256) k_dedup_flags(int64_t n, const KW* __restrict__ key0,
                                                      const uint32_t* __restrict__ ids, const KW* __restrict__ T,
                                                      int64_t tstride, int k, const uint32_t* __restrict__ cloud_plane,
-                                                     int cloud_digits, KW* __restrict__ y1, KW* __restrict__ y2,
+                                                     int cloud_digits,
                                                      uint32_t* __restrict__ keepbits, uint32_t* __restrict__ tile_cnt,
                                                      uint32_t* __restrict__ hist, int32_t* __restrict__ mcloud,
                                                      int* __restrict__ err) {
@@ -716,16 +715,6 @@ __global__ void __launch_bounds__(256) k_dedup_flags(int64_t n, const KW* __rest
         lastid = __shfl_sync(0xffffffffu, id, 31);
         bool dup = valid && pos > 0 && pk0 == k0 && same;
         if (dup && cloud_plane && cloud_plane[id] != cloud_plane[pid]) dup = false;
-        if (valid && y1) {
-            KW a = 0, b = 0;
-#pragma unroll
-            for (int d = 0; d < TM; ++d) {
-                if (d == tk - 1) a = r[d];
-                if (d == tk - 2) b = r[d];
-            }
-            y1[pos] = a;
-            if (y2) y2[pos] = b;
-        }
         if (dup) {
             for (int b = 0; b < D; ++b) atomicSub(&hist[b * RADIX + (uint32_t)((k0 >> (8 * b)) & 255u)], 1u);
 #pragma unroll
@@ -778,6 +767,8 @@ __global__ void __launch_bounds__(256) k_dedup_compact(int64_t n, const uint32_t
                                                        uint32_t* __restrict__ ids_out, const KW* __restrict__ y1,
                                                        const KW* __restrict__ y2, KW* __restrict__ y1_out,
                                                        KW* __restrict__ y2_out) {
+    // y1 / y2: planes of x_{k-1} and x_{k-2} in array-0 order (NULL: not
+    // wanted); the kept tuples' values go to y1_out / y2_out
     constexpr int IPT = DEDUP_TILE / 256;
     __shared__ uint32_t s_wsum[8];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -801,8 +792,8 @@ __global__ void __launch_bounds__(256) k_dedup_compact(int64_t n, const uint32_t
         if ((ball[j] >> lane) & 1u) {
             const uint32_t o = out + __popc(ball[j] & lanemask_lt());
             ids_out[o] = ids[pos];
-            if (y1_out) y1_out[o] = y1[pos];
-            if (y2_out) y2_out[o] = y2[pos];
+            if (y1 && y1_out) y1_out[o] = y1[pos];
+            if (y2 && y2_out) y2_out[o] = y2[pos];
         }
         out += __popc(ball[j]);
     }
@@ -1503,8 +1494,8 @@ size_t dedup_scratch_words(int64_t n) {
 }
 
 cudaError_t launch_dedup(int key64, int64_t n, const void* key0, const uint32_t* ids, const void* T, int64_t tstride,
-                         int k, const uint32_t* cloud_plane, int cloud_digits, uint32_t* ids_out, void* y1, void* y2,
-                         void* y1_out, void* y2_out, uint32_t* scratch, int64_t* m_out, uint32_t* hist,
+                         int k, const uint32_t* cloud_plane, int cloud_digits, uint32_t* ids_out, void* y1_out,
+                         void* y2_out, uint32_t* scratch, int64_t* m_out, uint32_t* hist,
                          int32_t* mcloud, int* err, cudaStream_t s) {
     const int64_t tiles = (n + DEDUP_TILE - 1) / DEDUP_TILE;
     if (tiles == 0) return cudaSuccess;
@@ -1514,11 +1505,12 @@ cudaError_t launch_dedup(int key64, int64_t n, const void* key0, const uint32_t*
 #define KD_DEDUP(KW)                                                                                          \
     k_dedup_flags<KW><<<(unsigned)tiles, 256, 0, s>>>(n, (const KW*)key0, ids, (const KW*)T, tstride, k,        \
                                                       cloud_plane,                                            \
-                                                      cloud_digits, (KW*)y1, (KW*)y2, keepbits, tcnt, hist,   \
+                                                      cloud_digits, keepbits, tcnt, hist,                     \
                                                       mcloud, err);                                           \
     k_tile_scan<<<1, 1024, 0, s>>>(tiles, tcnt, toff, m_out);                                                 \
-    k_dedup_compact<KW><<<(unsigned)tiles, 256, 0, s>>>(n, ids, keepbits, toff, ids_out, (const KW*)y1,       \
-                                                        (const KW*)y2, (KW*)y1_out, (KW*)y2_out);
+    k_dedup_compact<KW><<<(unsigned)tiles, 256, 0, s>>>(                                                      \
+        n, ids, keepbits, toff, ids_out, (y1_out && k >= 2) ? (const KW*)T + (int64_t)(k - 2) * tstride : nullptr, \
+        (y2_out && k >= 3) ? (const KW*)T + (int64_t)(k - 3) * tstride : nullptr, (KW*)y1_out, (KW*)y2_out);
     if (key64) {
         KD_DEDUP(uint64_t)
     } else {

@@ -672,10 +672,12 @@ __global__ void __launch_bounds__(256) k_dedup_flags(int64_t n, const KW* __rest
     {
         const int64_t p0 = base + wbase;
         if (p0 > 0 && p0 - 1 < n) {
-            lastid = ids[p0 - 1];
-            if ((int64_t)lastid >= n) {
-                atomicOr(err, ERR_INTERNAL);
-                lastid = 0;
+            if (cloud_plane) {
+                lastid = ids[p0 - 1];
+                if ((int64_t)lastid >= n) {
+                    atomicOr(err, ERR_INTERNAL);
+                    lastid = 0;
+                }
             }
             lastk0 = key0[p0 - 1];
 #pragma unroll
@@ -688,7 +690,8 @@ __global__ void __launch_bounds__(256) k_dedup_flags(int64_t n, const KW* __rest
     for (int j = 0; j < IPT; ++j) {
         const int64_t pos = base + wbase + j * 32 + lane;
         const bool valid = pos < n;
-        uint32_t id = valid ? ids[pos] : 0u;
+        // ids matter only for the cloud test of a batch
+        uint32_t id = (valid && cloud_plane) ? ids[pos] : 0u;
         if ((int64_t)id >= n) {
             atomicOr(err, ERR_INTERNAL);
             id = 0;

@@ -646,8 +646,9 @@ constexpr int DEDUP_TILE = 4096;
 // order): a tuple equal to its predecessor goes.  The keys x_1..x_{k-1} of
 // position i are T[d * tstride + i], in array-0 order (the predecessor's
 // are the neighbour lane's).  The kept tuples' counts leave the digit
-// histograms.
-template <typename KW>
+// histograms.  TM: the most tail planes the kernel compares (k - 1 at
+// most), so that k <= 3 keeps two of them in registers, not MAXK - 1.
+template <typename KW, int TM>
 __global__ void __launch_bounds__(256) k_dedup_flags(int64_t n, const KW* __restrict__ key0,
                                                      const uint32_t* __restrict__ ids, const KW* __restrict__ T,
                                                      int64_t tstride, int k, const uint32_t* __restrict__ cloud_plane,
@@ -657,7 +658,6 @@ __global__ void __launch_bounds__(256) k_dedup_flags(int64_t n, const KW* __rest
                                                      int* __restrict__ err) {
     constexpr int IPT = DEDUP_TILE / 256;
     constexpr int D = sizeof(KW);
-    constexpr int TM = MAXK - 1;
     __shared__ uint32_t s_wsum[8];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tk = k - 1;
@@ -686,57 +686,75 @@ __global__ void __launch_bounds__(256) k_dedup_flags(int64_t n, const KW* __rest
         }
     }
     uint32_t wcount = 0;
+    // rows are taken U at a time, all their loads issued before the first
+    // is used (ids matter only for the cloud test of a batch)
+    constexpr int U = D == 4 ? 4 : 2;
+    static_assert(IPT % U == 0, "rows per warp must be a multiple of the batch");
 #pragma unroll 1
-    for (int j = 0; j < IPT; ++j) {
-        const int64_t pos = base + wbase + j * 32 + lane;
-        const bool valid = pos < n;
-        // ids matter only for the cloud test of a batch
-        uint32_t id = (valid && cloud_plane) ? ids[pos] : 0u;
-        if ((int64_t)id >= n) {
-            atomicOr(err, ERR_INTERNAL);
-            id = 0;
-        }
-        const KW k0 = valid ? key0[pos] : (KW)0;
-        KW r[TM];
+    for (int j0 = 0; j0 < IPT; j0 += U) {
+        uint32_t idb[U];
+        KW k0b[U], rb[U][TM];
 #pragma unroll
-        for (int d = 0; d < TM; ++d) r[d] = (valid && d < tk) ? T[d * tstride + pos] : (KW)0;
-        KW pk0 = __shfl_up_sync(0xffffffffu, k0, 1);
-        uint32_t pid = __shfl_up_sync(0xffffffffu, id, 1);
-        bool same = true;
+        for (int u = 0; u < U; ++u) {
+            const int64_t pos = base + wbase + (j0 + u) * 32 + lane;
+            const bool valid = pos < n;
+            idb[u] = (valid && cloud_plane) ? ids[pos] : 0u;
+            k0b[u] = valid ? key0[pos] : (KW)0;
 #pragma unroll
-        for (int d = 0; d < TM; ++d) {
-            KW q = __shfl_up_sync(0xffffffffu, r[d], 1);
-            if (lane == 0) q = last[d];
-            same = same && (d >= tk || q == r[d]);
-            last[d] = __shfl_sync(0xffffffffu, r[d], 31);
+            for (int d = 0; d < TM; ++d) rb[u][d] = (valid && d < tk) ? T[d * tstride + pos] : (KW)0;
         }
-        if (lane == 0) {
-            pk0 = lastk0;
-            pid = lastid;
-        }
-        lastk0 = __shfl_sync(0xffffffffu, k0, 31);
-        lastid = __shfl_sync(0xffffffffu, id, 31);
-        bool dup = valid && pos > 0 && pk0 == k0 && same;
-        if (dup && cloud_plane && cloud_plane[id] != cloud_plane[pid]) dup = false;
-        if (dup) {
-            for (int b = 0; b < D; ++b) atomicSub(&hist[b * RADIX + (uint32_t)((k0 >> (8 * b)) & 255u)], 1u);
 #pragma unroll
-            for (int d = 0; d < TM; ++d)
-                if (d < tk)
-                    for (int b = 0; b < D; ++b)
-                        atomicSub(&hist[((d + 1) * D + b) * RADIX + (uint32_t)((r[d] >> (8 * b)) & 255u)], 1u);
-            if (cloud_plane) {
-                const uint32_t c = cloud_plane[id];
-                for (int b = 0; b < cloud_digits; ++b)
-                    atomicSub(&hist[(k * D + b) * RADIX + ((c >> (8 * b)) & 255u)], 1u);
-                atomicSub(&mcloud[c], 1);
-            } else if (mcloud) {
-                atomicSub(&mcloud[0], 1);
+        for (int u = 0; u < U; ++u) {
+            const int j = j0 + u;
+            const int64_t pos = base + wbase + j * 32 + lane;
+            const bool valid = pos < n;
+            uint32_t id = idb[u];
+            if ((int64_t)id >= n) {
+                atomicOr(err, ERR_INTERNAL);
+                id = 0;
             }
+            const KW k0 = k0b[u];
+            KW r[TM];
+#pragma unroll
+            for (int d = 0; d < TM; ++d) r[d] = rb[u][d];
+            KW pk0 = __shfl_up_sync(0xffffffffu, k0, 1);
+            uint32_t pid = __shfl_up_sync(0xffffffffu, id, 1);
+            bool same = true;
+#pragma unroll
+            for (int d = 0; d < TM; ++d) {
+                KW q = __shfl_up_sync(0xffffffffu, r[d], 1);
+                if (lane == 0) q = last[d];
+                same = same && (d >= tk || q == r[d]);
+                last[d] = __shfl_sync(0xffffffffu, r[d], 31);
+            }
+            if (lane == 0) {
+                pk0 = lastk0;
+                pid = lastid;
+            }
+            lastk0 = __shfl_sync(0xffffffffu, k0, 31);
+            lastid = __shfl_sync(0xffffffffu, id, 31);
+            bool dup = valid && pos > 0 && pk0 == k0 && same;
+            if (dup && cloud_plane && cloud_plane[id] != cloud_plane[pid]) dup = false;
+            if (dup) {
+                for (int b = 0; b < D; ++b) atomicSub(&hist[b * RADIX + (uint32_t)((k0 >> (8 * b)) & 255u)], 1u);
+#pragma unroll
+                for (int d = 0; d < TM; ++d)
+                    if (d < tk)
+                        for (int b = 0; b < D; ++b)
+                            atomicSub(&hist[((d + 1) * D + b) * RADIX + (uint32_t)((r[d] >> (8 * b)) & 255u)], 1u);
+                if (cloud_plane) {
+                    const uint32_t c = cloud_plane[id];
+                    for (int b = 0; b < cloud_digits; ++b)
+                        atomicSub(&hist[(k * D + b) * RADIX + ((c >> (8 * b)) & 255u)], 1u);
+                    atomicSub(&mcloud[c], 1);
+                } else if (mcloud) {
+                    atomicSub(&mcloud[0], 1);
+                }
+            }
+            const uint32_t ball = __ballot_sync(0xffffffffu, valid && !dup);
+            if (lane == 0 && base + wbase + j * 32 < n) keepbits[(base + wbase + j * 32) >> 5] = ball;
+            wcount += __popc(ball);
         }
-        const uint32_t ball = __ballot_sync(0xffffffffu, valid && !dup);
-        if (lane == 0 && base + wbase + j * 32 < n) keepbits[(base + wbase + j * 32) >> 5] = ball;
-        wcount += __popc(ball);
     }
     if (lane == 0) s_wsum[warp] = wcount;
     __syncthreads();
@@ -830,6 +848,8 @@ constexpr int RT_EXT = 512;
 constexpr int RT_CAP = RT_TILE + RT_EXT;  // positions a tile range holds at most
 constexpr int RT_WARP = 32;
 constexpr int RUN_BLOCK = 4096;
+constexpr int RS_ROWS = 8;  // rows of 32 positions whose loads k_run_stats issues together
+static_assert((RT_TILE / 32) % RS_ROWS == 0, "a tile's rows must be a multiple of the batch");
 
 // Shared memory of k_run_tiles (x_0, tk tail words or a packed 64-bit key,
 // and the id per staged position) and of k_run_cross (tk tail words and
@@ -890,25 +910,42 @@ __global__ void __launch_bounds__(256) k_run_stats(const int64_t* __restrict__ c
     const int64_t ntiles = (n + RT_TILE - 1) / RT_TILE;
     for (int64_t t = (int64_t)blockIdx.x * 8 + warp; t < ntiles; t += (int64_t)gridDim.x * 8) {
         const int64_t c0 = t * RT_TILE;
-        int64_t open = -1;   // first position of the run still open, if it began in this tile
-        int64_t first = -1;  // the tile's first run start
-#pragma unroll 8
-        for (int r = 0; r < RT_TILE / 32; ++r) {
-            const int64_t e = c0 + r * 32 + lane;
-            const bool valid = e < n;
-            const KW v = valid ? key0[e] : (KW)0;
-            KW pv = __shfl_up_sync(0xffffffffu, v, 1);
-            if (lane == 0 && valid && e > 0) pv = key0[e - 1];
-            const bool head = valid && (e == 0 || pv != v);
-            const uint32_t hb = __ballot_sync(0xffffffffu, head);
-            const uint32_t below = hb & lt;
-            const int64_t prev = below ? c0 + r * 32 + 31 - __clz(below) : open;
-            if (head && prev >= 0) RUN_ACCOUNT(e - prev);
-            if (hb) {
-                if (first < 0) first = c0 + r * 32 + __ffs(hb) - 1;
-                open = c0 + r * 32 + 31 - __clz(hb);
+        // positions relative to c0 while scanning the tile
+        int open_r = -1;   // first position of the run still open, if it began in this tile
+        int first_r = -1;  // the tile's first run start
+        const int valid_r = n - c0 < RT_TILE ? (int)(n - c0) : RT_TILE;  // positions of the tile
+        // x_0 at the position before each row (the tile's predecessor first)
+        KW carry = c0 > 0 ? key0[c0 - 1] : (KW)0;
+        const KW* tile = key0 + c0;
+#pragma unroll 1
+        for (int r0 = 0; r0 < RT_TILE / 32; r0 += RS_ROWS) {
+            KW vb[RS_ROWS];  // all rows' loads in flight before the first is used
+#pragma unroll
+            for (int u = 0; u < RS_ROWS; ++u) {
+                const int i = (r0 + u) * 32 + lane;
+                vb[u] = i < valid_r ? tile[i] : (KW)0;
+            }
+#pragma unroll
+            for (int u = 0; u < RS_ROWS; ++u) {
+                const int rb = (r0 + u) * 32;
+                const int i = rb + lane;
+                const KW v = vb[u];
+                KW pv = __shfl_up_sync(0xffffffffu, v, 1);
+                if (lane == 0) pv = carry;
+                carry = __shfl_sync(0xffffffffu, v, 31);
+                const bool head = i < valid_r && ((c0 == 0 && i == 0) || pv != v);
+                const uint32_t hb = __ballot_sync(0xffffffffu, head);
+                const uint32_t below = hb & lt;
+                const int prev = below ? rb + 31 - __clz(below) : open_r;
+                if (head && prev >= 0) RUN_ACCOUNT(i - prev);
+                if (hb) {
+                    if (first_r < 0) first_r = rb + __ffs(hb) - 1;
+                    open_r = rb + 31 - __clz(hb);
+                }
             }
         }
+        const int64_t open = open_r >= 0 ? c0 + open_r : -1;
+        int64_t first = first_r >= 0 ? c0 + first_r : -1;
         if (lane == 0) {
             // the run holding the tile's last position ends at `last`
             const int64_t tl = c0 + RT_TILE - 1 < n - 1 ? c0 + RT_TILE - 1 : n - 1;
@@ -1506,10 +1543,14 @@ cudaError_t launch_dedup(int key64, int64_t n, const void* key0, const uint32_t*
     uint32_t* tcnt = keepbits + (n + 31) / 32;
     uint32_t* toff = tcnt + tiles;
 #define KD_DEDUP(KW)                                                                                          \
-    k_dedup_flags<KW><<<(unsigned)tiles, 256, 0, s>>>(n, (const KW*)key0, ids, (const KW*)T, tstride, k,        \
-                                                      cloud_plane,                                            \
-                                                      cloud_digits, keepbits, tcnt, hist,                     \
-                                                      mcloud, err);                                           \
+    if (k <= 3)                                                                                               \
+        k_dedup_flags<KW, 2><<<(unsigned)tiles, 256, 0, s>>>(n, (const KW*)key0, ids, (const KW*)T, tstride, k, \
+                                                             cloud_plane, cloud_digits, keepbits, tcnt, hist,   \
+                                                             mcloud, err);                                      \
+    else                                                                                                      \
+        k_dedup_flags<KW, MAXK - 1><<<(unsigned)tiles, 256, 0, s>>>(n, (const KW*)key0, ids, (const KW*)T,      \
+                                                                    tstride, k, cloud_plane, cloud_digits,      \
+                                                                    keepbits, tcnt, hist, mcloud, err);         \
     k_tile_scan<<<1, 1024, 0, s>>>(tiles, tcnt, toff, m_out);                                                 \
     k_dedup_compact<KW><<<(unsigned)tiles, 256, 0, s>>>(                                                      \
         n, ids, keepbits, toff, ids_out, (y1_out && k >= 2) ? (const KW*)T + (int64_t)(k - 2) * tstride : nullptr, \

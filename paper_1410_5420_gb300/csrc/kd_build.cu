@@ -837,14 +837,37 @@ __device__ __forceinline__ void fin_load_unit(const AllBufs& bufs, const CloudDe
         if (i < S) rk[i] = v[0][j];
     }
     __syncthreads();
-    // the K-1 arrays' searches advance together: (K-1) x PPT independent chains
+    // The K-1 arrays' searches advance together: (K-1) x PPT independent
+    // chains.  The first five halvings pick one of 32 blocks of SMAX / 32
+    // positions by the last rank 0 of each block, held one per lane and
+    // read by shuffles (no shared-memory bank conflicts); the rest search
+    // the block in shared memory.
+    constexpr int BK = SMAX / 32;
+    const int lane = tid & 31;
+    const bool svalid = lane * BK + BK - 1 < S;  // block `lane` is full
+    const uint32_t sample = svalid ? rk[lane * BK + BK - 1] : 0u;
     int pos[K - 1][PPT];
 #pragma unroll
     for (int d = 0; d < K - 1; ++d)
 #pragma unroll
         for (int j = 0; j < PPT; ++j) pos[d][j] = 0;
 #pragma unroll
-    for (int step = SMAX / 2; step >= 1; step >>= 1) {
+    for (int step = 16; step >= 1; step >>= 1) {
+#pragma unroll
+        for (int d = 0; d < K - 1; ++d)
+#pragma unroll
+            for (int j = 0; j < PPT; ++j) {
+                const int c = pos[d][j] + step - 1;  // block index
+                const uint32_t sc = __shfl_sync(0xffffffffu, sample, c);
+                if (c * BK + BK - 1 < S && sc < v[d + 1][j]) pos[d][j] += step;
+            }
+    }
+#pragma unroll
+    for (int d = 0; d < K - 1; ++d)
+#pragma unroll
+        for (int j = 0; j < PPT; ++j) pos[d][j] *= BK;
+#pragma unroll
+    for (int step = BK / 2; step >= 1; step >>= 1) {
 #pragma unroll
         for (int d = 0; d < K - 1; ++d)
 #pragma unroll

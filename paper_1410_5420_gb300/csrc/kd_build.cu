@@ -811,6 +811,17 @@ __device__ __forceinline__ unsigned long long global_ns() {
         }                                                                          \
     } while (0)
 
+// Slot of entry i of the unit's rank table: within each run of 32 entries
+// the low five index bits are XORed with the entry's block of SMAX / 32,
+// so that the lanes of a warp searching different blocks at the same
+// offset read different banks.
+template <int SMAX>
+__device__ __forceinline__ int rk_slot(int i) {
+    constexpr int SH = SMAX == 1024 ? 5 : (SMAX == 2048 ? 6 : 7);
+    static_assert((SMAX >> SH) == 32, "32 blocks per unit");
+    return i ^ ((i >> SH) & 31);
+}
+
 // A finisher unit's input: rk[i] = rank 0 of array 0's element i (array 0
 // is sorted by rank 0), and for arrays d >= 1 the lid of each element (its
 // position in array 0).  All K loads per position are in flight before the
@@ -834,7 +845,7 @@ __device__ __forceinline__ void fin_load_unit(const AllBufs& bufs, const CloudDe
 #pragma unroll
     for (int j = 0; j < PPT; ++j) {
         const int i = tid + j * FIN_THREADS;
-        if (i < S) rk[i] = v[0][j];
+        if (i < S) rk[rk_slot<SMAX>(i)] = v[0][j];
     }
     __syncthreads();
     // The K-1 arrays' searches advance together: (K-1) x PPT independent
@@ -845,7 +856,7 @@ __device__ __forceinline__ void fin_load_unit(const AllBufs& bufs, const CloudDe
     constexpr int BK = SMAX / 32;
     const int lane = tid & 31;
     const bool svalid = lane * BK + BK - 1 < S;  // block `lane` is full
-    const uint32_t sample = svalid ? rk[lane * BK + BK - 1] : 0u;
+    const uint32_t sample = svalid ? rk[rk_slot<SMAX>(lane * BK + BK - 1)] : 0u;
     int pos[K - 1][PPT];
 #pragma unroll
     for (int d = 0; d < K - 1; ++d)
@@ -872,7 +883,8 @@ __device__ __forceinline__ void fin_load_unit(const AllBufs& bufs, const CloudDe
         for (int d = 0; d < K - 1; ++d)
 #pragma unroll
             for (int j = 0; j < PPT; ++j)
-                if (pos[d][j] + step <= S && rk[pos[d][j] + step - 1] < v[d + 1][j]) pos[d][j] += step;
+                if (pos[d][j] + step <= S && rk[rk_slot<SMAX>(pos[d][j] + step - 1)] < v[d + 1][j])
+                    pos[d][j] += step;
     }
 #pragma unroll
     for (int d = 1; d < K; ++d)
@@ -880,7 +892,7 @@ __device__ __forceinline__ void fin_load_unit(const AllBufs& bufs, const CloudDe
         for (int j = 0; j < PPT; ++j) {
             const int i = tid + j * FIN_THREADS;
             if (i < S) {
-                if (pos[d - 1][j] >= S || rk[pos[d - 1][j]] != v[d][j]) *bad = 1;
+                if (pos[d - 1][j] >= S || rk[rk_slot<SMAX>(pos[d - 1][j])] != v[d][j]) *bad = 1;
                 arr[d * SMAX + i] = (uint16_t)min(pos[d - 1][j], S - 1);
             }
         }
@@ -914,7 +926,7 @@ __global__ void __launch_bounds__(FIN_THREADS, fin_min_blocks(SMAX, K))
     __shared__ int2 s_lab[fin_labels(SMAX)];
     __shared__ int s_cur[MAXK + 1];
     __shared__ int s_nseg;
-    uint32_t* rk = sm;                                          // rk[lid]: rank 0
+    uint32_t* rk = sm;                                          // rk[rk_slot(lid)]: rank 0
     uint32_t* seg = rk + smax;                                  // packed segment per position
     uint16_t* arr = reinterpret_cast<uint16_t*>(seg + smax);   // (k+1) storages of lids
     uint16_t* nodelid = arr + (size_t)(k + 1) * smax;           // tuple chosen at each position
@@ -1122,7 +1134,7 @@ __global__ void __launch_bounds__(FIN_THREADS, fin_min_blocks(SMAX, K))
             bad = 1;
             continue;
         }
-        const uint32_t r0 = rk[nl];
+        const uint32_t r0 = rk[rk_slot<SMAX>((int)nl)];
         if (r0 >= C.off && r0 < C.off + C.m)
             C.node[lo + i] = (int32_t)((int64_t)perm0[r0] - C.in_off);
         else

@@ -971,8 +971,11 @@ __global__ void __launch_bounds__(FIN_THREADS, fin_min_blocks(SMAX, K))
     // the segment's median offset becomes the node, the others take the
     // label of their half.
     int dl = 0;
+    int ordered = -1;  // the array the last block level leaves in final segment order
     for (; (S >> dl) > 32; ++dl) {
         const int p = (C.lam + dl) % k;
+        const bool last_block_level = (S >> (dl + 1)) <= 32;
+        if (last_block_level) ordered = p;
         if (dl == 0) {
             // the unit is one segment: a tuple's rank is its position in array p
             const uint16_t* A = arr + p * smax;
@@ -1004,6 +1007,10 @@ __global__ void __launch_bounds__(FIN_THREADS, fin_min_blocks(SMAX, K))
                     lab[lid[j]] = LAB_DONE;
                 } else {
                     lab[lid[j]] = (uint8_t)(2 * X + (r > off ? 1 : 0));
+                    // the halves of segment X are [a, c-1] and [c+1, b]:
+                    // rank r in key-p order puts the tuple at a + r in both
+                    // (every read of the array preceded the ranking's barrier)
+                    if (last_block_level) arr[p * smax + ab.x + r] = (uint16_t)lid[j];
                 }
             }
         }
@@ -1012,8 +1019,11 @@ __global__ void __launch_bounds__(FIN_THREADS, fin_min_blocks(SMAX, K))
     }
     FIN_STAMP(1);  // block levels
     // every array in key order within each remaining segment: a stable
-    // multisplit by label, in place (all reads precede the first barrier)
+    // multisplit by label, in place (all reads precede the first barrier);
+    // the last block level's primary array is in that order already (at
+    // dl = 0 each half keeps its place, deeper levels wrote it above)
     for (int q = 0; q < k; ++q) {
+        if (q == ordered) continue;
         uint16_t* A = arr + q * smax;
         uint32_t lid[GMAX], dig[GMAX], rank[GMAX];
         fin_label_rank<SMAX>(A, S, dl, lab, s_wc, s_lab, lid, dig, rank, &bad);

@@ -96,6 +96,20 @@ def test_ragged_sizes(cuda_lib, ctx, n):
     assert_same_tree(gpu_tree(cuda_lib, ctx, coords), oracle.build_tree(coords))
 
 
+# One finisher unit whose last block level is each depth dl = 0..4 (the
+# unit holds 33..64, 65..128, ..., 513..1024 tuples): that level writes its
+# primary array in final segment order itself, every other array goes
+# through the multisplit.
+UNIT_SIZES = [34, 63, 64, 65, 100, 127, 128, 129, 200, 255, 256, 257, 511, 512, 513, 777, 1000]
+
+
+@pytest.mark.parametrize("k", [2, 3, 5])
+@pytest.mark.parametrize("n", UNIT_SIZES)
+def test_finisher_unit_sizes(cuda_lib, ctx, n, k):
+    coords = kdgen.cloud_int_uniform(n, k, 30, 4000 + 7 * n + k, np.int64)
+    assert_same_tree(gpu_tree(cuda_lib, ctx, coords), oracle.build_tree(coords))
+
+
 @pytest.mark.parametrize("k", [2, 3, 4, 5, 6, 7, 8])
 def test_small_switch_threshold_runs_many_level_passes(cuda_lib, k):
     """A small on-chip threshold forces many fused level passes and catch-up
